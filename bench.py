@@ -1,0 +1,420 @@
+#!/usr/bin/env python3
+"""Throughput of warm-started mixed-precision multigrid Poisson solves on one GB300.
+
+Workload, one step: ten periodic Poisson solves A phi = delta_t on a 512^3 mesh,
+delta_t = delta_0 + 0.05 t eta (t = 0..9; delta_0, eta seeded zero-mean
+unit-variance Gaussian random fields with P(k) ~ k^-2).  t = 0 starts from
+phi = 0, every later solve is warm-started from the previous phi (defect
+correction, Sec. 3.2), each runs V(3,3) Chebyshev cycles in FP32 inside the
+double-float outer refinement until ||F - A phi|| / ||F|| <= 1e-6.
+Metric: solves/s (whole job, all ranks).  Inputs (1 GiB each) are larger than L2.
+
+Also reported: per-kernel HBM roofline of the finest-level kernels (CUDA events
+on the solver's stream during the timed region), the end-to-end rate through the
+host-buffer C-ABI call, the plain FP64 V-cycle and cuFFT spectral solves of the
+same sources on the same GPU, SM clocks sampled during the timed region, and the
+CPU oracle timed on a bounded sample.
+
+--impl reference times the CPU oracle (the reference implementation of this
+build) on a bounded sample per step instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solves/s to rel. residual 1e-6 at 512^3 (warm-started sequence of 10 sources)"
+UNIT = "solves/s"
+# algorithmic bytes per finest-level cell of each timed kernel family
+BYTES_PER_CELL = {
+    "down0": 4 + 4 + 0.5,          # read r, write e, write R(r - A e) at 1/8 size
+    "up0": 4 + 4 + 0.5 + 4,        # read e, r, coarse e at 1/8; write e
+    "df0": 8 + 4 + 8 + 8 + 4,      # read phi (df), e, F (df); write phi (df), r
+}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--n", type=int, default=512)
+    p.add_argument("--seq", type=int, default=10)
+    p.add_argument("--tol", type=float, default=1e-6)
+    p.add_argument("--degree", type=int, default=3)
+    p.add_argument("--no-fused", action="store_true")
+    p.add_argument("--no-extras", action="store_true", help="skip e2e, baselines and CPU oracle legs")
+    p.add_argument("--max-vcycles", type=int, default=40)
+    return p.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def ncu_traffic(family):
+    """DRAM bytes per cell of a kernel from a committed ncu summary, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        src = os.path.join(ROOT, d["source"])
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if digest != d["source_sha256_16"]:
+            return None
+        return d["kernels"].get(family)
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [v.strip() for v in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sources(n, seq, rank):
+    """Host float64 sources of the warm-started sequence (seeds 2 and 3, shifted per rank)."""
+    from synth import grf
+    d0 = grf(n, 2 + 1000 * rank)
+    eta = grf(n, 3 + 1000 * rank)
+    return [d0 + (0.05 * t) * eta for t in range(seq)]
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+
+def oracle_sample(n_full, seq, tol):
+    """One oracle V-cycle at 256^3 (scaled by (n/256)^3) times the oracle's cycles per solve.
+
+    The cycles per solve come from the oracle's own solve of the same source recipe at
+    64^3 (the V-cycle's convergence factor is mesh-independent).
+    """
+    import numpy as np
+
+    from oracle import flat
+    from synth import grf
+    ns = min(256, n_full)
+    r = grf(ns, 5)
+    t0 = time.perf_counter()
+    flat.vcycle(0, np.zeros_like(r), r, len(flat.level_shapes(r.shape)))
+    t_cycle = (time.perf_counter() - t0) * (n_full / ns) ** 3
+    m = 64
+    d0, eta = grf(m, 2), grf(m, 3)
+    phi = np.zeros((m, m, m))
+    cycles = []
+    for t in range(seq):
+        phi, hist = flat.mg_solve(d0 + (0.05 * t) * eta, phi0=phi, tol=tol, max_cycles=50)
+        cycles.append(len(hist) - 1)
+    cps = sum(cycles) / len(cycles)
+    return {"value": 1.0 / (t_cycle * cps), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"one oracle FP64 V-cycle at {ns}^3 ({t_cycle / (n_full / ns) ** 3:.2f} s, NumPy, one thread), "
+                       f"scaled by {(n_full / ns) ** 3:.0f} to {n_full}^3 and by the oracle's {cps:.2f} cycles per solve "
+                       f"on the same 10-source recipe at 64^3")}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    samples = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        s = oracle_sample(args.n, args.seq, args.tol)
+        if k >= args.warmup:
+            samples.append((s, time.perf_counter() - t0))
+    vals = [s["value"] for s, _ in samples]
+    value = statistics.median(vals)
+    cpu = dict(samples[-1][0])
+    cpu["value"] = value
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * args.seq / value, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"periodic 3-D Poisson {args.n}^3, warm-started sequence of {args.seq} GRF sources, tol {args.tol:g}",
+                   "n": args.n, "sources": args.seq, "tol": args.tol},
+        "cpu_baseline": cpu,
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2607_10983_gb300 as gb
+    from paper_2607_10983_gb300 import _build
+
+    world, rank, local = dist_setup(args.gpus)
+    _build.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n, seq = args.n, args.seq
+    cells = n ** 3
+
+    host_src = sources(n, seq, rank)
+    F = [torch.from_numpy(a).to(dev) for a in host_src]
+    phi = torch.zeros((n, n, n), dtype=torch.float64, device=dev)
+    solver = gb.Solver(n, prec="mixed", degree=args.degree, fused=not args.no_fused)
+    stream = torch.cuda.current_stream()
+    cycles_log = []
+
+    def step(record=False):
+        phi.zero_()
+        for t in range(seq):
+            _, st = solver.solve(F[t], phi, tol=args.tol, max_vcycles=args.max_vcycles)
+            if st.status != 0:
+                raise RuntimeError(f"solve {t} failed: status {st.status}, rel_res {st.rel_res:.3e}")
+            if record:
+                cycles_log.append(st.cycles)
+
+    for _ in range(args.warmup):
+        step()
+    families = ["down0", "up0", "df0"] if not args.no_fused else ["smooth0", "df0"]
+    solver.profile_begin(families)
+    launches0 = gb.launch_count()
+    torch.cuda.synchronize()
+    barrier(world)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(torch.cuda.current_device()) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step(record=True)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    launches = gb.launch_count() - launches0
+    ms_total = max_over_ranks(ev0.elapsed_time(ev1), world)
+    prof = {f: solver.profile_read(f) for f in families}
+    solver.profile_end()
+    ms_per_step = ms_total / args.steps
+    value = world * seq * args.steps / (ms_total / 1000.0)
+
+    hbm_peak, peak_kind = measured_peaks()
+    kernels = {}
+    for f, (cnt, kms) in prof.items():
+        if cnt == 0:
+            continue
+        bpc = BYTES_PER_CELL.get(f, 20.0 if f == "smooth0" else 0.0)
+        avg_ms = kms / cnt
+        gbs = bpc * cells / (avg_ms / 1000.0) / 1e9
+        kernels[f] = {"launches": cnt, "avg_ms": avg_ms, "share_of_step": kms / ms_total,
+                      "bytes_per_cell": bpc, "achieved_gbs": gbs, "frac": gbs / hbm_peak}
+    dom = max(kernels, key=lambda f: kernels[f]["avg_ms"] * kernels[f]["launches"])
+    tr = ncu_traffic(dom)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": kernels[dom]["achieved_gbs"], "peak": hbm_peak,
+                "peak_kind": f"{peak_kind} copy bandwidth (burst)", "unit": "GB/s",
+                "frac": kernels[dom]["achieved_gbs"] / hbm_peak,
+                "traffic": (tr * cells if tr is not None else None)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"periodic 3-D Poisson {n}^3, warm-started sequence of {seq} GRF sources "
+                               f"(P(k)~k^-2), tol {args.tol:g}, V({args.degree},{args.degree}) Chebyshev, "
+                               f"{solver.levels} levels, mixed precision"
+                               + ("" if not args.no_fused else ", unfused"),
+                   "n": n, "sources": seq, "tol": args.tol, "levels": solver.levels,
+                   "l2": "inputs larger than L2 (1 GiB per field)", "parallelism": f"replicas x{world}"},
+        "cycles_per_solve": sum(cycles_log) / max(1, len(cycles_log)),
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "kernels": kernels,
+    }
+    clocks = clk.summary()
+    if clocks:
+        line["clocks"] = clocks
+
+    if not args.no_extras and rank == 0:
+        line["e2e"] = e2e_leg(args, solver, host_src)
+        line["baselines"] = baseline_legs(args, F, dev)
+        line["cpu_baseline"] = oracle_sample(n, seq, args.tol)
+    if rank == 0:
+        print(json.dumps(line))
+    solver.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def e2e_leg(args, solver, host_src):
+    """Same sequence through mg_solve_host: host buffers in, host result out, copies timed."""
+    import torch
+    n, seq = args.n, args.seq
+    pinned = [torch.from_numpy(a).pin_memory() for a in host_src]
+    phi_h = torch.zeros((n, n, n), dtype=torch.float64).pin_memory()
+
+    def step():
+        phi_h.zero_()
+        for t in range(seq):
+            solver.solve_host(pinned[t], phi_h, tol=args.tol, max_vcycles=args.max_vcycles)
+
+    step()
+    steps = max(1, min(args.steps, 2))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    dt = time.perf_counter() - t0
+    b = n ** 3 * 8
+    return {"value": seq * steps / dt, "unit": UNIT, "h2d_bytes_per_step": seq * 2 * b,
+            "d2h_bytes_per_step": seq * b, "api": "mg_solve_host (pinned host buffers)"}
+
+
+def baseline_legs(args, F, dev):
+    """Plain FP64 V-cycle (one kernel per operation) and cuFFT spectral solves of the same sources."""
+    import math
+
+    import torch
+
+    import paper_2607_10983_gb300 as gb
+    n = args.n
+    out = {}
+    # plain FP64 V-cycle on the first three sources of the sequence (cold, warm, warm)
+    s64 = gb.Solver(n, prec="fp64", degree=args.degree)
+    phi = torch.zeros_like(F[0])
+    cyc = 0
+    s64.solve(F[1], phi.clone(), tol=1e-2, max_vcycles=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for t in range(3):
+        _, st = s64.solve(F[t], phi, tol=args.tol, max_vcycles=args.max_vcycles)
+        cyc += st.cycles
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    out["plain_fp64_vcycle"] = {"solves_per_s": 3 / dt, "cycles_per_solve": cyc / 3,
+                                "ms_per_cycle": 1000 * dt / cyc, "sources": "t = 0, 1, 2 of the sequence"}
+    s64.close()
+    del phi
+    # cuFFT spectral solve of the same 7-point operator (torch.fft), FP64 and FP32
+    kz = 2 * math.pi * torch.fft.fftfreq(n, device=dev, dtype=torch.float64)
+    kx = 2 * math.pi * torch.fft.rfftfreq(n, device=dev, dtype=torch.float64)
+    lam = -4.0 * (torch.sin(kz / 2)[:, None, None] ** 2 + torch.sin(kz / 2)[None, :, None] ** 2
+                  + torch.sin(kx / 2)[None, None, :] ** 2)
+    lam[0, 0, 0] = 1.0
+    inv = 1.0 / lam
+    inv[0, 0, 0] = 0.0
+    for name, dt_ in (("cufft_fp64", torch.float64), ("cufft_fp32", torch.float32)):
+        iv = inv.to(dt_)
+        srcs = [f.to(dt_) for f in F[:3]]
+
+        def solve(f):
+            return torch.fft.irfftn(torch.fft.rfftn(f) * iv, s=(n, n, n))
+
+        solve(srcs[0])
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for f in srcs:
+            solve(f)
+        ev1.record()
+        torch.cuda.synchronize()
+        out[name] = {"solves_per_s": 3 / (ev0.elapsed_time(ev1) / 1000.0),
+                     "note": "rfftn, divide by the 7-point symbol, irfftn; inputs resident"}
+        del srcs
+    return out
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,203 @@
+/*
+ * gbmg.h — C ABI of the GB300 geometric-multigrid Poisson library.
+ *
+ * The library solves the particle-mesh Poisson problem on a periodic 3-D mesh by
+ * geometric multigrid V-cycles (arxiv 2607.10983, Sec. 2.3 "Geometric multigrid"):
+ *
+ *   flat operator  (GBMG_OP_FLAT7): A phi = F, A the second-order 7-point
+ *                  Laplacian (Sec. 2.1, Eq. linsys), F mean-projected, phi zero mean.
+ *
+ * Conventions for every entry point
+ *   - Fields are dense arrays of nx*ny*nz values, row-major [z][y][x] with x the
+ *     fastest index, mesh spacing one cell on the finest level (h_l = 2^l on level l).
+ *   - Pointers named *_dev are device pointers on the device that was current at
+ *     mg_setup; pointers named *_host are host pointers (pinned or pageable).
+ *   - The caller owns every buffer passed in; the library never keeps a pointer
+ *     past the call.  The library owns its hierarchy workspace (allocated once in
+ *     mg_setup, released in mg_destroy).
+ *   - All GPU work is queued on the context's stream (mg_setup / mg_set_stream).
+ *     Component calls return after queueing; solves wait for the stream.
+ *   - Every function returns a gbmg_status and never throws or aborts.  CUDA errors
+ *     map to GBMG_ERR_CUDA; mg_last_error() gives the message of the last failure
+ *     in this thread.
+ *   - dtype arguments select the element type of component calls: GBMG_F32 (float)
+ *     or GBMG_F64 (double).
+ */
+#ifndef GBMG_H
+#define GBMG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gbmg_ctx gbmg_ctx;
+
+typedef enum {
+  GBMG_OK = 0,
+  GBMG_ERR_INVALID_ARG = 1, /* bad sizes, NULL pointers, unsupported option         */
+  GBMG_ERR_CUDA = 2,        /* a CUDA runtime call or kernel launch failed            */
+  GBMG_ERR_OOM = 3,         /* device or pinned-host allocation failed                */
+  GBMG_ERR_NOT_CONVERGED = 4, /* max_vcycles reached above tol; phi holds the last iterate */
+  GBMG_ERR_NONFINITE = 5,   /* a residual norm was NaN or inf; phi holds the last iterate */
+  GBMG_ERR_DIVERGED = 6,    /* residual grew 10x over two cycles; phi holds the last iterate */
+  GBMG_ERR_STATE = 7        /* call not valid in the context's current state          */
+} gbmg_status;
+
+typedef enum { GBMG_OP_FLAT7 = 0, GBMG_OP_CURV19 = 1 } gbmg_op;
+/* GBMG_FP64: plain FP64 V-cycle, one kernel per operation (the baseline method).
+ * GBMG_MIXED: FP32 V-cycle inside FP64-accurate defect correction (Sec. 3.2) whose
+ *             residual and solution update use double-float (two-FP32) arithmetic. */
+typedef enum { GBMG_FP64 = 0, GBMG_MIXED = 1 } gbmg_prec;
+typedef enum { GBMG_SMOOTH_CHEBYSHEV = 0, GBMG_SMOOTH_JACOBI = 1 } gbmg_smoother;
+typedef enum { GBMG_F32 = 0, GBMG_F64 = 1 } gbmg_dtype;
+
+/* Solver options.  gbmg_default_opts fills the paper's defaults:
+ * Chebyshev degree 3 on [2/alpha, 2] with alpha = 8 (Sec. 2.3, Eq. flat_chebyshev),
+ * Jacobi omega = 2/3 with nu1 = nu2 = 2 (Sec. 2.3 Eq. flat_jacobi, Sec. 4.3.3),
+ * mixed precision, fused level kernels. */
+typedef struct {
+  int op;        /* gbmg_op                                                        */
+  int prec;      /* gbmg_prec                                                      */
+  int smoother;  /* gbmg_smoother                                                  */
+  int degree;    /* Chebyshev: operator applications per smoothing pass (>= 1)     */
+  double alpha;  /* Chebyshev target interval [2/alpha, 2] of D^-1 A (alpha > 1)   */
+  int nu1, nu2;  /* Jacobi sweeps before / after the coarse correction (>= 0)      */
+  double omega;  /* Jacobi weight                                                  */
+  int fused;     /* 1: temporally blocked level kernels (GBMG_MIXED + Chebyshev);   */
+                 /* 0: one kernel per operation                                    */
+} gbmg_opts;
+
+typedef struct {
+  int cycles;           /* V-cycles performed by the call                          */
+  int status;           /* gbmg_status of the solve                                */
+  double rel_res0;      /* ||F - A phi0|| / ||F|| before the first cycle           */
+  double rel_res;       /* ||F - A phi|| / ||F|| after the last cycle              */
+  double res_hist[64];  /* relative residual after cycle k (k < 64)                */
+} gbmg_stats;
+
+/* Fill *opts with the defaults listed above.  opts must not be NULL. */
+void gbmg_default_opts(gbmg_opts* opts);
+
+/* Create a solver for an nx x ny x nz periodic mesh (Sec. 2.3 hierarchy).
+ *   levels: number of levels, 0 = as many as possible.  A level is coarsened while
+ *           every side is even and half of it is at least 4, so n^3 with n a power
+ *           of two gives log2(n) - 1 levels (Sec. 4.3.3); the coarsest level is solved
+ *           exactly on the zero-mean subspace.  The coarsest level may hold at most
+ *           512 cells.
+ *   smoother_degree: Chebyshev degree (overrides opts->degree when > 0).
+ *   opts: NULL = defaults.  cuda_stream: a cudaStream_t, NULL = legacy default stream.
+ * Errors: GBMG_ERR_INVALID_ARG for sides < 4, a coarsest level above 512 cells or bad
+ * options; GBMG_ERR_OOM when the hierarchy does not fit; *out is set only on success. */
+gbmg_status mg_setup(gbmg_ctx** out, int nx, int ny, int nz, int levels, int smoother_degree,
+                     const gbmg_opts* opts, void* cuda_stream);
+
+/* Release everything the context owns.  NULL is ignored. */
+void mg_destroy(gbmg_ctx* ctx);
+
+/* Queue later work on `cuda_stream` (a cudaStream_t; NULL = legacy default stream). */
+gbmg_status mg_set_stream(gbmg_ctx* ctx, void* cuda_stream);
+
+/* Solve A phi = F (Sec. 2.1).  source_dev: F (nx*ny*nz doubles; its mean is
+ * projected out, the buffer is not modified).  coeffs_dev: must be NULL for the flat
+ * operator.  phi_inout_dev: initial guess in (zeros = cold start, previous solution =
+ * warm start, Sec. 3.1-3.2), zero-mean solution out.  V-cycles run until
+ * ||F - A phi|| / ||F|| <= tol or max_vcycles cycles (max_vcycles <= 0 runs none and
+ * only evaluates the residual).  The call waits for the stream and returns the
+ * convergence status: GBMG_OK, or NOT_CONVERGED / NONFINITE / DIVERGED with phi still
+ * written (last iterate, gauge applied).  stats: NULL or filled on return; the same
+ * record is kept for mg_last_stats(). */
+gbmg_status mg_solve(gbmg_ctx* ctx, const double* source_dev, const float* coeffs_dev,
+                     double* phi_inout_dev, double tol, int max_vcycles, gbmg_stats* stats);
+
+/* Same solve with host buffers: copies F and the initial phi to the device, solves,
+ * copies phi back and waits.  Staging buffers are allocated on the first call and
+ * kept until mg_destroy. */
+gbmg_status mg_solve_host(gbmg_ctx* ctx, const double* source_host, double* phi_inout_host,
+                          double tol, int max_vcycles, gbmg_stats* stats);
+
+/* Statistics of the last completed mg_solve on this context (waits for the stream). */
+gbmg_status mg_last_stats(gbmg_ctx* ctx, gbmg_stats* stats);
+
+/* Number of levels, and the sides of level `level` (0 = finest). */
+int mg_num_levels(const gbmg_ctx* ctx);
+gbmg_status mg_level_dims(const gbmg_ctx* ctx, int level, int* nx, int* ny, int* nz);
+
+/* ---------------------------------------------------------------------------------
+ * Measurement.  While a kernel family is being timed, every launch of it is
+ * bracketed by CUDA events on the context's stream (no extra synchronisation).
+ * --------------------------------------------------------------------------------- */
+typedef enum {
+  GBMG_PROF_OFF = 0,
+  GBMG_PROF_DOWN0 = 1,   /* finest level, fused pre-smoothing + residual + restriction  */
+  GBMG_PROF_UP0 = 2,     /* finest level, fused prolongation + post-smoothing            */
+  GBMG_PROF_DF0 = 3,     /* finest level, double-float update and residual               */
+  GBMG_PROF_SMOOTH0 = 4  /* finest level, one-kernel-per-operation smoother steps        */
+} gbmg_prof_family;
+
+/* Start timing the kernel families whose bits (1 << family) are set in family_mask
+ * (waits for the stream; clears earlier records). */
+gbmg_status mg_profile_begin(gbmg_ctx* ctx, int family_mask);
+/* Number of timed launches of `family` since mg_profile_begin and their summed device
+ * time in milliseconds (waits for the stream; timing continues). */
+gbmg_status mg_profile_read(gbmg_ctx* ctx, int family, int* launches, double* total_ms);
+/* Stop timing and clear the records. */
+gbmg_status mg_profile_end(gbmg_ctx* ctx);
+/* Number of kernels this library has launched in the process so far. */
+long long mg_launch_count(void);
+
+/* Human-readable status; never NULL. */
+const char* mg_status_string(gbmg_status s);
+/* Message of the last error raised in the calling thread ("" if none). */
+const char* mg_last_error(void);
+
+/* ---------------------------------------------------------------------------------
+ * Component calls: one operation of the V-cycle on level `level`, on caller buffers
+ * of that level's size, in precision dtype.  They exist so that each kernel can be
+ * checked on its own; they run the same kernels as mg_solve.
+ * --------------------------------------------------------------------------------- */
+
+/* out = A_l u: 7-point Laplacian with spacing h_l = 2^level (Sec. 2.1, rediscretised
+ * per level, Sec. 2.3). */
+gbmg_status mg_apply(gbmg_ctx* ctx, int level, int dtype, const void* u_dev, void* out_dev);
+
+/* out = f - A_l u (Sec. 2.3, Eq. flat_residual). */
+gbmg_status mg_residual(gbmg_ctx* ctx, int level, int dtype, const void* f_dev, const void* u_dev,
+                        void* out_dev);
+
+/* One smoothing pass of the configured smoother on A_l e = r, in place on e:
+ * Chebyshev (Eq. flat_chebyshev, `degree` operator applications) or weighted Jacobi
+ * (Eq. flat_jacobi, nu1 sweeps). */
+gbmg_status mg_smooth(gbmg_ctx* ctx, int level, int dtype, void* e_inout_dev, const void* r_dev);
+
+/* coarse = R fine: full weighting [1/4,1/2,1/4] per axis then decimation (Appendix B);
+ * fine is level `level`, coarse is level+1. */
+gbmg_status mg_restrict(gbmg_ctx* ctx, int level, int dtype, const void* fine_dev, void* coarse_dev);
+
+/* fine += P coarse: trilinear prolongation (Sec. 2.3, Eq. coarse_correction);
+ * fine is level `level`, coarse is level+1. */
+gbmg_status mg_prolong_add(gbmg_ctx* ctx, int level, int dtype, const void* coarse_dev, void* fine_dev);
+
+/* e = exact minimum-norm solution of A_c e = r on the coarsest level (Sec. 2.3
+ * "directly on the coarsest level"): the pseudo-inverse, built at setup. */
+gbmg_status mg_coarse_solve(gbmg_ctx* ctx, int dtype, const void* r_dev, void* e_dev);
+
+/* One V-cycle (mu = 1) on the error equation A_0 e = r of the finest level in the
+ * working precision of the context (GBMG_FP64: double, GBMG_MIXED: float), starting
+ * from e = 0, with the configured smoother and fusion. */
+gbmg_status mg_vcycle(gbmg_ctx* ctx, const void* r_dev, void* e_dev);
+
+/* Double-float helpers of the mixed-precision path.  A double-float array stores each
+ * value x as the float pair (hi, lo), hi = round(x), lo = round(x - hi): 2*n floats. */
+gbmg_status mg_f64_to_df(gbmg_ctx* ctx, long long n, const double* x_dev, float* df_dev);
+gbmg_status mg_df_to_f64(gbmg_ctx* ctx, long long n, const float* df_dev, double* x_dev);
+/* r = (F - m) - A_0 phi on the finest level in double-float arithmetic, rounded to
+ * float; F and phi are double-float arrays, m a double. */
+gbmg_status mg_df_residual(gbmg_ctx* ctx, const float* F_df_dev, double m, const float* phi_df_dev,
+                           float* r_dev);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBMG_H */

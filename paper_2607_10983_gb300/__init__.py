@@ -1,0 +1,310 @@
+"""GB300-native geometric multigrid for the particle-mesh Poisson equation.
+
+Thin ctypes binding of the C ABI in include/gbmg.h (libgbmg.so, built in-tree by
+`_build.build()`).  This module only marshals arguments: every step of a solve
+runs in the library's CUDA kernels.  Tensors are torch CUDA tensors, contiguous,
+shaped (nz, ny, nx) with x fastest; torch's current stream is used for each call.
+
+If libgbmg.so is missing the import still succeeds but every call raises
+RuntimeError: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+from . import _build
+
+__all__ = ["Solver", "GbmgError", "Stats", "lib", "library_path", "launch_count", "F32", "F64"]
+
+F32, F64 = 0, 1
+OP_FLAT7, OP_CURV19 = 0, 1
+FP64, MIXED = 0, 1
+CHEBYSHEV, JACOBI = 0, 1
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of memory", 4: "not converged",
+          5: "non-finite residual", 6: "diverged", 7: "invalid state"}
+CONVERGENCE_STATUSES = (4, 5, 6)
+
+
+class GbmgError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int), ("prec", ctypes.c_int), ("smoother", ctypes.c_int),
+                ("degree", ctypes.c_int), ("alpha", ctypes.c_double), ("nu1", ctypes.c_int),
+                ("nu2", ctypes.c_int), ("omega", ctypes.c_double), ("fused", ctypes.c_int)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("cycles", ctypes.c_int), ("status", ctypes.c_int), ("rel_res0", ctypes.c_double),
+                ("rel_res", ctypes.c_double), ("res_hist", ctypes.c_double * 64)]
+
+
+@dataclass
+class Stats:
+    cycles: int
+    status: int
+    rel_res0: float
+    rel_res: float
+    history: list
+
+    @classmethod
+    def from_c(cls, s: _Stats) -> "Stats":
+        return cls(s.cycles, s.status, s.rel_res0, s.rel_res, [s.res_hist[i] for i in range(min(s.cycles, 64))])
+
+
+_LIB = None
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_LL = ctypes.c_longlong
+_S = ctypes.c_int  # gbmg_status
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "gbmg_default_opts": (None, [ctypes.POINTER(_Opts)]),
+    "mg_setup": (_S, [ctypes.POINTER(_P), _I, _I, _I, _I, _I, ctypes.POINTER(_Opts), _P]),
+    "mg_destroy": (None, [_P]),
+    "mg_set_stream": (_S, [_P, _P]),
+    "mg_solve": (_S, [_P, _P, _P, _P, _D, _I, ctypes.POINTER(_Stats)]),
+    "mg_solve_host": (_S, [_P, _P, _P, _D, _I, ctypes.POINTER(_Stats)]),
+    "mg_last_stats": (_S, [_P, ctypes.POINTER(_Stats)]),
+    "mg_num_levels": (_I, [_P]),
+    "mg_level_dims": (_S, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "mg_status_string": (ctypes.c_char_p, [_S]),
+    "mg_last_error": (ctypes.c_char_p, []),
+    "mg_apply": (_S, [_P, _I, _I, _P, _P]),
+    "mg_residual": (_S, [_P, _I, _I, _P, _P, _P]),
+    "mg_smooth": (_S, [_P, _I, _I, _P, _P]),
+    "mg_restrict": (_S, [_P, _I, _I, _P, _P]),
+    "mg_prolong_add": (_S, [_P, _I, _I, _P, _P]),
+    "mg_coarse_solve": (_S, [_P, _I, _P, _P]),
+    "mg_vcycle": (_S, [_P, _P, _P]),
+    "mg_f64_to_df": (_S, [_P, _LL, _P, _P]),
+    "mg_df_to_f64": (_S, [_P, _LL, _P, _P]),
+    "mg_df_residual": (_S, [_P, _P, _D, _P, _P]),
+    "mg_profile_begin": (_S, [_P, _I]),
+    "mg_profile_read": (_S, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "mg_profile_end": (_S, [_P]),
+    "mg_launch_count": (_LL, []),
+}
+
+PROF = {"down0": 1, "up0": 2, "df0": 3, "smooth0": 4}
+
+
+def launch_count() -> int:
+    """Kernels launched by libgbmg.so in this process so far."""
+    return int(lib().mg_launch_count())
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libgbmg.so (built by `_build.build()`); raises if it is not there."""
+    global _LIB
+    if _LIB is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libgbmg.so is not built ({path}); run __graft_entry__.build() first")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _check(status: int, allow_convergence: bool = False):
+    if status == 0 or (allow_convergence and status in CONVERGENCE_STATUSES):
+        return
+    raise GbmgError(status, lib().mg_last_error().decode())
+
+
+def _ptr(t: torch.Tensor | None, dtype=None, shape=None) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"expected dtype {dtype}, got {t.dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"expected shape {tuple(shape)}, got {tuple(t.shape)}")
+    return t.data_ptr()
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.float64:
+        return F64
+    raise ValueError("expected float32 or float64")
+
+
+def _shape3(n) -> tuple[int, int, int]:
+    if isinstance(n, int):
+        return (n, n, n)
+    return tuple(int(v) for v in n)
+
+
+class Solver:
+    """One multigrid hierarchy for a periodic (nz, ny, nx) mesh on the current CUDA device."""
+
+    def __init__(self, shape, levels: int = 0, degree: int = 3, prec: str = "mixed",
+                 smoother: str = "chebyshev", fused: bool = True, alpha: float = 8.0,
+                 nu1: int = 2, nu2: int = 2, omega: float = 2.0 / 3.0, op: str = "flat"):
+        L = lib()
+        self.shape = _shape3(shape)
+        o = _Opts()
+        L.gbmg_default_opts(ctypes.byref(o))
+        o.op = {"flat": OP_FLAT7, "curv": OP_CURV19}[op]
+        o.prec = {"fp64": FP64, "mixed": MIXED}[prec]
+        o.smoother = {"chebyshev": CHEBYSHEV, "jacobi": JACOBI}[smoother]
+        o.degree, o.alpha, o.nu1, o.nu2, o.omega, o.fused = degree, alpha, nu1, nu2, omega, int(fused)
+        self.prec = prec
+        self.work_dtype = torch.float64 if prec == "fp64" else torch.float32
+        ctx = _P()
+        nz, ny, nx = self.shape
+        _check(L.mg_setup(ctypes.byref(ctx), nx, ny, nz, levels, degree, ctypes.byref(o),
+                          torch.cuda.current_stream().cuda_stream))
+        self._ctx = ctx
+        self.levels = L.mg_num_levels(ctx)
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_ctx", None):
+            lib().mg_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _c(self):
+        if not self._ctx:
+            raise RuntimeError("solver is closed")
+        _check(lib().mg_set_stream(self._ctx, torch.cuda.current_stream().cuda_stream))
+        return self._ctx
+
+    def level_shape(self, level: int) -> tuple[int, int, int]:
+        x, y, z = _I(), _I(), _I()
+        _check(lib().mg_level_dims(self._ctx, level, ctypes.byref(x), ctypes.byref(y), ctypes.byref(z)))
+        return (z.value, y.value, x.value)
+
+    # -- solves
+    def solve(self, F: torch.Tensor, phi: torch.Tensor | None = None, tol: float = 1e-6,
+              max_vcycles: int = 50, raise_on_nonconvergence: bool = False):
+        """Solve A phi = F; phi (float64, same shape) is the warm start and is overwritten.
+
+        Returns (phi, Stats).  Non-convergence is reported in Stats.status unless
+        raise_on_nonconvergence is set.
+        """
+        ctx = self._c()
+        if phi is None:
+            phi = torch.zeros_like(F)
+        st = _Stats()
+        s = lib().mg_solve(ctx, _ptr(F, torch.float64, self.shape), None, _ptr(phi, torch.float64, self.shape),
+                           float(tol), int(max_vcycles), ctypes.byref(st))
+        _check(s, allow_convergence=not raise_on_nonconvergence)
+        return phi, Stats.from_c(st)
+
+    def solve_host(self, F, phi, tol: float = 1e-6, max_vcycles: int = 50):
+        """Same solve on host float64 arrays (numpy or CPU tensors); phi is overwritten."""
+        import numpy as np
+        Fa = F.numpy() if isinstance(F, torch.Tensor) else F
+        Pa = phi.numpy() if isinstance(phi, torch.Tensor) else phi
+        for a in (Fa, Pa):
+            if a.dtype != np.float64 or not a.flags.c_contiguous or tuple(a.shape) != self.shape:
+                raise ValueError("expected C-contiguous float64 arrays of the solver's shape")
+        st = _Stats()
+        s = lib().mg_solve_host(self._c(), Fa.ctypes.data, Pa.ctypes.data, float(tol), int(max_vcycles),
+                                ctypes.byref(st))
+        _check(s, allow_convergence=True)
+        return phi, Stats.from_c(st)
+
+    # -- measurement
+    def profile_begin(self, families):
+        """Time every launch of the named kernel families (see PROF) with CUDA events."""
+        mask = 0
+        for f in families:
+            mask |= 1 << PROF[f]
+        _check(lib().mg_profile_begin(self._c(), mask))
+
+    def profile_read(self, family: str) -> tuple[int, float]:
+        """(launches, total device milliseconds) of a timed family since profile_begin."""
+        n, ms = _I(), _D()
+        _check(lib().mg_profile_read(self._c(), PROF[family], ctypes.byref(n), ctypes.byref(ms)))
+        return n.value, ms.value
+
+    def profile_end(self):
+        _check(lib().mg_profile_end(self._c()))
+
+    # -- components (each runs one kernel family of the V-cycle)
+    def apply(self, level: int, u: torch.Tensor, out: torch.Tensor | None = None):
+        out = torch.empty_like(u) if out is None else out
+        _check(lib().mg_apply(self._c(), level, _dtype_code(u), _ptr(u, shape=self.level_shape(level)), _ptr(out)))
+        return out
+
+    def residual(self, level: int, f: torch.Tensor, u: torch.Tensor, out: torch.Tensor | None = None):
+        out = torch.empty_like(u) if out is None else out
+        shp = self.level_shape(level)
+        _check(lib().mg_residual(self._c(), level, _dtype_code(u), _ptr(f, u.dtype, shp), _ptr(u, shape=shp),
+                                 _ptr(out, u.dtype, shp)))
+        return out
+
+    def smooth(self, level: int, e: torch.Tensor, r: torch.Tensor):
+        shp = self.level_shape(level)
+        _check(lib().mg_smooth(self._c(), level, _dtype_code(e), _ptr(e, shape=shp), _ptr(r, e.dtype, shp)))
+        return e
+
+    def restrict(self, level: int, fine: torch.Tensor, out: torch.Tensor | None = None):
+        shp = self.level_shape(level + 1)
+        out = torch.empty(shp, dtype=fine.dtype, device=fine.device) if out is None else out
+        _check(lib().mg_restrict(self._c(), level, _dtype_code(fine), _ptr(fine, shape=self.level_shape(level)),
+                                 _ptr(out, fine.dtype, shp)))
+        return out
+
+    def prolong_add(self, level: int, coarse: torch.Tensor, fine: torch.Tensor):
+        _check(lib().mg_prolong_add(self._c(), level, _dtype_code(fine), _ptr(coarse, fine.dtype, self.level_shape(level + 1)),
+                                    _ptr(fine, shape=self.level_shape(level))))
+        return fine
+
+    def coarse_solve(self, r: torch.Tensor, out: torch.Tensor | None = None):
+        out = torch.empty_like(r) if out is None else out
+        shp = self.level_shape(self.levels - 1)
+        _check(lib().mg_coarse_solve(self._c(), _dtype_code(r), _ptr(r, shape=shp), _ptr(out, r.dtype, shp)))
+        return out
+
+    def vcycle(self, r: torch.Tensor, out: torch.Tensor | None = None):
+        out = torch.empty_like(r) if out is None else out
+        _check(lib().mg_vcycle(self._c(), _ptr(r, self.work_dtype, self.shape), _ptr(out, self.work_dtype, self.shape)))
+        return out
+
+    def f64_to_df(self, x: torch.Tensor) -> torch.Tensor:
+        out = torch.empty(x.shape + (2,), dtype=torch.float32, device=x.device)
+        _check(lib().mg_f64_to_df(self._c(), x.numel(), _ptr(x, torch.float64), _ptr(out)))
+        return out
+
+    def df_to_f64(self, df: torch.Tensor) -> torch.Tensor:
+        out = torch.empty(df.shape[:-1], dtype=torch.float64, device=df.device)
+        _check(lib().mg_df_to_f64(self._c(), out.numel(), _ptr(df, torch.float32), _ptr(out)))
+        return out
+
+    def df_residual(self, F_df: torch.Tensor, m: float, phi_df: torch.Tensor) -> torch.Tensor:
+        out = torch.empty(self.shape, dtype=torch.float32, device=F_df.device)
+        _check(lib().mg_df_residual(self._c(), _ptr(F_df, torch.float32), float(m), _ptr(phi_df, torch.float32), _ptr(out)))
+        return out

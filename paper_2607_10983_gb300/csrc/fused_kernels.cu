@@ -1,0 +1,495 @@
+// Temporally blocked FP32 level kernels (the single-GPU form of the paper's
+// communication-avoiding whole-level fusion, Sec. 3.4 implementation list): one
+// HBM pass per level visit instead of one per operation.
+//
+//   k_down_fused : Chebyshev pre-smoothing from e = 0 (degree V), residual and
+//                  full-weighting restriction.  Reads r, writes e and R(r - A e).
+//   k_up_fused   : trilinear prolongation + correction and Chebyshev
+//                  post-smoothing.  Reads e, e_c, r; writes the new e.
+//   k_df_update_residual : finest level, phi' = phi + e in double-float and the
+//                  next defect-correction residual r' = F - m - A phi'.
+//
+// Blocking scheme.  A CTA owns an output tile of TX x TY cells in (x, y) and a
+// chunk of z planes; it computes on the tile plus a halo of H cells, so that the
+// stages, each of which needs its input on one more ring of cells, still produce
+// valid values on the tile.  The CTA streams through z: in each iteration it
+// loads one input plane and every stage advances one plane, stage s working one
+// plane behind stage s-1.  The current plane of each stage's input sits in a
+// padded, double-buffered shared-memory plane (x/y neighbours); the two older
+// planes of the z direction stay in registers.  One barrier per iteration.
+// Cells outside the valid region of a stage hold garbage that never reaches an
+// output.  Arithmetic is the same per-cell code as the one-kernel-per-operation
+// path, so results are bit-identical to it.
+#include <cstdio>
+
+#include "kernels.h"
+#include "stencil.cuh"
+
+namespace gbmg {
+
+namespace {
+
+__device__ __forceinline__ int wrapmod(int i, int n) {
+  const int r = i % n;
+  return r < 0 ? r + n : r;
+}
+
+template <int TX, int TY, int H, int NT>
+struct Tile {
+  static constexpr int WX = TX + 2 * H;
+  static constexpr int WY = TY + 2 * H;
+  static constexpr int NPOS = WX * WY;
+  static constexpr int K = (NPOS + NT - 1) / NT;  // positions per thread
+  static constexpr int PAD = WX + 1;              // padding so p +- 1, p +- WX stay in bounds
+  static constexpr int PLANE = NPOS + 2 * PAD;
+};
+
+// Per-thread position bookkeeping: plane offset of each owned position in the
+// (wrapped) global mesh, and bit masks of valid / in-tile positions.
+template <int TX, int TY, int H, int NT>
+struct Positions {
+  using TL = Tile<TX, TY, H, NT>;
+  int goff[TL::K];
+  unsigned vmask = 0, tmask = 0;
+  __device__ __forceinline__ void init(Dims d, int x0, int y0) {
+#pragma unroll
+    for (int k = 0; k < TL::K; ++k) {
+      const int p = threadIdx.x + k * NT;
+      goff[k] = 0;
+      if (p < TL::NPOS) {
+        const int px = p % TL::WX, py = p / TL::WX;
+        const int ux = x0 - H + px, uy = y0 - H + py;
+        goff[k] = wrapmod(ux, d.nx) + wrapmod(uy, d.ny) * d.nx;
+        vmask |= 1u << k;
+        if (px >= H && px < H + TX && py >= H && py < H + TY && ux < d.nx && uy < d.ny) tmask |= 1u << k;
+      }
+    }
+  }
+};
+
+struct Coef {
+  float c1[16];
+  float c2[16];
+};
+
+// ------------------------------------------------------------------ down leg
+
+template <int V, int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT, 1)
+k_down_fused(Dims d, const float* __restrict__ r, float* __restrict__ e_out, float* __restrict__ rc, int zc,
+             float inv_h2, float dinv, Coef cf) {
+  constexpr int H = V + 1;
+  using TL = Tile<TX, TY, H, NT>;
+  constexpr int WX = TL::WX, K = TL::K, PLANE = TL::PLANE, PAD = TL::PAD;
+  static_assert(NT == (TX / 2) * (TY / 2), "one coarse output per thread");
+  extern __shared__ float sm[];
+  // plane(s, b): s = 0..V-1 holds e_{s+1}, s = V holds the z-weighted residual
+  auto plane = [&](int s, int b) -> float* { return sm + (s * 2 + b) * PLANE + PAD; };
+
+  const int tid = threadIdx.x;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * zc;
+  const int zend = min(z0 + zc, d.nz);
+  const long long pst = (long long)d.nx * d.ny;
+  Positions<TX, TY, H, NT> P;
+  P.init(d, x0, y0);
+  const Dims dc{d.nx / 2, d.ny / 2, d.nz / 2};
+  const int ccx = tid % (TX / 2), ccy = tid / (TX / 2);
+  const int cX = x0 / 2 + ccx, cY = y0 / 2 + ccy;
+  const bool cvalid = cX < dc.nx && cY < dc.ny;
+  const int cp = (H + 2 * ccy) * WX + H + 2 * ccx;
+
+  float rq[V + 1][K];              // rq[j][k] = r at plane t - j
+  float wp[V + 2][K], wc[V + 2][K];  // stage s input window: planes p-1, p
+  float dh[V + 1][K];              // d_{s-1} at stage s's plane
+  float rsp[K], rsc[K];            // residual window
+  float rnext[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+#pragma unroll
+    for (int j = 0; j <= V; ++j) rq[j][k] = 0.f, dh[j][k] = 0.f;
+#pragma unroll
+    for (int s = 0; s < V + 2; ++s) wp[s][k] = 0.f, wc[s][k] = 0.f;
+    rsp[k] = rsc[k] = 0.f;
+  }
+  const int tb = z0 - H, te = zend + V;
+  {
+    const long long base = (long long)wrapmod(tb, d.nz) * pst;
+#pragma unroll
+    for (int k = 0; k < K; ++k) rnext[k] = (P.vmask >> k & 1u) ? __ldg(r + base + P.goff[k]) : 0.f;
+  }
+  for (int t = tb; t <= te; ++t) {
+    const int cur = (t - tb) & 1, prv = cur ^ 1;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+#pragma unroll
+      for (int j = V; j > 0; --j) rq[j][k] = rq[j - 1][k];
+      rq[0][k] = rnext[k];
+    }
+    if (t < te) {
+      const long long base = (long long)wrapmod(t + 1, d.nz) * pst;
+#pragma unroll
+      for (int k = 0; k < K; ++k) rnext[k] = (P.vmask >> k & 1u) ? __ldg(r + base + P.goff[k]) : 0.f;
+    }
+    float en[V + 1][K], dn[V + 1][K];
+    // stage 1 (pointwise, e starts at zero): e_1 = d_1 = c2_0 D^-1 r
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      float dd = 0.f;
+      en[1][k] = cheb_step(0.f, rq[0][k], dd, dinv, cf.c1[0], cf.c2[0]);
+      dn[1][k] = dd;
+      if (P.vmask >> k & 1u) plane(0, cur)[tid + k * NT] = en[1][k];
+    }
+    // stages 2..V: Chebyshev steps with the stencil on e_{s-1}
+#pragma unroll
+    for (int s = 2; s <= V; ++s) {
+      const float* src = plane(s - 2, prv);
+      float* dst = plane(s - 1, cur);
+      const int zp = t - s + 1;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int p = (P.vmask >> k & 1u) ? tid + k * NT : 0;  // invalid slots read in bounds
+        const float c = wc[s][k];
+        const float res = resid_from_sum(rq[s - 1][k],
+                                         nbr_sum(src[p - 1], src[p + 1], src[p - WX], src[p + WX], wp[s][k], en[s - 1][k]),
+                                         c, inv_h2);
+        float dd = dh[s][k];
+        en[s][k] = cheb_step(c, res, dd, dinv, cf.c1[s - 1], cf.c2[s - 1]);
+        dn[s][k] = dd;
+        if (P.vmask >> k & 1u) dst[p] = en[s][k];
+        if (s == V && (P.tmask >> k & 1u) && zp >= z0 && zp < zend) e_out[(long long)zp * pst + P.goff[k]] = en[s][k];
+      }
+    }
+    if (V == 1) {
+      const int zp = t;
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        if ((P.tmask >> k & 1u) && zp >= z0 && zp < zend) e_out[(long long)zp * pst + P.goff[k]] = en[1][k];
+    }
+    // residual stage at plane t - V, then z weights of the restriction at c = t - V - 1
+    {
+      const float* src = plane(V - 1, prv);
+      float* zsd = plane(V, cur);
+      const int c = t - V - 1;
+      const bool cz = ((c & 1) == 0) && c >= z0 && c < zend;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int p = (P.vmask >> k & 1u) ? tid + k * NT : 0;  // invalid slots read in bounds
+        const float rn = resid_from_sum(rq[V][k],
+                                        nbr_sum(src[p - 1], src[p + 1], src[p - WX], src[p + WX], wp[V + 1][k], en[V][k]),
+                                        wc[V + 1][k], inv_h2);
+        if (cz && (P.vmask >> k & 1u)) zsd[p] = fw3(rsp[k], rsc[k], rn);
+        rsp[k] = rsc[k];
+        rsc[k] = rn;
+      }
+    }
+    // coarse output from the z-weighted plane of the previous iteration
+    {
+      const int c = t - V - 2;
+      if (((c & 1) == 0) && c >= z0 && c < zend && cvalid) {
+        const float* zs = plane(V, prv);
+        float yv[3];
+#pragma unroll
+        for (int a = -1; a <= 1; ++a) yv[a + 1] = fw3(zs[cp + a - WX], zs[cp + a], zs[cp + a + WX]);
+        rc[((long long)(c >> 1) * dc.ny + cY) * dc.nx + cX] = fw3(yv[0], yv[1], yv[2]);
+      }
+    }
+    // advance the z windows
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+#pragma unroll
+      for (int s = 2; s <= V + 1; ++s) {
+        wp[s][k] = wc[s][k];
+        wc[s][k] = en[s - 1][k];
+      }
+#pragma unroll
+      for (int s = 2; s <= V; ++s) dh[s][k] = dn[s - 1][k];
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ up leg
+
+template <int V, int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT, 1)
+k_up_fused(Dims d, const float* __restrict__ e_in, const float* __restrict__ ec, const float* __restrict__ r,
+           float* __restrict__ e_out, int zc, float inv_h2, float dinv, Coef cf) {
+  constexpr int H = V;
+  using TL = Tile<TX, TY, H, NT>;
+  constexpr int WX = TL::WX, K = TL::K, PLANE = TL::PLANE, PAD = TL::PAD;
+  extern __shared__ float sm[];
+  // plane(s, b): e_s for s = 0..V-1 (e_0 = e + P e_c)
+  auto plane = [&](int s, int b) -> float* { return sm + (s * 2 + b) * PLANE + PAD; };
+
+  const int tid = threadIdx.x;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * zc;
+  const int zend = min(z0 + zc, d.nz);
+  const long long pst = (long long)d.nx * d.ny;
+  const Dims dc{d.nx / 2, d.ny / 2, d.nz / 2};
+  Positions<TX, TY, H, NT> P;
+  P.init(d, x0, y0);
+  int gx[K], gy[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    gx[k] = P.goff[k] % d.nx;
+    gy[k] = P.goff[k] / d.nx;
+  }
+
+  float rq[V + 1][K];
+  float wp[V + 1][K], wc[V + 1][K];
+  float dh[V + 1][K];
+  float rnext[K], enext[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+#pragma unroll
+    for (int j = 0; j <= V; ++j) rq[j][k] = 0.f, dh[j][k] = 0.f, wp[j][k] = 0.f, wc[j][k] = 0.f;
+  }
+  const int tb = z0 - V, te = zend + V - 1;
+  auto load = [&](int t) {
+    const long long base = (long long)wrapmod(t, d.nz) * pst;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const bool v = P.vmask >> k & 1u;
+      rnext[k] = v ? __ldg(r + base + P.goff[k]) : 0.f;
+      enext[k] = v ? __ldg(e_in + base + P.goff[k]) : 0.f;
+    }
+  };
+  load(tb);
+  for (int t = tb; t <= te; ++t) {
+    const int cur = (t - tb) & 1, prv = cur ^ 1;
+    float en[V + 1][K], dn[V + 1][K];
+    const int tz = wrapmod(t, d.nz);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+#pragma unroll
+      for (int j = V; j > 0; --j) rq[j][k] = rq[j - 1][k];
+      rq[0][k] = rnext[k];
+      en[0][k] = enext[k];
+    }
+    if (t < te) load(t + 1);
+    // stage 0: e_0 = e + P e_c (pointwise)
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (P.vmask >> k & 1u) {
+        en[0][k] = t_add(en[0][k], prolong_value(ec, dc, gx[k], gy[k], tz));
+        plane(0, cur)[tid + k * NT] = en[0][k];
+      }
+    }
+    // stages 1..V: Chebyshev post-smoothing steps at plane t - s
+#pragma unroll
+    for (int s = 1; s <= V; ++s) {
+      const float* src = plane(s - 1, prv);
+      const int zp = t - s;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int p = (P.vmask >> k & 1u) ? tid + k * NT : 0;  // invalid slots read in bounds
+        const float c = wc[s][k];
+        const float res = resid_from_sum(rq[s][k],
+                                         nbr_sum(src[p - 1], src[p + 1], src[p - WX], src[p + WX], wp[s][k], en[s - 1][k]),
+                                         c, inv_h2);
+        float dd = s == 1 ? 0.f : dh[s][k];
+        en[s][k] = cheb_step(c, res, dd, dinv, cf.c1[s - 1], cf.c2[s - 1]);
+        dn[s][k] = dd;
+        if (s < V) {
+          if (P.vmask >> k & 1u) plane(s, cur)[p] = en[s][k];
+        } else if ((P.tmask >> k & 1u) && zp >= z0 && zp < zend) {
+          e_out[(long long)zp * pst + P.goff[k]] = en[s][k];
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+#pragma unroll
+      for (int s = 1; s <= V; ++s) {
+        wp[s][k] = wc[s][k];
+        wc[s][k] = en[s - 1][k];
+      }
+#pragma unroll
+      for (int s = 2; s <= V; ++s) dh[s][k] = dn[s - 1][k];
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ finest level, double-float
+
+// phi' = phi + e (double-float) on the tile plus a one-cell halo, then
+// r' = F - m - A phi' on the tile; block partial sums of r'^2 and of phi'.
+template <int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT)
+k_df_update_residual(Dims d, const float2* __restrict__ phi_in, const float* __restrict__ e,
+                     const float2* __restrict__ F, const double* __restrict__ m_dev, float2* __restrict__ phi_out,
+                     float* __restrict__ r_out, double* __restrict__ pr2, double* __restrict__ psum, int zc) {
+  constexpr int H = 1;
+  using TL = Tile<TX, TY, H, NT>;
+  constexpr int WX = TL::WX, K = TL::K, PLANE = TL::PLANE, PAD = TL::PAD;
+  __shared__ float2 sp[2][PLANE];
+  __shared__ double shr[32];
+  const int tid = threadIdx.x;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * zc;
+  const int zend = min(z0 + zc, d.nz);
+  const long long pst = (long long)d.nx * d.ny;
+  Positions<TX, TY, H, NT> P;
+  P.init(d, x0, y0);
+  const float2 m = f64_to_df(m_dev[0]);
+  float2 wp[K], wc[K];
+  float r2 = 0.f, ps = 0.f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) wp[k] = wc[k] = make_float2(0.f, 0.f);
+  const int tb = z0 - 1, te = zend;
+  for (int t = tb; t <= te; ++t) {
+    const int cur = (t - tb) & 1, prv = cur ^ 1;
+    const long long base = (long long)wrapmod(t, d.nz) * pst;
+    float2 pn[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      pn[k] = make_float2(0.f, 0.f);
+      if (P.vmask >> k & 1u) {
+        const long long gi = base + P.goff[k];
+        pn[k] = df_add_f(phi_in[gi], __ldg(e + gi));
+        sp[cur][PAD + tid + k * NT] = pn[k];
+        if ((P.tmask >> k & 1u) && t >= z0 && t < zend) {
+          phi_out[gi] = pn[k];
+          ps += pn[k].x;
+        }
+      }
+    }
+    const int zp = t - 1;
+    if (zp >= z0 && zp < zend) {
+      const float2* src = sp[prv] + PAD;
+      const long long pbase = (long long)zp * pst;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        if (P.tmask >> k & 1u) {
+          const int p = (P.vmask >> k & 1u) ? tid + k * NT : 0;  // invalid slots read in bounds
+          const long long gi = pbase + P.goff[k];
+          const float rv = df_resid(wc[k], src[p - 1], src[p + 1], src[p - WX], src[p + WX], wp[k], pn[k], F[gi], m);
+          r_out[gi] = rv;
+          r2 += rv * rv;
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      wp[k] = wc[k];
+      wc[k] = pn[k];
+    }
+    __syncthreads();
+  }
+  const double b2 = block_sum_f(r2, shr);
+  const double bs = block_sum_f(ps, shr);
+  if (tid == 0) {
+    const int bid = block_linear_id();
+    pr2[bid] = b2;
+    psum[bid] = bs;
+  }
+}
+
+constexpr int DTX = 64, DTY = 32, DNT = 512;   // down-leg tile
+constexpr int UTX = 64, UTY = 32, UNT = 512;   // up-leg tile
+constexpr int FTX = 64, FTY = 16, FNT = 256;   // double-float update tile
+
+template <int V>
+size_t down_smem() {
+  return (size_t)(V + 1) * 2 * Tile<DTX, DTY, V + 1, DNT>::PLANE * sizeof(float);
+}
+template <int V>
+size_t up_smem() {
+  return (size_t)V * 2 * Tile<UTX, UTY, V, UNT>::PLANE * sizeof(float);
+}
+
+Coef make_coef(const double* c1, const double* c2, int v) {
+  Coef cf{};
+  for (int i = 0; i < v && i < 16; ++i) {
+    cf.c1[i] = (float)c1[i];
+    cf.c2[i] = (float)c2[i];
+  }
+  return cf;
+}
+
+template <int V>
+cudaError_t down_v(cudaStream_t st, Dims d, const float* r, float* e, float* rc, int zc, float ih2, float dinv,
+                   const Coef& cf) {
+  static bool attr = false;
+  const size_t sm = down_smem<V>();
+  if (!attr) {
+    cudaError_t err = cudaFuncSetAttribute(k_down_fused<V, DTX, DTY, DNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (err != cudaSuccess) return err;
+    attr = true;
+  }
+  const dim3 grid((d.nx + DTX - 1) / DTX, (d.ny + DTY - 1) / DTY, (d.nz + zc - 1) / zc);
+  k_down_fused<V, DTX, DTY, DNT><<<grid, DNT, sm, st>>>(d, r, e, rc, zc, ih2, dinv, cf);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <int V>
+cudaError_t up_v(cudaStream_t st, Dims d, const float* e_in, const float* ec, const float* r, float* e_out, int zc,
+                 float ih2, float dinv, const Coef& cf) {
+  static bool attr = false;
+  const size_t sm = up_smem<V>();
+  if (!attr) {
+    cudaError_t err = cudaFuncSetAttribute(k_up_fused<V, UTX, UTY, UNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (err != cudaSuccess) return err;
+    attr = true;
+  }
+  const dim3 grid((d.nx + UTX - 1) / UTX, (d.ny + UTY - 1) / UTY, (d.nz + zc - 1) / zc);
+  k_up_fused<V, UTX, UTY, UNT><<<grid, UNT, sm, st>>>(d, e_in, ec, r, e_out, zc, ih2, dinv, cf);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool fused_degree_supported(int degree) { return degree >= 1 && degree <= 4; }
+
+int fused_zchunk(Dims d) {
+  // z chunk: enough CTAs to fill the GPU several times while keeping the
+  // redundant warm-up planes of each chunk small.
+  const long long tiles = (long long)((d.nx + DTX - 1) / DTX) * ((d.ny + DTY - 1) / DTY);
+  int zc = d.nz;
+  while (zc > 16 && tiles * ((d.nz + zc - 1) / zc) < 4 * 152) zc /= 2;
+  return zc;
+}
+
+cudaError_t launch_down_fused(cudaStream_t st, int degree, Dims d, const float* r, float* e, float* rc, float inv_h2,
+                              float dinv, const double* c1, const double* c2) {
+  const Coef cf = make_coef(c1, c2, degree);
+  const int zc = fused_zchunk(d);
+  switch (degree) {
+    case 1: return down_v<1>(st, d, r, e, rc, zc, inv_h2, dinv, cf);
+    case 2: return down_v<2>(st, d, r, e, rc, zc, inv_h2, dinv, cf);
+    case 3: return down_v<3>(st, d, r, e, rc, zc, inv_h2, dinv, cf);
+    case 4: return down_v<4>(st, d, r, e, rc, zc, inv_h2, dinv, cf);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_up_fused(cudaStream_t st, int degree, Dims d, const float* e_in, const float* ec, const float* r,
+                            float* e_out, float inv_h2, float dinv, const double* c1, const double* c2) {
+  const Coef cf = make_coef(c1, c2, degree);
+  const int zc = fused_zchunk(d);
+  switch (degree) {
+    case 1: return up_v<1>(st, d, e_in, ec, r, e_out, zc, inv_h2, dinv, cf);
+    case 2: return up_v<2>(st, d, e_in, ec, r, e_out, zc, inv_h2, dinv, cf);
+    case 3: return up_v<3>(st, d, e_in, ec, r, e_out, zc, inv_h2, dinv, cf);
+    case 4: return up_v<4>(st, d, e_in, ec, r, e_out, zc, inv_h2, dinv, cf);
+  }
+  return cudaErrorInvalidValue;
+}
+
+long long df_update_residual_partials(Dims d) {
+  const int zc = fused_zchunk(d);
+  return (long long)((d.nx + FTX - 1) / FTX) * ((d.ny + FTY - 1) / FTY) * ((d.nz + zc - 1) / zc);
+}
+
+cudaError_t launch_df_update_residual(cudaStream_t st, Dims d, const float2* phi_in, const float* e, const float2* F,
+                                      const double* m_dev, float2* phi_out, float* r_out, double* pr2, double* psum) {
+  const int zc = fused_zchunk(d);
+  const dim3 grid((d.nx + FTX - 1) / FTX, (d.ny + FTY - 1) / FTY, (d.nz + zc - 1) / zc);
+  k_df_update_residual<FTX, FTY, FNT><<<grid, FNT, 0, st>>>(d, phi_in, e, F, m_dev, phi_out, r_out, pr2, psum, zc);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace gbmg

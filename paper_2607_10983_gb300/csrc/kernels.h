@@ -1,0 +1,74 @@
+// Launch functions of the multigrid kernels (host-callable, internal to the library).
+// Each queues one kernel on `st` and returns the launch status.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace gbmg {
+
+// Counts kernel launches made by this library (process-wide, for measurement).
+void note_launch();
+long long launch_count();
+
+// Number of per-block partial sums a reduction-producing launch writes for a level.
+long long partial_count(Dims d);
+
+// ---- one kernel per operation, T = float or double (flat 7-point operator) ----
+template <typename T>
+cudaError_t launch_apply(cudaStream_t st, Dims d, const T* u, T* out, T inv_h2);
+template <typename T>
+cudaError_t launch_residual(cudaStream_t st, Dims d, const T* f, const T* u, T* out, T inv_h2,
+                            double* partials_sq);
+template <typename T>
+cudaError_t launch_cheb_step(cudaStream_t st, Dims d, const T* r, const T* e_in, T* e_out, T* dvec,
+                             T inv_h2, T dinv, T c1, T c2);
+template <typename T>
+cudaError_t launch_jacobi(cudaStream_t st, Dims d, const T* r, const T* e_in, T* e_out, T inv_h2,
+                          T w_dinv);
+template <typename T>
+cudaError_t launch_restrict(cudaStream_t st, Dims fine, const T* f, T* c);
+template <typename T>
+cudaError_t launch_prolong_add(cudaStream_t st, Dims coarse, const T* c, T* f);
+template <typename T>
+cudaError_t launch_coarse_matvec(cudaStream_t st, int n, const T* G, const T* r, T* e);
+template <typename T>
+cudaError_t launch_sum(cudaStream_t st, long long n, const T* x, double* partials_sum,
+                       double* partials_sq);
+template <typename T>
+cudaError_t launch_shift(cudaStream_t st, long long n, const T* x, const double* shift_dev, T* out);
+
+// out[0] = scale * (sum of `count` partials), summed in a fixed order (one block).
+cudaError_t launch_finalize(cudaStream_t st, const double* partials, long long count, double* out, double scale);
+
+// ---- double-float path (finest level, h = 1) ----
+cudaError_t launch_f64_to_df(cudaStream_t st, long long n, const double* x, float2* out,
+                             double* partials_sum);
+cudaError_t launch_df_to_f64(cudaStream_t st, long long n, const float2* in, const double* shift_dev,
+                             double* out);
+cudaError_t launch_df_residual(cudaStream_t st, Dims d, const float2* F, const double* m_dev,
+                               const float2* phi, float* r, double* partials_r2,
+                               double* partials_f2);
+// phi += e (e NULL: phi unchanged); partials_sum (nullable) gets the block sums of phi.
+cudaError_t launch_df_update(cudaStream_t st, long long n, float2* phi, const float* e,
+                             double* partials_sum);
+long long df_partial_count(long long n);
+
+// ---- temporally blocked FP32 level kernels (Chebyshev smoother) ----
+bool fused_degree_supported(int degree);
+int fused_zchunk(Dims d);
+// e = Chebyshev pre-smoothing of A e = r from e = 0; rc = R (r - A e) on the next level.
+cudaError_t launch_down_fused(cudaStream_t st, int degree, Dims d, const float* r, float* e, float* rc,
+                              float inv_h2, float dinv, const double* c1, const double* c2);
+// e_out = Chebyshev post-smoothing of A e = r starting from e_in + P ec.
+cudaError_t launch_up_fused(cudaStream_t st, int degree, Dims d, const float* e_in, const float* ec,
+                            const float* r, float* e_out, float inv_h2, float dinv, const double* c1,
+                            const double* c2);
+// Finest level: phi_out = phi_in + e (double-float), r_out = F - m - A phi_out, with block partials
+// of ||r_out||^2 and sum(phi_out) (df_update_residual_partials(d) of each).
+long long df_update_residual_partials(Dims d);
+cudaError_t launch_df_update_residual(cudaStream_t st, Dims d, const float2* phi_in, const float* e,
+                                      const float2* F, const double* m_dev, float2* phi_out, float* r_out,
+                                      double* partials_r2, double* partials_sum);
+
+}  // namespace gbmg

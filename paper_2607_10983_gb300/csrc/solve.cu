@@ -1,0 +1,496 @@
+// V-cycle level loop, solve drivers and the component entry points of the C ABI.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "kernels.h"
+#include "solver.h"
+
+using namespace gbmg;
+
+#define TRY(call)                                  \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+#define TRYS(call)                  \
+  do {                              \
+    gbmg_status s_ = (call);        \
+    if (s_ != GBMG_OK) return s_;   \
+  } while (0)
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+// Brackets one launch with CUDA events on the context's stream when its kernel
+// family is being timed (mg_profile_begin); no effect otherwise.
+struct ProfScope {
+  gbmg_ctx* c;
+  int f;
+  bool on = false;
+  ProfScope(gbmg_ctx* ctx, int family) : c(ctx), f(family) {
+    if (family <= GBMG_PROF_OFF || family > 7 || !(c->prof_mask >> family & 1)) return;
+    std::vector<cudaEvent_t>& ev = c->prof_ev[f];
+    const size_t need = 2 * (size_t)c->prof_n[f] + 2;
+    while (ev.size() < need) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return;
+      ev.push_back(e);
+    }
+    on = cudaEventRecord(ev[2 * c->prof_n[f]], c->stream) == cudaSuccess;
+  }
+  ~ProfScope() {
+    if (on && cudaEventRecord(c->prof_ev[f][2 * c->prof_n[f] + 1], c->stream) == cudaSuccess) c->prof_n[f] += 1;
+  }
+};
+
+template <typename T>
+const T* coarse_G(const gbmg_ctx* c);
+template <>
+const float* coarse_G<float>(const gbmg_ctx* c) { return c->G32; }
+template <>
+const double* coarse_G<double>(const gbmg_ctx* c) { return c->G64; }
+
+// One smoothing pass on level l (pre: nu1 Jacobi sweeps, post: nu2), one kernel per
+// step, ping-ponging e and eo.
+template <typename T>
+gbmg_status smooth_pass(gbmg_ctx* c, int l, T*& e, T*& eo, const T* r, T* dv, bool post) {
+  const Level& L = c->lv[l];
+  const T inv_h2 = (T)(1.0 / (L.h * L.h));
+  const double dinv = -(L.h * L.h) / 6.0;
+  if (c->o.smoother == GBMG_SMOOTH_CHEBYSHEV) {
+    for (int k = 0; k < c->o.degree; ++k) {
+      ProfScope ps(c, l == 0 ? GBMG_PROF_SMOOTH0 : GBMG_PROF_OFF);
+      TRY(launch_cheb_step<T>(c->stream, L.d, r, e, eo, dv, inv_h2, (T)dinv, (T)c->cc1[k], (T)c->cc2[k]));
+      std::swap(e, eo);
+    }
+  } else {
+    const int nu = post ? c->o.nu2 : c->o.nu1;
+    const T wd = (T)(c->o.omega * dinv);
+    for (int k = 0; k < nu; ++k) {
+      TRY(launch_jacobi<T>(c->stream, L.d, r, e, eo, inv_h2, wd));
+      std::swap(e, eo);
+    }
+  }
+  return GBMG_OK;
+}
+
+// V-cycle (Sec. 2.3) on level l for A_l e = r, one kernel per operation.  e / eo are
+// the level's ping-pong buffers; on return e points at the result.
+template <typename T>
+gbmg_status vcycle_unfused(gbmg_ctx* c, int l, T*& e, T*& eo, const T* r) {
+  const Level& L = c->lv[l];
+  if (l == c->L - 1) {
+    TRY(launch_coarse_matvec<T>(c->stream, c->nc, coarse_G<T>(c), r, e));
+    return GBMG_OK;
+  }
+  T* dv = (T*)L.dv;
+  TRYS(smooth_pass<T>(c, l, e, eo, r, dv, false));
+  const T inv_h2 = (T)(1.0 / (L.h * L.h));
+  TRY(launch_residual<T>(c->stream, L.d, r, e, (T*)L.t, inv_h2, nullptr));
+  const Level& C = c->lv[l + 1];
+  TRY(launch_restrict<T>(c->stream, L.d, (const T*)L.t, (T*)C.r));
+  T* ce = (T*)C.e;
+  T* ceo = (T*)C.e2;
+  if (l + 1 < c->L - 1) TRY(cudaMemsetAsync(ce, 0, (size_t)ncell(C.d) * sizeof(T), c->stream));
+  TRYS(vcycle_unfused<T>(c, l + 1, ce, ceo, (const T*)C.r));
+  TRY(launch_prolong_add<T>(c->stream, C.d, ce, e));
+  TRYS(smooth_pass<T>(c, l, e, eo, r, dv, true));
+  return GBMG_OK;
+}
+
+// Levels at least this large in every direction use the temporally blocked kernels.
+bool level_fused(const gbmg_ctx* c, int l) {
+  const Dims d = c->lv[l].d;
+  return c->o.fused && l < c->L - 1 && d.nx >= 16 && d.ny >= 16 && d.nz >= 16;
+}
+
+// V-cycle in FP32 with the temporally blocked kernels on large levels (one launch per
+// level visit on each leg) and the one-kernel-per-operation path below them.  e
+// receives the pointer to the level's correction.
+gbmg_status vcycle_fused(gbmg_ctx* c, int l, float*& e, const float* r) {
+  const Level& L = c->lv[l];
+  if (!level_fused(c, l)) {
+    float* ee = (float*)L.e;
+    float* eo = (float*)L.e2;
+    if (l < c->L - 1) TRY(cudaMemsetAsync(ee, 0, (size_t)ncell(L.d) * sizeof(float), c->stream));
+    TRYS(vcycle_unfused<float>(c, l, ee, eo, r));
+    e = ee;
+    return GBMG_OK;
+  }
+  const float ih2 = (float)(1.0 / (L.h * L.h));
+  const float dinv = (float)(-(L.h * L.h) / 6.0);
+  const Level& C = c->lv[l + 1];
+  {
+    ProfScope ps(c, l == 0 ? GBMG_PROF_DOWN0 : GBMG_PROF_OFF);
+    TRY(launch_down_fused(c->stream, c->o.degree, L.d, r, (float*)L.e, (float*)C.r, ih2, dinv, c->cc1.data(),
+                          c->cc2.data()));
+  }
+  float* ce = nullptr;
+  TRYS(vcycle_fused(c, l + 1, ce, (const float*)C.r));
+  {
+    ProfScope ps(c, l == 0 ? GBMG_PROF_UP0 : GBMG_PROF_OFF);
+    TRY(launch_up_fused(c->stream, c->o.degree, L.d, (const float*)L.e, ce, r, (float*)L.e2, ih2, dinv,
+                        c->cc1.data(), c->cc2.data()));
+  }
+  e = (float*)L.e2;
+  return GBMG_OK;
+}
+
+// Reads ||F||^2 and ||r||^2 back and returns the relative residual.
+gbmg_status read_rel(gbmg_ctx* c, double& rel) {
+  TRY(cudaMemcpyAsync(c->host_scal, c->scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  TRY(cudaStreamSynchronize(c->stream));
+  const double f2 = c->host_scal[S_F2], r2 = c->host_scal[S_R2];
+  rel = f2 > 0.0 ? std::sqrt(r2 / f2) : std::sqrt(r2);
+  return GBMG_OK;
+}
+
+// Convergence bookkeeping shared by the solve drivers: stop at tol, at max_vcycles,
+// on a non-finite residual, or when the residual grew tenfold over two cycles.
+struct Monitor {
+  gbmg_stats& st;
+  double tol;
+  int maxv;
+  std::vector<double> hist;  // hist[k] = relative residual after k cycles
+  Monitor(gbmg_stats& s, double t, int m) : st(s), tol(t), maxv(m) {}
+  void start(double rel) {
+    st.rel_res0 = rel;
+    st.rel_res = rel;
+    st.cycles = 0;
+    st.status = GBMG_OK;
+    hist.assign(1, rel);
+  }
+  bool done() {
+    if (!std::isfinite(st.rel_res)) {
+      st.status = GBMG_ERR_NONFINITE;
+      return true;
+    }
+    if (st.rel_res <= tol) return true;
+    if (st.cycles >= maxv) {
+      st.status = GBMG_ERR_NOT_CONVERGED;
+      return true;
+    }
+    return false;
+  }
+  // record the residual after one more cycle; true if the solve must stop (diverged)
+  bool record(double rel) {
+    if (st.cycles < 64) st.res_hist[st.cycles] = rel;
+    st.cycles += 1;
+    st.rel_res = rel;
+    hist.push_back(rel);
+    const size_t k = hist.size() - 1;
+    if (k >= 2 && std::isfinite(rel) && rel > 10.0 * hist[k - 2]) {
+      st.status = GBMG_ERR_DIVERGED;
+      return true;
+    }
+    return false;
+  }
+};
+
+gbmg_status solve_fp64(gbmg_ctx* c, const double* F, double* phi, double tol, int maxv, gbmg_stats& st) {
+  const Level& L0 = c->lv[0];
+  const long long n = ncell(L0.d);
+  double* part = c->partials;
+  double* sc = c->scal;
+  const long long pr = df_partial_count(n);
+  TRY(launch_sum<double>(c->stream, n, F, part, nullptr));
+  TRY(launch_finalize(c->stream, part, pr, sc + S_MEAN_F, 1.0 / (double)n));
+  double* f0 = (double*)L0.r;
+  TRY(launch_shift<double>(c->stream, n, F, sc + S_MEAN_F, f0));
+  TRY(launch_sum<double>(c->stream, n, f0, nullptr, part));
+  TRY(launch_finalize(c->stream, part, pr, sc + S_F2, 1.0));
+  double* u = (double*)L0.e;
+  double* uo = (double*)L0.e2;
+  TRY(cudaMemcpyAsync(u, phi, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  auto resnorm = [&]() -> gbmg_status {
+    TRY(launch_residual<double>(c->stream, L0.d, f0, u, (double*)L0.t, 1.0, part));
+    TRY(launch_finalize(c->stream, part, partial_count(L0.d), sc + S_R2, 1.0));
+    return GBMG_OK;
+  };
+  TRYS(resnorm());
+  double rel;
+  TRYS(read_rel(c, rel));
+  Monitor mon(st, tol, maxv);
+  mon.start(rel);
+  while (!mon.done()) {
+    TRYS(vcycle_unfused<double>(c, 0, u, uo, f0));
+    TRYS(resnorm());
+    TRYS(read_rel(c, rel));
+    if (mon.record(rel)) break;
+  }
+  TRY(launch_sum<double>(c->stream, n, u, part, nullptr));
+  TRY(launch_finalize(c->stream, part, pr, sc + S_MEAN_PHI, 1.0 / (double)n));
+  TRY(launch_shift<double>(c->stream, n, u, sc + S_MEAN_PHI, phi));
+  return GBMG_OK;
+}
+
+gbmg_status solve_mixed(gbmg_ctx* c, const double* F, double* phi, double tol, int maxv, gbmg_stats& st) {
+  const Level& L0 = c->lv[0];
+  const long long n = ncell(L0.d);
+  double* part = c->partials;
+  double* part1 = c->partials + c->npart;
+  double* part2 = c->partials + 2 * c->npart;
+  double* sc = c->scal;
+  const long long pr = df_partial_count(n), pc = partial_count(L0.d);
+  // prologue: F and phi to double-float, mean of F, first residual and ||F - mean||
+  TRY(launch_f64_to_df(c->stream, n, F, c->F_df, part));
+  TRY(launch_finalize(c->stream, part, pr, sc + S_MEAN_F, 1.0 / (double)n));
+  TRY(launch_f64_to_df(c->stream, n, phi, c->phi_df, nullptr));
+  float* r0 = (float*)L0.r;
+  TRY(launch_df_residual(c->stream, L0.d, c->F_df, sc + S_MEAN_F, c->phi_df, r0, part, part1));
+  TRY(launch_finalize(c->stream, part, pc, sc + S_R2, 1.0));
+  TRY(launch_finalize(c->stream, part1, pc, sc + S_F2, 1.0));
+  double rel;
+  TRYS(read_rel(c, rel));
+  Monitor mon(st, tol, maxv);
+  mon.start(rel);
+  float2* phi_cur = c->phi_df;
+  float2* phi_nxt = c->phi_df2;
+  float* r_alt = c->r_alt;
+  const long long pu = df_update_residual_partials(L0.d);
+  bool have_sum = false;
+  while (!mon.done()) {
+    if (c->o.fused) {
+      float* e = nullptr;
+      TRYS(vcycle_fused(c, 0, e, r0));
+      {
+        ProfScope ps(c, GBMG_PROF_DF0);
+        TRY(launch_df_update_residual(c->stream, L0.d, phi_cur, e, c->F_df, sc + S_MEAN_F, phi_nxt, r_alt, part,
+                                      part2));
+      }
+      std::swap(phi_cur, phi_nxt);
+      std::swap(r0, r_alt);
+      TRY(launch_finalize(c->stream, part, pu, sc + S_R2, 1.0));
+      have_sum = true;
+    } else {
+      float* e = (float*)L0.e;
+      float* eo = (float*)L0.e2;
+      TRY(cudaMemsetAsync(e, 0, (size_t)n * sizeof(float), c->stream));
+      TRYS(vcycle_unfused<float>(c, 0, e, eo, r0));
+      TRY(launch_df_update(c->stream, n, phi_cur, e, nullptr));
+      {
+        ProfScope ps(c, GBMG_PROF_DF0);
+        TRY(launch_df_residual(c->stream, L0.d, c->F_df, sc + S_MEAN_F, phi_cur, r0, part, nullptr));
+      }
+      TRY(launch_finalize(c->stream, part, pc, sc + S_R2, 1.0));
+    }
+    TRYS(read_rel(c, rel));
+    if (mon.record(rel)) break;
+  }
+  // epilogue: gauge (remove the mean of phi) and convert back to FP64
+  if (have_sum) {
+    TRY(launch_finalize(c->stream, part2, pu, sc + S_MEAN_PHI, 1.0 / (double)n));
+  } else {
+    TRY(launch_df_update(c->stream, n, phi_cur, nullptr, part2));
+    TRY(launch_finalize(c->stream, part2, pr, sc + S_MEAN_PHI, 1.0 / (double)n));
+  }
+  TRY(launch_df_to_f64(c->stream, n, phi_cur, sc + S_MEAN_PHI, phi));
+  return GBMG_OK;
+}
+
+gbmg_status check_level(const gbmg_ctx* c, int level, int dtype, const char* who) {
+  if (!c) return fail(GBMG_ERR_INVALID_ARG, std::string(who) + ": ctx is NULL");
+  if (level < 0 || level >= c->L) return fail(GBMG_ERR_INVALID_ARG, std::string(who) + ": bad level");
+  if (dtype != GBMG_F32 && dtype != GBMG_F64) return fail(GBMG_ERR_INVALID_ARG, std::string(who) + ": bad dtype");
+  return GBMG_OK;
+}
+
+gbmg_status comp_scratch(gbmg_ctx* c, int dtype, void** out) {
+  if (!c->comp_scratch[dtype]) {
+    const size_t esz = dtype == GBMG_F64 ? 8 : 4;
+    void* p = nullptr;
+    TRY(cudaMalloc(&p, 2 * (size_t)ncell(c->lv[0].d) * esz));
+    c->owned.push_back(p);
+    c->comp_scratch[dtype] = p;
+  }
+  *out = c->comp_scratch[dtype];
+  return GBMG_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ solve
+
+extern "C" gbmg_status mg_solve(gbmg_ctx* ctx, const double* source_dev, const float* coeffs_dev,
+                                double* phi_inout_dev, double tol, int max_vcycles, gbmg_stats* stats) {
+  g_last_error.clear();
+  if (!ctx || !source_dev || !phi_inout_dev) return fail(GBMG_ERR_INVALID_ARG, "mg_solve: NULL argument");
+  if (coeffs_dev) return fail(GBMG_ERR_INVALID_ARG, "mg_solve: coeffs must be NULL for the flat operator");
+  if (!(tol >= 0.0)) return fail(GBMG_ERR_INVALID_ARG, "mg_solve: tol must be >= 0");
+  DeviceGuard g(ctx->device);
+  gbmg_stats st;
+  std::memset(&st, 0, sizeof(st));
+  gbmg_status s = ctx->o.prec == GBMG_FP64 ? solve_fp64(ctx, source_dev, phi_inout_dev, tol, max_vcycles, st)
+                                           : solve_mixed(ctx, source_dev, phi_inout_dev, tol, max_vcycles, st);
+  if (s != GBMG_OK) return s;
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "mg_solve");
+  ctx->last = st;
+  if (stats) *stats = st;
+  if (st.status != GBMG_OK) {
+    char buf[160];
+    std::snprintf(buf, sizeof(buf), "mg_solve: %s after %d cycles, relative residual %.3e",
+                  mg_status_string((gbmg_status)st.status), st.cycles, st.rel_res);
+    g_last_error = buf;
+  }
+  return (gbmg_status)st.status;
+}
+
+extern "C" gbmg_status mg_solve_host(gbmg_ctx* ctx, const double* source_host, double* phi_inout_host, double tol,
+                                     int max_vcycles, gbmg_stats* stats) {
+  g_last_error.clear();
+  if (!ctx || !source_host || !phi_inout_host) return fail(GBMG_ERR_INVALID_ARG, "mg_solve_host: NULL argument");
+  DeviceGuard g(ctx->device);
+  const size_t bytes = (size_t)ncell(ctx->lv[0].d) * sizeof(double);
+  if (!ctx->stage_F) {
+    TRY(cudaMalloc((void**)&ctx->stage_F, bytes));
+    ctx->owned.push_back(ctx->stage_F);
+    TRY(cudaMalloc((void**)&ctx->stage_phi, bytes));
+    ctx->owned.push_back(ctx->stage_phi);
+  }
+  TRY(cudaMemcpyAsync(ctx->stage_F, source_host, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  TRY(cudaMemcpyAsync(ctx->stage_phi, phi_inout_host, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  const gbmg_status s = mg_solve(ctx, ctx->stage_F, nullptr, ctx->stage_phi, tol, max_vcycles, stats);
+  if (s != GBMG_OK && s != GBMG_ERR_NOT_CONVERGED && s != GBMG_ERR_NONFINITE && s != GBMG_ERR_DIVERGED) return s;
+  TRY(cudaMemcpyAsync(phi_inout_host, ctx->stage_phi, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  TRY(cudaStreamSynchronize(ctx->stream));
+  return s;
+}
+
+// ------------------------------------------------------------------ components
+
+extern "C" gbmg_status mg_apply(gbmg_ctx* c, int level, int dtype, const void* u, void* out) {
+  TRYS(check_level(c, level, dtype, "mg_apply"));
+  if (!u || !out) return fail(GBMG_ERR_INVALID_ARG, "mg_apply: NULL buffer");
+  DeviceGuard g(c->device);
+  const Level& L = c->lv[level];
+  const double ih2 = 1.0 / (L.h * L.h);
+  if (dtype == GBMG_F64) TRY(launch_apply<double>(c->stream, L.d, (const double*)u, (double*)out, ih2));
+  else TRY(launch_apply<float>(c->stream, L.d, (const float*)u, (float*)out, (float)ih2));
+  return GBMG_OK;
+}
+
+extern "C" gbmg_status mg_residual(gbmg_ctx* c, int level, int dtype, const void* f, const void* u, void* out) {
+  TRYS(check_level(c, level, dtype, "mg_residual"));
+  if (!f || !u || !out) return fail(GBMG_ERR_INVALID_ARG, "mg_residual: NULL buffer");
+  DeviceGuard g(c->device);
+  const Level& L = c->lv[level];
+  const double ih2 = 1.0 / (L.h * L.h);
+  if (dtype == GBMG_F64)
+    TRY(launch_residual<double>(c->stream, L.d, (const double*)f, (const double*)u, (double*)out, ih2, nullptr));
+  else
+    TRY(launch_residual<float>(c->stream, L.d, (const float*)f, (const float*)u, (float*)out, (float)ih2, nullptr));
+  return GBMG_OK;
+}
+
+template <typename T>
+static gbmg_status smooth_component(gbmg_ctx* c, int level, int dtype, T* e_io, const T* r) {
+  void* s = nullptr;
+  TRYS(comp_scratch(c, dtype, &s));
+  T* eo = (T*)s;
+  T* dv = eo + ncell(c->lv[0].d);
+  T* e = e_io;
+  TRYS(smooth_pass<T>(c, level, e, eo, r, dv, false));
+  if (e != e_io)
+    TRY(cudaMemcpyAsync(e_io, e, (size_t)ncell(c->lv[level].d) * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
+  return GBMG_OK;
+}
+
+extern "C" gbmg_status mg_smooth(gbmg_ctx* c, int level, int dtype, void* e, const void* r) {
+  TRYS(check_level(c, level, dtype, "mg_smooth"));
+  if (!e || !r) return fail(GBMG_ERR_INVALID_ARG, "mg_smooth: NULL buffer");
+  DeviceGuard g(c->device);
+  if (dtype == GBMG_F64) return smooth_component<double>(c, level, dtype, (double*)e, (const double*)r);
+  return smooth_component<float>(c, level, dtype, (float*)e, (const float*)r);
+}
+
+extern "C" gbmg_status mg_restrict(gbmg_ctx* c, int level, int dtype, const void* fine, void* coarse) {
+  TRYS(check_level(c, level, dtype, "mg_restrict"));
+  if (level + 1 >= c->L) return fail(GBMG_ERR_INVALID_ARG, "mg_restrict: level has no coarser level");
+  if (!fine || !coarse) return fail(GBMG_ERR_INVALID_ARG, "mg_restrict: NULL buffer");
+  DeviceGuard g(c->device);
+  if (dtype == GBMG_F64) TRY(launch_restrict<double>(c->stream, c->lv[level].d, (const double*)fine, (double*)coarse));
+  else TRY(launch_restrict<float>(c->stream, c->lv[level].d, (const float*)fine, (float*)coarse));
+  return GBMG_OK;
+}
+
+extern "C" gbmg_status mg_prolong_add(gbmg_ctx* c, int level, int dtype, const void* coarse, void* fine) {
+  TRYS(check_level(c, level, dtype, "mg_prolong_add"));
+  if (level + 1 >= c->L) return fail(GBMG_ERR_INVALID_ARG, "mg_prolong_add: level has no coarser level");
+  if (!fine || !coarse) return fail(GBMG_ERR_INVALID_ARG, "mg_prolong_add: NULL buffer");
+  DeviceGuard g(c->device);
+  const Dims dc = c->lv[level + 1].d;
+  if (dtype == GBMG_F64) TRY(launch_prolong_add<double>(c->stream, dc, (const double*)coarse, (double*)fine));
+  else TRY(launch_prolong_add<float>(c->stream, dc, (const float*)coarse, (float*)fine));
+  return GBMG_OK;
+}
+
+extern "C" gbmg_status mg_coarse_solve(gbmg_ctx* c, int dtype, const void* r, void* e) {
+  TRYS(check_level(c, 0, dtype, "mg_coarse_solve"));
+  if (!r || !e) return fail(GBMG_ERR_INVALID_ARG, "mg_coarse_solve: NULL buffer");
+  DeviceGuard g(c->device);
+  if (dtype == GBMG_F64) TRY(launch_coarse_matvec<double>(c->stream, c->nc, c->G64, (const double*)r, (double*)e));
+  else TRY(launch_coarse_matvec<float>(c->stream, c->nc, c->G32, (const float*)r, (float*)e));
+  return GBMG_OK;
+}
+
+extern "C" gbmg_status mg_vcycle(gbmg_ctx* c, const void* r, void* e_out) {
+  if (!c || !r || !e_out) return fail(GBMG_ERR_INVALID_ARG, "mg_vcycle: NULL argument");
+  DeviceGuard g(c->device);
+  const Level& L0 = c->lv[0];
+  const long long n = ncell(L0.d);
+  if (c->o.prec == GBMG_FP64) {
+    double* e = (double*)L0.e;
+    double* eo = (double*)L0.e2;
+    TRY(cudaMemsetAsync(e, 0, (size_t)n * 8, c->stream));
+    TRYS(vcycle_unfused<double>(c, 0, e, eo, (const double*)r));
+    TRY(cudaMemcpyAsync(e_out, e, (size_t)n * 8, cudaMemcpyDeviceToDevice, c->stream));
+  } else {
+    float* e = (float*)L0.e;
+    if (c->o.fused) {
+      TRYS(vcycle_fused(c, 0, e, (const float*)r));
+    } else {
+      float* eo = (float*)L0.e2;
+      TRY(cudaMemsetAsync(e, 0, (size_t)n * 4, c->stream));
+      TRYS(vcycle_unfused<float>(c, 0, e, eo, (const float*)r));
+    }
+    TRY(cudaMemcpyAsync(e_out, e, (size_t)n * 4, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  return GBMG_OK;
+}
+
+extern "C" gbmg_status mg_f64_to_df(gbmg_ctx* c, long long n, const double* x, float* df) {
+  if (!c || !x || !df || n < 0) return fail(GBMG_ERR_INVALID_ARG, "mg_f64_to_df: bad argument");
+  DeviceGuard g(c->device);
+  TRY(launch_f64_to_df(c->stream, n, x, (float2*)df, nullptr));
+  return GBMG_OK;
+}
+
+extern "C" gbmg_status mg_df_to_f64(gbmg_ctx* c, long long n, const float* df, double* x) {
+  if (!c || !x || !df || n < 0) return fail(GBMG_ERR_INVALID_ARG, "mg_df_to_f64: bad argument");
+  DeviceGuard g(c->device);
+  TRY(launch_df_to_f64(c->stream, n, (const float2*)df, nullptr, x));
+  return GBMG_OK;
+}
+
+extern "C" gbmg_status mg_df_residual(gbmg_ctx* c, const float* F, double m, const float* phi, float* r) {
+  if (!c || !F || !phi || !r) return fail(GBMG_ERR_INVALID_ARG, "mg_df_residual: NULL argument");
+  DeviceGuard g(c->device);
+  double* slot = c->scal + S_USER;
+  TRY(cudaStreamSynchronize(c->stream));
+  TRY(cudaMemcpy(slot, &m, sizeof(double), cudaMemcpyHostToDevice));
+  TRY(launch_df_residual(c->stream, c->lv[0].d, (const float2*)F, slot, (const float2*)phi, r, nullptr, nullptr));
+  return GBMG_OK;
+}

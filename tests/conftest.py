@@ -16,3 +16,29 @@ def pytest_configure(config):
 @pytest.fixture(scope="session")
 def golden_dir():
     return os.path.join(ROOT, "tests", "golden")
+
+
+def pytest_collection_modifyitems(config, items):
+    try:
+        import torch
+        has_gpu = torch.cuda.is_available()
+    except Exception:
+        has_gpu = False
+    if has_gpu:
+        return
+    skip = pytest.mark.skip(reason="no CUDA device")
+    for item in items:
+        if "gpu" in item.keywords:
+            item.add_marker(skip)
+
+
+@pytest.fixture(scope="session")
+def gb():
+    """The built package on cuda:0 (GPU tests only)."""
+    import torch
+    from paper_2607_10983_gb300 import _build
+    _build.build()
+    import paper_2607_10983_gb300 as pkg
+    pkg.lib()
+    torch.cuda.set_device(0)
+    return pkg

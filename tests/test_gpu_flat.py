@@ -1,0 +1,249 @@
+"""Parity of the CUDA flat path with the FP64 oracle, through the C ABI (GPU)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import flat
+from synth import grf
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+SHAPES = [(32, 32, 32), (16, 8, 32), (24, 24, 24), (12, 12, 12)]
+
+
+def to_dev(a, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV, dtype)
+
+
+def rand(shape, seed):
+    return np.random.default_rng(seed).standard_normal(shape)
+
+
+def rel_max(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-14), (torch.float32, 2e-6)])
+def test_apply_and_residual(gb, shape, dtype, tol):
+    s = gb.Solver(shape, prec="fp64")
+    for level in range(min(2, s.levels)):
+        shp = s.level_shape(level)
+        h = 2.0 ** level
+        u, f = rand(shp, 1), rand(shp, 2)
+        ud = to_dev(u, dtype)
+        u32 = ud.double().cpu().numpy()
+        f32 = to_dev(f, dtype).double().cpu().numpy()
+        got = s.apply(level, ud).double().cpu().numpy()
+        ref = flat.apply_A(u32, h)
+        assert rel_max(got, ref) < tol * 12
+        got = s.residual(level, to_dev(f, dtype), ud).double().cpu().numpy()
+        assert rel_max(got, flat.residual(f32, u32, h)) < tol * 12
+
+
+@pytest.mark.parametrize("smoother", ["chebyshev", "jacobi"])
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-13), (torch.float32, 1e-5)])
+def test_smoothers(gb, smoother, dtype, tol):
+    s = gb.Solver((16, 8, 32), prec="fp64", smoother=smoother, degree=4, nu1=3)
+    for level in range(s.levels):
+        shp = s.level_shape(level)
+        h = 2.0 ** level
+        e, r = rand(shp, 3), rand(shp, 4)
+        ed, rd = to_dev(e, dtype), to_dev(r, dtype)
+        e_in, r_in = ed.double().cpu().numpy(), rd.double().cpu().numpy()
+        got = s.smooth(level, ed, rd).double().cpu().numpy()
+        if smoother == "chebyshev":
+            ref = flat.smooth_chebyshev(e_in, r_in, h, 4, 8.0)
+        else:
+            ref = flat.smooth_jacobi(e_in, r_in, h, 3, 2.0 / 3.0)
+        assert rel_max(got, ref) < tol
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-15), (torch.float32, 1e-6)])
+def test_transfers(gb, shape, dtype, tol):
+    s = gb.Solver(shape, prec="fp64")
+    for level in range(s.levels - 1):
+        fine = rand(s.level_shape(level), 5)
+        fd = to_dev(fine, dtype)
+        got = s.restrict(level, fd).double().cpu().numpy()
+        assert rel_max(got, flat.restrict_fw(fd.double().cpu().numpy())) < tol
+        coarse = rand(s.level_shape(level + 1), 6)
+        cd = to_dev(coarse, dtype)
+        base = rand(s.level_shape(level), 7)
+        bd = to_dev(base, dtype)
+        ref = bd.double().cpu().numpy() + flat.prolong(cd.double().cpu().numpy())
+        got = s.prolong_add(level, cd, bd).double().cpu().numpy()
+        assert rel_max(got, ref) < tol * 4
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (24, 24, 24), (16, 8, 32), (8, 8, 8)])
+def test_coarse_solve(gb, shape):
+    s = gb.Solver(shape, prec="fp64")
+    cshape = s.level_shape(s.levels - 1)
+    h = 2.0 ** (s.levels - 1)
+    r = rand(cshape, 8) + 0.25
+    ref = flat.coarse_solve(r, h)
+    got = s.coarse_solve(to_dev(r)).cpu().numpy()
+    assert rel_max(got, ref) < 1e-12
+    got32 = s.coarse_solve(to_dev(r, torch.float32)).double().cpu().numpy()
+    assert rel_max(got32, ref) < 1e-5
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("mixed", 2e-5)])
+@pytest.mark.parametrize("shape", [(32, 32, 32), (16, 8, 32), (24, 24, 24)])
+def test_vcycle_matches_oracle(gb, prec, tol, shape):
+    s = gb.Solver(shape, prec=prec, fused=False)
+    r = grf(shape, 9)
+    rd = to_dev(r, s.work_dtype)
+    got = s.vcycle(rd).double().cpu().numpy()
+    ref = flat.vcycle(0, np.zeros(shape), rd.double().cpu().numpy(), s.levels)
+    assert rel_max(got, ref) < tol
+
+
+def test_df_conversions_bit_exact(gb):
+    rng = np.random.default_rng(10)
+    x = np.concatenate([
+        rng.standard_normal(100000) * 10.0 ** rng.integers(-30, 30, 100000),
+        np.array([0.0, -0.0, 1.0, -1.0, 1 + 2.0 ** -24, 1 + 3 * 2.0 ** -24, 1 + 2.0 ** -24 + 2.0 ** -50,
+                  2.0 ** -126, 3.4e38, -3.0e38, 1e-300, 123456789.123456789, np.pi * 1e20]),
+    ])
+    s = gb.Solver(8, prec="mixed")
+    df = s.f64_to_df(to_dev(x)).cpu().numpy()
+    hi = x.astype(np.float32)
+    lo = (x - hi.astype(np.float64)).astype(np.float32)
+    normal = np.abs(x) >= 2.0 ** -126
+    np.testing.assert_array_equal(df[normal, 0], hi[normal])
+    np.testing.assert_array_equal(df[normal, 1], lo[normal])
+    assert np.all(df[~normal, 0] == 0.0)
+    back = s.df_to_f64(to_dev(df, torch.float32)).cpu().numpy()
+    big = np.abs(x) >= 2.0 ** -100
+    err = np.abs(back[big] - x[big]) / np.abs(x[big])
+    assert err.max() < 2.0 ** -46
+    special = s.f64_to_df(to_dev(np.array([np.inf, -np.inf, np.nan]))).cpu().numpy()
+    assert np.isposinf(special[0, 0]) and np.isneginf(special[1, 0]) and np.isnan(special[2, 0])
+
+
+@pytest.mark.parametrize("n", [32, 64])
+def test_df_residual_matches_fp64(gb, n):
+    F = grf(n, 11) + 0.3
+    phi = flat.fft_solve(F) * (1 + 1e-4) + 1e-3 * grf(n, 12)
+    m = float(F.mean())
+    s = gb.Solver(n, prec="mixed")
+    r = s.df_residual(s.f64_to_df(to_dev(F)), m, s.f64_to_df(to_dev(phi))).double().cpu().numpy()
+    ref = flat.residual(F - m, phi)
+    tol = 1e-7 * np.abs(ref) + 1e-12 * np.abs(phi).max()
+    assert np.all(np.abs(r - ref) <= tol), float(np.abs(r - ref).max())
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (16, 8, 32)])
+def test_plain_fp64_solve_plain_method(gb, shape):
+    # plain-method workload: FP64, V(3,3) Chebyshev, 4 levels at 32^3, phi = 0, tol 1e-10
+    F = grf(shape, 1)
+    s = gb.Solver(shape, prec="fp64")
+    phi, st = s.solve(to_dev(F), tol=1e-10, max_vcycles=50)
+    assert st.status == 0 and st.rel_res <= 1e-10
+    ref = flat.fft_solve(F)
+    assert np.linalg.norm(phi.cpu().numpy() - ref) / np.linalg.norm(ref) < 1e-10
+    _, hist = flat.mg_solve(F, tol=1e-10)
+    assert st.cycles == len(hist) - 1
+    np.testing.assert_allclose(st.history, hist[1:], rtol=1e-3)
+
+
+def test_fixed_cycle_iterates_match_oracle(gb):
+    F = grf(32, 13)
+    phi0 = flat.fft_solve(grf(32, 14))
+    ref, _ = flat.mg_solve(F, phi0=phi0, fixed_cycles=3)
+    s = gb.Solver(32, prec="fp64")
+    # tol 0 never converges, so exactly max_vcycles cycles run
+    phi, st = s.solve(to_dev(F), to_dev(phi0), tol=0.0, max_vcycles=3)
+    assert st.cycles == 3 and st.status == 4
+    assert rel_max(phi.cpu().numpy(), ref) < 1e-12
+    sm = gb.Solver(32, prec="mixed", fused=False)
+    phim, _ = sm.solve(to_dev(F), to_dev(phi0), tol=0.0, max_vcycles=3)
+    assert np.linalg.norm(phim.cpu().numpy() - ref) / np.linalg.norm(ref) < 1e-5
+
+
+@pytest.mark.parametrize("fused", [False, True])
+@pytest.mark.parametrize("shape", [(32, 32, 32), (64, 64, 64), (16, 8, 32), (48, 48, 48)])
+def test_mixed_solve_to_1e6(gb, shape, fused):
+    F = grf(shape, 15)
+    s = gb.Solver(shape, prec="mixed", fused=fused)
+    phi, st = s.solve(to_dev(F), tol=1e-6, max_vcycles=40)
+    assert st.status == 0 and st.rel_res <= 1e-6
+    ref = flat.fft_solve(F)
+    err = np.linalg.norm(phi.cpu().numpy() - ref) / np.linalg.norm(ref)
+    assert err < 1e-6
+    # the mixed solve can go far below FP32 accuracy thanks to the double-float outer loop
+    phi, st = s.solve(to_dev(F), tol=1e-11, max_vcycles=60)
+    assert st.status == 0
+    assert np.linalg.norm(phi.cpu().numpy() - ref) / np.linalg.norm(ref) < 1e-10
+
+
+def test_warm_start_saves_cycles(gb):
+    n = 64
+    d0, eta = grf(n, 2), grf(n, 3)
+    s = gb.Solver(n, prec="mixed")
+    phi, st0 = s.solve(to_dev(d0), tol=1e-6)
+    F1 = d0 + 0.05 * eta
+    _, cold = s.solve(to_dev(F1), tol=1e-6)
+    warm_phi, warm = s.solve(to_dev(F1), phi.clone(), tol=1e-6)
+    assert warm.cycles < cold.cycles
+    assert abs(warm.rel_res0 - 0.05 * np.linalg.norm(eta) / np.linalg.norm(F1)) < 0.01
+    ref = flat.fft_solve(F1)
+    assert np.linalg.norm(warm_phi.cpu().numpy() - ref) / np.linalg.norm(ref) < 1e-6
+
+
+def test_host_buffer_solve_matches_device(gb):
+    n = 32
+    F = grf(n, 16)
+    s = gb.Solver(n, prec="mixed")
+    phi_d, st_d = s.solve(to_dev(F), tol=1e-8)
+    phi_h = np.zeros_like(F)
+    _, st_h = s.solve_host(F, phi_h, tol=1e-8)
+    assert st_h.cycles == st_d.cycles
+    np.testing.assert_array_equal(phi_h, phi_d.cpu().numpy())
+
+
+def test_error_statuses(gb):
+    n = 16
+    s = gb.Solver(n, prec="mixed")
+    F = grf(n, 17)
+    bad = F.copy()
+    bad[3, 4, 5] = np.nan
+    phi, st = s.solve(to_dev(bad), tol=1e-6)
+    assert st.status == 5
+    phi0 = to_dev(grf(n, 18))
+    phi, st = s.solve(to_dev(F), phi0.clone(), tol=1e-6, max_vcycles=0)
+    assert st.status == 4 and st.cycles == 0
+    # phi written with the gauge applied even when no cycle ran
+    np.testing.assert_allclose(phi.cpu().numpy(), phi0.cpu().numpy() - phi0.cpu().numpy().mean(), atol=1e-12)
+    with pytest.raises(gb.GbmgError):
+        s.solve(to_dev(F), tol=1e-30, max_vcycles=2, raise_on_nonconvergence=True)
+    with pytest.raises(ValueError):
+        s.solve(to_dev(F).float())
+    with pytest.raises(gb.GbmgError):
+        gb.Solver((4, 4, 2))
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (64, 64, 64), (32, 48, 64), (96, 96, 96)])
+@pytest.mark.parametrize("degree", [2, 3, 4])
+def test_fused_vcycle_bit_identical_to_unfused(gb, shape, degree):
+    # the temporally blocked kernels round exactly like the one-kernel-per-operation chain
+    r = to_dev(grf(shape, 19), torch.float32)
+    a = gb.Solver(shape, prec="mixed", fused=True, degree=degree).vcycle(r)
+    b = gb.Solver(shape, prec="mixed", fused=False, degree=degree).vcycle(r)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("shape", [(64, 64, 64), (32, 48, 64)])
+def test_fused_solve_iterates_match_unfused(gb, shape):
+    F = to_dev(grf(shape, 20))
+    pa, sa = gb.Solver(shape, prec="mixed", fused=True).solve(F, tol=0.0, max_vcycles=4)
+    pb, sb = gb.Solver(shape, prec="mixed", fused=False).solve(F, tol=0.0, max_vcycles=4)
+    assert sa.cycles == sb.cycles == 4
+    diff = (pa - pb).abs().max().item()
+    assert diff <= 1e-14 * pb.abs().max().item()
+    np.testing.assert_allclose(sa.history, sb.history, rtol=1e-5)
