@@ -6,6 +6,11 @@
  *
  *   flat operator  (GBMG_OP_FLAT7): A phi = F, A the second-order 7-point
  *                  Laplacian (Sec. 2.1, Eq. linsys), F mean-projected, phi zero mean.
+ *   curvilinear    (GBMG_OP_CURV19): the moving-mesh Laplace-Beltrami operator
+ *                  L = M / sqrt(g) of a deformation potential psi (Sec. 4.2-4.3,
+ *                  Eq. LB and curv_linsys), M the conservative 19-point flux
+ *                  divergence; L phi = delta - sum(delta sqrt g)/sum(sqrt g)
+ *                  (Eq. solvability), phi zero mean.
  *
  * Conventions for every entry point
  *   - Fields are dense arrays of nx*ny*nz values, row-major [z][y][x] with x the
@@ -65,8 +70,9 @@ typedef struct {
   double alpha;  /* Chebyshev target interval [2/alpha, 2] of D^-1 A (alpha > 1)   */
   int nu1, nu2;  /* Jacobi sweeps before / after the coarse correction (>= 0)      */
   double omega;  /* Jacobi weight                                                  */
-  int fused;     /* 1: temporally blocked level kernels (GBMG_MIXED + Chebyshev);   */
-                 /* 0: one kernel per operation                                    */
+  int fused;     /* temporally blocked level kernels (GBMG_MIXED + Chebyshev):       */
+                 /* 1: on levels of at least 128^3 cells, 2: on every level of at  */
+                 /* least 16^3 (results are identical), 0: one kernel per operation */
 } gbmg_opts;
 
 typedef struct {
@@ -99,17 +105,39 @@ void mg_destroy(gbmg_ctx* ctx);
 /* Queue later work on `cuda_stream` (a cudaStream_t; NULL = legacy default stream). */
 gbmg_status mg_set_stream(gbmg_ctx* ctx, void* cuda_stream);
 
-/* Solve A phi = F (Sec. 2.1).  source_dev: F (nx*ny*nz doubles; its mean is
- * projected out, the buffer is not modified).  coeffs_dev: must be NULL for the flat
- * operator.  phi_inout_dev: initial guess in (zeros = cold start, previous solution =
+/* Curvilinear contexts only: set the deformation potential psi (nx*ny*nz doubles,
+ * cell units, periodic).  psi is restricted to every level by full weighting and the
+ * triad A = I + Hess psi, sqrt(g) = det A and B = sqrt(g) g^-1 are rebuilt per level
+ * (Sec. 4.2, Eq. triad, Eq. metric; Appendix B); the coarsest operator is inverted
+ * exactly.  Waits for the stream.  GBMG_ERR_INVALID_ARG if a coarsest volume element
+ * is not positive (a folded mesh). */
+gbmg_status mg_set_geometry(gbmg_ctx* ctx, const double* psi_dev);
+
+/* Solve A phi = F (Sec. 2.1) or, on a curvilinear context, L phi = f (Sec. 4.3).
+ * source_dev: F (nx*ny*nz doubles; its mean, or volume-weighted mean for the
+ * curvilinear operator, is projected out; the buffer is not modified).  coeffs_dev:
+ * NULL for the flat operator; on a curvilinear context the deformation potential psi
+ * (as for mg_set_geometry) or NULL to keep the geometry already set.  phi_inout_dev: initial guess in (zeros = cold start, previous solution =
  * warm start, Sec. 3.1-3.2), zero-mean solution out.  V-cycles run until
  * ||F - A phi|| / ||F|| <= tol or max_vcycles cycles (max_vcycles <= 0 runs none and
  * only evaluates the residual).  The call waits for the stream and returns the
  * convergence status: GBMG_OK, or NOT_CONVERGED / NONFINITE / DIVERGED with phi still
  * written (last iterate, gauge applied).  stats: NULL or filled on return; the same
  * record is kept for mg_last_stats(). */
-gbmg_status mg_solve(gbmg_ctx* ctx, const double* source_dev, const float* coeffs_dev,
+gbmg_status mg_solve(gbmg_ctx* ctx, const double* source_dev, const double* coeffs_dev,
                      double* phi_inout_dev, double tol, int max_vcycles, gbmg_stats* stats);
+
+/* Vector-Jacobian product of the solve (Sec. 4.8, Eq. adj_rhs and Eq. adj_op) for the
+ * scalar <phi_bar, phi(source, psi)>:
+ *   flat: source_bar = P A^+ P phi_bar (A symmetric; P removes the mean);
+ *   curvilinear: M^T lam = phi_bar - mean(phi_bar) is solved by the same multigrid on
+ *   the exact transpose, source_bar = J (lam - sum(J lam)/sum(J)), and, if psi_bar_dev
+ *   is not NULL, psi_bar = the gradient through the geometry, which needs the forward
+ *   solution phi_dev and source_dev.  All fields nx*ny*nz doubles; psi_bar_dev must be
+ *   NULL for the flat operator.  Convergence as in mg_solve; waits for the stream. */
+gbmg_status mg_solve_adjoint(gbmg_ctx* ctx, const double* phi_bar_dev, double* source_bar_dev,
+                             double* psi_bar_dev, const double* phi_dev, const double* source_dev,
+                             double tol, int max_vcycles, gbmg_stats* stats);
 
 /* Same solve with host buffers: copies F and the initial phi to the device, solves,
  * copies phi back and waits.  Staging buffers are allocated on the first call and
@@ -187,6 +215,17 @@ gbmg_status mg_coarse_solve(gbmg_ctx* ctx, int dtype, const void* r_dev, void* e
  * working precision of the context (GBMG_FP64: double, GBMG_MIXED: float), starting
  * from e = 0, with the configured smoother and fusion. */
 gbmg_status mg_vcycle(gbmg_ctx* ctx, const void* r_dev, void* e_dev);
+
+/* Curvilinear components (geometry must be set).  out = op(u) or op(u) / J on level
+ * `level`, op = M (transpose 0) or its exact transpose M^T (transpose 1). */
+gbmg_status mg_curv_apply(gbmg_ctx* ctx, int level, int dtype, int transpose, int divide_by_J,
+                          const void* u_dev, void* out_dev);
+/* Copy the geometry of a level: J (n floats) and B packed xx, yy, zz, xy, xz, yz (6 n
+ * floats); either pointer may be NULL. */
+gbmg_status mg_curv_geometry(gbmg_ctx* ctx, int level, float* J_dev, float* B_dev);
+/* One FP32 curvilinear V-cycle (weighted Jacobi nu1/nu2) on L e = r (transpose 0) or on
+ * the transposed-solve operator M^T / J (transpose 1), from e = 0. */
+gbmg_status mg_curv_vcycle(gbmg_ctx* ctx, int transpose, const float* r_dev, float* e_dev);
 
 /* Double-float helpers of the mixed-precision path.  A double-float array stores each
  * value x as the float pair (hi, lo), hi = round(x), lo = round(x - hi): 2*n floats. */

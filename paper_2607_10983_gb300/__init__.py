@@ -91,6 +91,11 @@ _SIGS = {
     "mg_f64_to_df": (_S, [_P, _LL, _P, _P]),
     "mg_df_to_f64": (_S, [_P, _LL, _P, _P]),
     "mg_df_residual": (_S, [_P, _P, _D, _P, _P]),
+    "mg_set_geometry": (_S, [_P, _P]),
+    "mg_solve_adjoint": (_S, [_P, _P, _P, _P, _P, _P, _D, _I, ctypes.POINTER(_Stats)]),
+    "mg_curv_apply": (_S, [_P, _I, _I, _I, _I, _P, _P]),
+    "mg_curv_geometry": (_S, [_P, _I, _P, _P]),
+    "mg_curv_vcycle": (_S, [_P, _I, _P, _P]),
     "mg_profile_begin": (_S, [_P, _I]),
     "mg_profile_read": (_S, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "mg_profile_end": (_S, [_P]),
@@ -163,9 +168,12 @@ class Solver:
     """One multigrid hierarchy for a periodic (nz, ny, nx) mesh on the current CUDA device."""
 
     def __init__(self, shape, levels: int = 0, degree: int = 3, prec: str = "mixed",
-                 smoother: str = "chebyshev", fused: bool = True, alpha: float = 8.0,
+                 smoother: str | None = None, fused: bool = True, alpha: float = 8.0,
                  nu1: int = 2, nu2: int = 2, omega: float = 2.0 / 3.0, op: str = "flat"):
         L = lib()
+        if smoother is None:
+            smoother = "jacobi" if op == "curv" else "chebyshev"
+        self.op = op
         self.shape = _shape3(shape)
         o = _Opts()
         L.gbmg_default_opts(ctypes.byref(o))
@@ -206,21 +214,59 @@ class Solver:
         return (z.value, y.value, x.value)
 
     # -- solves
+    def set_geometry(self, psi: torch.Tensor):
+        """Curvilinear contexts: set the deformation potential psi (float64, mesh shape)."""
+        _check(lib().mg_set_geometry(self._c(), _ptr(psi, torch.float64, self.shape)))
+
     def solve(self, F: torch.Tensor, phi: torch.Tensor | None = None, tol: float = 1e-6,
-              max_vcycles: int = 50, raise_on_nonconvergence: bool = False):
-        """Solve A phi = F; phi (float64, same shape) is the warm start and is overwritten.
+              max_vcycles: int = 50, raise_on_nonconvergence: bool = False, psi: torch.Tensor | None = None):
+        """Solve A phi = F (or L_psi phi = F); phi (float64) is the warm start and is overwritten.
 
         Returns (phi, Stats).  Non-convergence is reported in Stats.status unless
-        raise_on_nonconvergence is set.
+        raise_on_nonconvergence is set.  psi (curvilinear only) sets the geometry first.
         """
         ctx = self._c()
         if phi is None:
             phi = torch.zeros_like(F)
         st = _Stats()
-        s = lib().mg_solve(ctx, _ptr(F, torch.float64, self.shape), None, _ptr(phi, torch.float64, self.shape),
-                           float(tol), int(max_vcycles), ctypes.byref(st))
+        s = lib().mg_solve(ctx, _ptr(F, torch.float64, self.shape), _ptr(psi, torch.float64, self.shape),
+                           _ptr(phi, torch.float64, self.shape), float(tol), int(max_vcycles), ctypes.byref(st))
         _check(s, allow_convergence=not raise_on_nonconvergence)
         return phi, Stats.from_c(st)
+
+    def solve_adjoint(self, phi_bar: torch.Tensor, phi: torch.Tensor | None = None,
+                      source: torch.Tensor | None = None, want_psi_bar: bool = False, tol: float = 1e-6,
+                      max_vcycles: int = 50):
+        """Vector-Jacobian product of the solve: returns (source_bar, psi_bar or None, Stats)."""
+        src_bar = torch.empty_like(phi_bar)
+        psi_bar = torch.empty_like(phi_bar) if want_psi_bar else None
+        st = _Stats()
+        s = lib().mg_solve_adjoint(self._c(), _ptr(phi_bar, torch.float64, self.shape), _ptr(src_bar),
+                                   _ptr(psi_bar), _ptr(phi, torch.float64, self.shape),
+                                   _ptr(source, torch.float64, self.shape), float(tol), int(max_vcycles),
+                                   ctypes.byref(st))
+        _check(s, allow_convergence=True)
+        return src_bar, psi_bar, Stats.from_c(st)
+
+    def curv_apply(self, level: int, u: torch.Tensor, transpose: bool = False, divide_by_J: bool = True):
+        out = torch.empty_like(u)
+        _check(lib().mg_curv_apply(self._c(), level, _dtype_code(u), int(transpose), int(divide_by_J),
+                                   _ptr(u, shape=self.level_shape(level)), _ptr(out)))
+        return out
+
+    def curv_geometry(self, level: int):
+        """(J, B) of a level as float32 tensors, B packed xx, yy, zz, xy, xz, yz."""
+        shp = self.level_shape(level)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        J = torch.empty(shp, dtype=torch.float32, device=dev)
+        B = torch.empty((6,) + shp, dtype=torch.float32, device=dev)
+        _check(lib().mg_curv_geometry(self._c(), level, _ptr(J), _ptr(B)))
+        return J, B
+
+    def curv_vcycle(self, r: torch.Tensor, transpose: bool = False):
+        out = torch.empty_like(r)
+        _check(lib().mg_curv_vcycle(self._c(), int(transpose), _ptr(r, torch.float32, self.shape), _ptr(out)))
+        return out
 
     def solve_host(self, F, phi, tol: float = 1e-6, max_vcycles: int = 50):
         """Same solve on host float64 arrays (numpy or CPU tensors); phi is overwritten."""
@@ -308,3 +354,44 @@ class Solver:
         out = torch.empty(self.shape, dtype=torch.float32, device=F_df.device)
         _check(lib().mg_df_residual(self._c(), _ptr(F_df, torch.float32), float(m), _ptr(phi_df, torch.float32), _ptr(out)))
         return out
+
+
+# ---------------------------------------------------------------- autograd
+
+
+class MGSolve(torch.autograd.Function):
+    """phi = solve(F) for the flat operator; backward: the adjoint solve (same operator)."""
+
+    @staticmethod
+    def forward(ctx, F, solver, tol, max_vcycles):
+        phi, st = solver.solve(F.detach().contiguous(), tol=tol, max_vcycles=max_vcycles)
+        ctx.solver, ctx.tol, ctx.maxv = solver, tol, max_vcycles
+        return phi
+
+    @staticmethod
+    def backward(ctx, phi_bar):
+        src_bar, _, _ = ctx.solver.solve_adjoint(phi_bar.contiguous(), tol=ctx.tol, max_vcycles=ctx.maxv)
+        return src_bar, None, None, None
+
+
+class CurvMGSolve(torch.autograd.Function):
+    """phi = solve(delta, psi) for the moving-mesh operator; backward: adjoint solve on
+    the exact transpose and the gradient through the geometry (recomputed from psi)."""
+
+    @staticmethod
+    def forward(ctx, delta, psi, solver, tol, max_vcycles):
+        delta = delta.detach().contiguous()
+        psi = psi.detach().contiguous()
+        phi, st = solver.solve(delta, tol=tol, max_vcycles=max_vcycles, psi=psi)
+        ctx.save_for_backward(delta, psi, phi)
+        ctx.solver, ctx.tol, ctx.maxv = solver, tol, max_vcycles
+        return phi.clone()
+
+    @staticmethod
+    def backward(ctx, phi_bar):
+        delta, psi, phi = ctx.saved_tensors
+        ctx.solver.set_geometry(psi)
+        d_bar, p_bar, _ = ctx.solver.solve_adjoint(phi_bar.contiguous(), phi=phi, source=delta,
+                                                   want_psi_bar=ctx.needs_input_grad[1], tol=ctx.tol,
+                                                   max_vcycles=ctx.maxv)
+        return d_bar, p_bar, None, None, None

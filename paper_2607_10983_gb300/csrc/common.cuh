@@ -221,6 +221,12 @@ __device__ __forceinline__ double block_sum_f(float v, double* sh) {
   return r;
 }
 
+// Block sum of per-thread compensated sums (s + c): each thread's pair goes to FP64
+// once, then a deterministic FP64 block reduction.  Result valid in thread 0.
+__device__ __forceinline__ double block_sum_acc(const DfAcc& a, double* sh) {
+  return block_sum((double)a.s + (double)a.c, sh);
+}
+
 __device__ __forceinline__ int block_linear_id() {
   return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
 }

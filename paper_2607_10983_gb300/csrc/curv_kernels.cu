@@ -1,0 +1,636 @@
+// Moving-mesh (curvilinear) operator kernels (Sec. 4.2-4.3, Appendix B).
+//
+// Geometry per level (Sec. 4.2, Eq. triad and Eq. metric): A = I + Hess psi with
+// second-order central differences (mixed terms by the four-point 1/(4h^2)
+// stencil), J = sqrt(g) = det A and B = sqrt(g) g^-1 = J A^-2 = adj(A)^2 / J.
+// Built in FP64 from the FP64 psi of the level, stored as FP32 (J and the six
+// components of the symmetric B).
+//
+// Operator (Sec. 4.3.1): (M u)_i = sum_a (F^a_{i+1/2} - F^a_{i-1/2}) / h with face
+// fluxes F^a = sum_b B^{ab}_face G_b, B_face the mean of the two adjacent cells,
+// G_a the two-point normal difference and G_b (b != a) the central differences of
+// the two adjacent cells averaged onto the face.  L = M / J is the operator the
+// V-cycle solves (Eq. curv_linsys); the transposed solve of the adjoint uses the
+// exact transpose M^T (by summation by parts) with the same 1/J.
+#include "kernels.h"
+#include "stencil.cuh"
+
+namespace gbmg {
+
+namespace {
+
+constexpr int BX = 32, BY = 8;
+inline dim3 cell_grid(Dims d) { return dim3((d.nx + BX - 1) / BX, (d.ny + BY - 1) / BY, d.nz); }
+
+// component index of B^{ab} in the packed symmetric layout xx, yy, zz, xy, xz, yz
+__host__ __device__ constexpr int bidx(int a, int b) {
+  return a == b ? a : (a + b == 1 ? 3 : (a + b == 2 ? 4 : 5));
+}
+
+// 3x3x3 neighbourhood of a cell with periodic wrap: idx(dx, dy, dz), d* in {-1, 0, 1}.
+struct Nbhd {
+  long long zo[3];
+  int yo[3];
+  int xo[3];
+  __device__ __forceinline__ Nbhd(Dims d, int x, int y, int z) {
+    const long long pst = (long long)d.nx * d.ny;
+    xo[0] = wrapi(x - 1, d.nx);
+    xo[1] = x;
+    xo[2] = wrapi(x + 1, d.nx);
+    yo[0] = wrapi(y - 1, d.ny) * d.nx;
+    yo[1] = y * d.nx;
+    yo[2] = wrapi(y + 1, d.ny) * d.nx;
+    zo[0] = (long long)wrapi(z - 1, d.nz) * pst;
+    zo[1] = (long long)z * pst;
+    zo[2] = (long long)wrapi(z + 1, d.nz) * pst;
+  }
+  // offset of the cell displaced by (dx, dy, dz)
+  __device__ __forceinline__ long long operator()(int dx, int dy, int dz) const {
+    return zo[dz + 1] + yo[dy + 1] + xo[dx + 1];
+  }
+};
+
+// displacement of unit vector a (0 = x, 1 = y, 2 = z) scaled by s, added to (dx, dy, dz)
+__device__ __forceinline__ void shift(int a, int s, int& dx, int& dy, int& dz) {
+  if (a == 0) dx += s;
+  else if (a == 1) dy += s;
+  else dz += s;
+}
+
+// Face coefficient B^{ab} on the a-face between the cell at offset c and c + e_a.
+template <typename T, typename BF>
+__device__ __forceinline__ T face_B(const BF& Bc, int a, int b, int cx, int cy, int cz) {
+  int px = cx, py = cy, pz = cz;
+  shift(a, 1, px, py, pz);
+  return T(0.5) * (T(Bc(bidx(a, b), cx, cy, cz)) + T(Bc(bidx(a, b), px, py, pz)));
+}
+
+// h * (flux F^a on the face between offset c and c + e_a), plain arithmetic in T.
+template <typename T, typename UF, typename BF>
+__device__ __forceinline__ T face_flux(const UF& u, const BF& Bc, int a, int cx, int cy, int cz) {
+  int px = cx, py = cy, pz = cz;
+  shift(a, 1, px, py, pz);
+  T f = face_B<T>(Bc, a, a, cx, cy, cz) * (u(px, py, pz) - u(cx, cy, cz));
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    if (b == a) continue;
+    int c1x = cx, c1y = cy, c1z = cz, c2x = cx, c2y = cy, c2z = cz;
+    shift(b, 1, c1x, c1y, c1z);
+    shift(b, -1, c2x, c2y, c2z);
+    int d1x = px, d1y = py, d1z = pz, d2x = px, d2y = py, d2z = pz;
+    shift(b, 1, d1x, d1y, d1z);
+    shift(b, -1, d2x, d2y, d2z);
+    const T tang = T(0.25) * ((u(c1x, c1y, c1z) - u(c2x, c2y, c2z)) + (u(d1x, d1y, d1z) - u(d2x, d2y, d2z)));
+    f += face_B<T>(Bc, a, b, cx, cy, cz) * tang;
+  }
+  return f;
+}
+
+// h^2 (M u) at the centre cell.
+template <typename T, typename UF, typename BF>
+__device__ __forceinline__ T apply_M_h2(const UF& u, const BF& Bc) {
+  T out = T(0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    int mx = 0, my = 0, mz = 0;
+    shift(a, -1, mx, my, mz);
+    out += face_flux<T>(u, Bc, a, 0, 0, 0) - face_flux<T>(u, Bc, a, mx, my, mz);
+  }
+  return out;
+}
+
+// h^2 (M^T y) at the centre cell j, from <y, M x> = sum_a sum_i h F^a[x]_i (y_i - y_{i+a}) / h^2:
+// q_ab(c) = B^{ab}_face(c) (y_c - y_{c+a});  M^T y = sum_a [q_aa(j-a) - q_aa(j)]
+//   + sum_{b != a} [(q_ab(j-b) - q_ab(j+b)) + (q_ab(j-a-b) - q_ab(j-a+b))] / 4.
+template <typename T, typename UF, typename BF>
+__device__ __forceinline__ T apply_MT_h2(const UF& y, const BF& Bc) {
+  auto q = [&](int a, int b, int cx, int cy, int cz) -> T {
+    int px = cx, py = cy, pz = cz;
+    shift(a, 1, px, py, pz);
+    return face_B<T>(Bc, a, b, cx, cy, cz) * (y(cx, cy, cz) - y(px, py, pz));
+  };
+  T out = T(0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    int ax = 0, ay = 0, az = 0;
+    shift(a, -1, ax, ay, az);  // j - a
+    out += q(a, a, ax, ay, az) - q(a, a, 0, 0, 0);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      if (b == a) continue;
+      int m1x = 0, m1y = 0, m1z = 0, p1x = 0, p1y = 0, p1z = 0;
+      shift(b, -1, m1x, m1y, m1z);
+      shift(b, 1, p1x, p1y, p1z);
+      int m2x = ax, m2y = ay, m2z = az, p2x = ax, p2y = ay, p2z = az;
+      shift(b, -1, m2x, m2y, m2z);
+      shift(b, 1, p2x, p2y, p2z);
+      out += T(0.25) * ((q(a, b, m1x, m1y, m1z) - q(a, b, p1x, p1y, p1z)) +
+                        (q(a, b, m2x, m2y, m2z) - q(a, b, p2x, p2y, p2z)));
+    }
+  }
+  return out;
+}
+
+// h^2 times the diagonal of M (and of M^T): -sum_a (B^{aa}_{+face} + B^{aa}_{-face}) (Appendix B).
+template <typename T, typename BF>
+__device__ __forceinline__ T diag_M_h2(const BF& Bc) {
+  T d = T(0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    int mx = 0, my = 0, mz = 0;
+    shift(a, -1, mx, my, mz);
+    d -= face_B<T>(Bc, a, a, 0, 0, 0) + face_B<T>(Bc, a, a, mx, my, mz);
+  }
+  return d;
+}
+
+template <typename V>
+struct FieldAt {
+  const V* __restrict__ p;
+  const Nbhd* nb;
+  __device__ __forceinline__ V operator()(int dx, int dy, int dz) const { return p[(*nb)(dx, dy, dz)]; }
+};
+
+struct CoefAt {
+  CurvCoef c;
+  const Nbhd* nb;
+  __device__ __forceinline__ float operator()(int comp, int dx, int dy, int dz) const {
+    return c.B[comp][(*nb)(dx, dy, dz)];
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ T op_h2(const FieldAt<T>& u, const CoefAt& B, bool transpose) {
+  return transpose ? apply_MT_h2<T>(u, B) : apply_M_h2<T>(u, B);
+}
+
+// ------------------------------------------------------------------ kernels
+
+__global__ void k_geom(Dims d, const double* __restrict__ psi, double h, CurvCoefOut out) {
+  const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y, z = blockIdx.z;
+  if (x >= d.nx || y >= d.ny) return;
+  const Nbhd nb(d, x, y, z);
+  auto P = [&](int dx, int dy, int dz) { return psi[nb(dx, dy, dz)]; };
+  const double ih2 = 1.0 / (h * h), iq = 0.25 / (h * h);
+  const double c0 = P(0, 0, 0);
+  const double a = 1.0 + (P(1, 0, 0) - 2.0 * c0 + P(-1, 0, 0)) * ih2;
+  const double b = 1.0 + (P(0, 1, 0) - 2.0 * c0 + P(0, -1, 0)) * ih2;
+  const double c = 1.0 + (P(0, 0, 1) - 2.0 * c0 + P(0, 0, -1)) * ih2;
+  const double dxy = (P(1, 1, 0) - P(1, -1, 0) - P(-1, 1, 0) + P(-1, -1, 0)) * iq;
+  const double dxz = (P(1, 0, 1) - P(1, 0, -1) - P(-1, 0, 1) + P(-1, 0, -1)) * iq;
+  const double dyz = (P(0, 1, 1) - P(0, 1, -1) - P(0, -1, 1) + P(0, -1, -1)) * iq;
+  // adjugate of the symmetric triad [[a, dxy, dxz], [dxy, b, dyz], [dxz, dyz, c]]
+  const double j00 = b * c - dyz * dyz, j11 = a * c - dxz * dxz, j22 = a * b - dxy * dxy;
+  const double j01 = dxz * dyz - dxy * c, j02 = dxy * dyz - b * dxz, j12 = dxy * dxz - a * dyz;
+  const double J = a * j00 + dxy * j01 + dxz * j02;
+  const double iJ = 1.0 / J;
+  const long long i = nb(0, 0, 0);
+  out.J[i] = (float)J;
+  out.B[0][i] = (float)((j00 * j00 + j01 * j01 + j02 * j02) * iJ);
+  out.B[1][i] = (float)((j01 * j01 + j11 * j11 + j12 * j12) * iJ);
+  out.B[2][i] = (float)((j02 * j02 + j12 * j12 + j22 * j22) * iJ);
+  out.B[3][i] = (float)((j00 * j01 + j01 * j11 + j02 * j12) * iJ);
+  out.B[4][i] = (float)((j00 * j02 + j01 * j12 + j02 * j22) * iJ);
+  out.B[5][i] = (float)((j01 * j02 + j11 * j12 + j12 * j22) * iJ);
+}
+
+// out = op(u) / J (divide_J) or op(u), op = M or M^T
+template <typename T>
+__global__ void k_curv_apply(Dims d, CurvCoef cf, const T* __restrict__ u, T* __restrict__ out, T inv_h2,
+                             int transpose, int divide_J) {
+  const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y, z = blockIdx.z;
+  if (x >= d.nx || y >= d.ny) return;
+  const Nbhd nb(d, x, y, z);
+  const FieldAt<T> U{u, &nb};
+  const CoefAt Bc{cf, &nb};
+  const long long i = nb(0, 0, 0);
+  T v = op_h2<T>(U, Bc, transpose) * inv_h2;
+  if (divide_J) v /= T(cf.J[i]);
+  out[i] = v;
+}
+
+// out = r - op(u) / J, with optional block partial sums of out^2
+template <typename T>
+__global__ void k_curv_residual(Dims d, CurvCoef cf, const T* __restrict__ r, const T* __restrict__ u,
+                                T* __restrict__ out, T inv_h2, int transpose, double* __restrict__ partials) {
+  __shared__ double sh[32];
+  const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y, z = blockIdx.z;
+  T res = T(0);
+  if (x < d.nx && y < d.ny) {
+    const Nbhd nb(d, x, y, z);
+    const FieldAt<T> U{u, &nb};
+    const CoefAt Bc{cf, &nb};
+    const long long i = nb(0, 0, 0);
+    res = r[i] - op_h2<T>(U, Bc, transpose) * inv_h2 / T(cf.J[i]);
+    out[i] = res;
+  }
+  if (partials) {
+    double s;
+    if constexpr (sizeof(T) == 8) s = block_sum((double)res * (double)res, sh);
+    else s = block_sum_f(res * res, sh);
+    if (is_thread0()) partials[block_linear_id()] = s;
+  }
+}
+
+// Weighted Jacobi (Appendix B, Eq. jacobi): e' = e + omega (r - L e) / D_L, D_L = diag(M) / J,
+// written as e + omega (J r - M e) / diag(M).
+template <typename T>
+__global__ void k_curv_jacobi(Dims d, CurvCoef cf, const T* __restrict__ r, const T* __restrict__ e_in,
+                              T* __restrict__ e_out, int transpose, T omega) {
+  const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y, z = blockIdx.z;
+  if (x >= d.nx || y >= d.ny) return;
+  const Nbhd nb(d, x, y, z);
+  const FieldAt<T> U{e_in, &nb};
+  const CoefAt Bc{cf, &nb};
+  const long long i = nb(0, 0, 0);
+  const T Mh2 = op_h2<T>(U, Bc, transpose);
+  const T Dh2 = diag_M_h2<T>(Bc);
+  // (J r - M e) / diag(M) with h^2 scalings cancelling: (J r h^2 - M e h^2) / (diag h^2)
+  e_out[i] = e_in[i] + omega * ((T(cf.J[i]) * r[i] * cf.h2 - Mh2) / Dh2);
+}
+
+// Dense matrix of the level operator (row-major n x n, FP64): entry (i, j) = (op(e_j) / J)_i.
+struct UnitAt {
+  const Nbhd* nb;
+  long long j;
+  __device__ __forceinline__ double operator()(int dx, int dy, int dz) const { return (*nb)(dx, dy, dz) == j ? 1.0 : 0.0; }
+};
+
+__global__ void k_curv_dense(Dims d, CurvCoef cf, int transpose, double* __restrict__ out) {
+  const long long n = ncell(d);
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const long long i = idx / n, j = idx % n;
+  const int x = (int)(i % d.nx), y = (int)((i / d.nx) % d.ny), z = (int)(i / ((long long)d.nx * d.ny));
+  const Nbhd nb(d, x, y, z);
+  const UnitAt U{&nb, j};
+  const CoefAt Bc{cf, &nb};
+  const double v = transpose ? apply_MT_h2<double>(U, Bc) : apply_M_h2<double>(U, Bc);
+  out[idx] = v / ((double)cf.h2 * (double)cf.J[i]);
+}
+
+// ---- double-float residual of the outer defect correction on the finest level ----
+
+// DF difference a - b of two double-float values.
+__device__ __forceinline__ float2 df_sub(float2 a, float2 b) {
+  float s, e;
+  two_sum(a.x, -b.x, s, e);
+  e += a.y - b.y;
+  float h, l;
+  quick_two_sum(s, e, h, l);
+  return make_float2(h, l);
+}
+
+// acc += w * v exactly up to the rounding of the small terms (w float, v double-float).
+__device__ __forceinline__ void df_acc_prod(DfAcc& acc, float w, float2 v) {
+  const float p = w * v.x;
+  const float pe = __fmaf_rn(w, v.x, -p);
+  acc.add(p);
+  acc.c += pe + w * v.y;
+}
+
+struct DfFieldAt {
+  const float2* __restrict__ p;
+  const Nbhd* nb;
+  __device__ __forceinline__ float2 operator()(int dx, int dy, int dz) const { return p[(*nb)(dx, dy, dz)]; }
+};
+
+// acc += h^2 (M u) (forward) with u double-float, every flux difference in double-float.
+__device__ __forceinline__ void df_apply_M(DfAcc& acc, const DfFieldAt& u, const CoefAt& Bc, float sign) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      // face between c and c + e_a; side 0: c = 0 (+), side 1: c = -e_a (-)
+      int cx = 0, cy = 0, cz = 0;
+      if (side) shift(a, -1, cx, cy, cz);
+      const float sg = side ? -sign : sign;
+      int px = cx, py = cy, pz = cz;
+      shift(a, 1, px, py, pz);
+      df_acc_prod(acc, sg * face_B<float>(Bc, a, a, cx, cy, cz), df_sub(u(px, py, pz), u(cx, cy, cz)));
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        if (b == a) continue;
+        const float w = sg * 0.25f * face_B<float>(Bc, a, b, cx, cy, cz);
+        int c1x = cx, c1y = cy, c1z = cz, c2x = cx, c2y = cy, c2z = cz;
+        shift(b, 1, c1x, c1y, c1z);
+        shift(b, -1, c2x, c2y, c2z);
+        int d1x = px, d1y = py, d1z = pz, d2x = px, d2y = py, d2z = pz;
+        shift(b, 1, d1x, d1y, d1z);
+        shift(b, -1, d2x, d2y, d2z);
+        df_acc_prod(acc, w, df_sub(u(c1x, c1y, c1z), u(c2x, c2y, c2z)));
+        df_acc_prod(acc, w, df_sub(u(d1x, d1y, d1z), u(d2x, d2y, d2z)));
+      }
+    }
+  }
+}
+
+// acc += sign * h^2 (M^T y) with y double-float.
+__device__ __forceinline__ void df_apply_MT(DfAcc& acc, const DfFieldAt& y, const CoefAt& Bc, float sign) {
+  auto q = [&](float w, int a, int b, int cx, int cy, int cz) {
+    int px = cx, py = cy, pz = cz;
+    shift(a, 1, px, py, pz);
+    df_acc_prod(acc, w * face_B<float>(Bc, a, b, cx, cy, cz), df_sub(y(cx, cy, cz), y(px, py, pz)));
+  };
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    int ax = 0, ay = 0, az = 0;
+    shift(a, -1, ax, ay, az);
+    q(sign, a, a, ax, ay, az);
+    q(-sign, a, a, 0, 0, 0);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      if (b == a) continue;
+      int m1x = 0, m1y = 0, m1z = 0, p1x = 0, p1y = 0, p1z = 0;
+      shift(b, -1, m1x, m1y, m1z);
+      shift(b, 1, p1x, p1y, p1z);
+      int m2x = ax, m2y = ay, m2z = az, p2x = ax, p2y = ay, p2z = az;
+      shift(b, -1, m2x, m2y, m2z);
+      shift(b, 1, p2x, p2y, p2z);
+      const float w = 0.25f * sign;
+      q(w, a, b, m1x, m1y, m1z);
+      q(-w, a, b, p1x, p1y, p1z);
+      q(w, a, b, m2x, m2y, m2z);
+      q(-w, a, b, p2x, p2y, p2z);
+    }
+  }
+}
+
+// r = (b - op(u) / h^2) / J rounded to float, with b = J (src - m) when scale_J (forward
+// source in L-form) or b = src (transposed solve, M-form right-hand side).  Partial sums
+// of r^2 and of (b / J)^2.
+__global__ void k_curv_df_residual(Dims d, CurvCoef cf, const float2* __restrict__ src, const double* __restrict__ m_dev,
+                                   int scale_J, const float2* __restrict__ u, int transpose, float* __restrict__ r,
+                                   double* __restrict__ pr2, double* __restrict__ pf2) {
+  __shared__ double sh[32];
+  const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y, z = blockIdx.z;
+  float rv = 0.f, fv = 0.f;
+  if (x < d.nx && y < d.ny) {
+    const Nbhd nb(d, x, y, z);
+    const long long i = nb(0, 0, 0);
+    const DfFieldAt U{u, &nb};
+    const CoefAt Bc{cf, &nb};
+    const float J = cf.J[i];
+    float2 b = src[i];
+    if (m_dev) {
+      const float2 m = f64_to_df(m_dev[0]);
+      b = df_add(b, make_float2(-m.x, -m.y));
+    }
+    // acc = h^2 b_M - h^2 op(u), b_M = J * b (forward) or b (transposed)
+    DfAcc acc{0.f, 0.f};
+    const float wb = scale_J ? J * cf.h2 : cf.h2;
+    // wb * b exactly: J * h^2 is rounded once; the operator's h^2 scaling is exact (power of 4)
+    df_acc_prod(acc, wb, b);
+    if (transpose) df_apply_MT(acc, U, Bc, -1.f);
+    else df_apply_M(acc, U, Bc, -1.f);
+    rv = (acc.s + acc.c) / (J * cf.h2);
+    r[i] = rv;
+    fv = scale_J ? (b.x + b.y) : (b.x + b.y) / J;
+  }
+  if (pr2) {
+    const double s = block_sum_f(rv * rv, sh);
+    if (is_thread0()) pr2[block_linear_id()] = s;
+  }
+  if (pf2) {
+    const double s = block_sum_f(fv * fv, sh);
+    if (is_thread0()) pf2[block_linear_id()] = s;
+  }
+}
+
+// partial sums of x * J and of J (volume-weighted mean, Eq. solvability)
+__global__ void k_wsum(long long n, const double* __restrict__ x, const float* __restrict__ J,
+                       double* __restrict__ pxj, double* __restrict__ pj) {
+  __shared__ double sh[32];
+  DfAcc s{0.f, 0.f}, w{0.f, 0.f};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float2 v = f64_to_df(x[i]);
+    const float j = J[i];
+    const float p = v.x * j;
+    s.add(p);
+    s.c += __fmaf_rn(v.x, j, -p) + v.y * j;
+    w.add(j);
+  }
+  const double bs = block_sum_acc(s, sh);
+  const double bw = block_sum_acc(w, sh);
+  if (threadIdx.x == 0) {
+    pxj[blockIdx.x] = bs;
+    pj[blockIdx.x] = bw;
+  }
+}
+
+__global__ void k_ratio(const double* a, const double* b, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) out[0] = b[0] != 0.0 ? a[0] / b[0] : 0.0;
+}
+
+
+// ---- adjoint of the geometry (Sec. 4.8, Eq. adj_op) ----
+
+// Per cell of the finest level: the cotangent of the triad A for the scalar
+//   <lam, b(J)> - <lam, M(B) phi>,  b = J (delta - m_w),
+// where Jbar = (delta - m_w)(lam - s_lam), s_lam = sum(J lam)/sum(J), and Bbar
+// comes from <lam, M phi> = sum_a sum_i sum_b B^{ab}_face(i) G^a_b[phi](i) (lam_i - lam_{i+a})/h,
+// B^{ab}_face(i) = (B^{ab}_i + B^{ab}_{i+a})/2.  With B = J A^-2 and J = det A:
+//   Abar_J = Jbar J A^-1,  Abar_B = J <Bbar, A^-2> A^-1 - J (A^-1 Bbar A^-2 + A^-2 Bbar A^-1).
+// Writes S = Abar_J - Abar_B symmetrised for the Hessian stencils:
+// S_aa = Abar_aa, S_ab = Abar_ab + Abar_ba (a < b), packed xx, yy, zz, xy, xz, yz.
+__global__ void k_psibar_A(Dims d, const double* __restrict__ psi, const double* __restrict__ phi,
+                           const double* __restrict__ lam, const double* __restrict__ delta,
+                           const double* __restrict__ mw_dev, const double* __restrict__ slam_dev,
+                           double h, double* __restrict__ S) {
+  const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y, z = blockIdx.z;
+  if (x >= d.nx || y >= d.ny) return;
+  const long long n = ncell(d);
+  const Nbhd nb(d, x, y, z);
+  const long long i = nb(0, 0, 0);
+  // triad at this cell
+  auto P = [&](int dx, int dy, int dz) { return psi[nb(dx, dy, dz)]; };
+  const double ih2 = 1.0 / (h * h), iq = 0.25 / (h * h);
+  const double c0 = P(0, 0, 0);
+  double A[3][3];
+  A[0][0] = 1.0 + (P(1, 0, 0) - 2.0 * c0 + P(-1, 0, 0)) * ih2;
+  A[1][1] = 1.0 + (P(0, 1, 0) - 2.0 * c0 + P(0, -1, 0)) * ih2;
+  A[2][2] = 1.0 + (P(0, 0, 1) - 2.0 * c0 + P(0, 0, -1)) * ih2;
+  A[0][1] = A[1][0] = (P(1, 1, 0) - P(1, -1, 0) - P(-1, 1, 0) + P(-1, -1, 0)) * iq;
+  A[0][2] = A[2][0] = (P(1, 0, 1) - P(1, 0, -1) - P(-1, 0, 1) + P(-1, 0, -1)) * iq;
+  A[1][2] = A[2][1] = (P(0, 1, 1) - P(0, 1, -1) - P(0, -1, 1) + P(0, -1, -1)) * iq;
+  double adj[3][3];
+  adj[0][0] = A[1][1] * A[2][2] - A[1][2] * A[1][2];
+  adj[1][1] = A[0][0] * A[2][2] - A[0][2] * A[0][2];
+  adj[2][2] = A[0][0] * A[1][1] - A[0][1] * A[0][1];
+  adj[0][1] = adj[1][0] = A[0][2] * A[1][2] - A[0][1] * A[2][2];
+  adj[0][2] = adj[2][0] = A[0][1] * A[1][2] - A[1][1] * A[0][2];
+  adj[1][2] = adj[2][1] = A[0][1] * A[0][2] - A[0][0] * A[1][2];
+  const double J = A[0][0] * adj[0][0] + A[0][1] * adj[0][1] + A[0][2] * adj[0][2];
+  double Ai[3][3], Ai2[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) Ai[a][b] = adj[a][b] / J;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) Ai2[a][b] = Ai[a][0] * Ai[0][b] + Ai[a][1] * Ai[1][b] + Ai[a][2] * Ai[2][b];
+  // Bbar at this cell: faces a at i (own) and i - a (left neighbour's face)
+  auto PH = [&](int dx, int dy, int dz) { return phi[nb(dx, dy, dz)]; };
+  auto LA = [&](int dx, int dy, int dz) { return lam[nb(dx, dy, dz)]; };
+  // face value of G^a_b[phi] * (lam_c - lam_{c+a}) / h on the a-face between c and c + a
+  auto fbar = [&](int a, int b, int cx, int cy, int cz) -> double {
+    int px = cx, py = cy, pz = cz;
+    shift(a, 1, px, py, pz);
+    const double Lam = (LA(cx, cy, cz) - LA(px, py, pz)) / h;
+    double G;
+    if (a == b) {
+      G = (PH(px, py, pz) - PH(cx, cy, cz)) / h;
+    } else {
+      int c1x = cx, c1y = cy, c1z = cz, c2x = cx, c2y = cy, c2z = cz;
+      shift(b, 1, c1x, c1y, c1z);
+      shift(b, -1, c2x, c2y, c2z);
+      int d1x = px, d1y = py, d1z = pz, d2x = px, d2y = py, d2z = pz;
+      shift(b, 1, d1x, d1y, d1z);
+      shift(b, -1, d2x, d2y, d2z);
+      G = 0.25 * ((PH(c1x, c1y, c1z) - PH(c2x, c2y, c2z)) + (PH(d1x, d1y, d1z) - PH(d2x, d2y, d2z))) / h;
+    }
+    return G * Lam;
+  };
+  double Bb[3][3];
+  for (int a = 0; a < 3; ++a) {
+    int mx = 0, my = 0, mz = 0;
+    shift(a, -1, mx, my, mz);
+    for (int b = 0; b < 3; ++b) Bb[a][b] = 0.5 * (fbar(a, b, 0, 0, 0) + fbar(a, b, mx, my, mz));
+  }
+  // Abar_B = J <Bbar, A^-2> A^-1 - J (A^-1 Bbar A^-2 + A^-2 Bbar A^-1)   (A symmetric)
+  double inner = 0.0;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) inner += Bb[a][b] * Ai2[a][b];
+  double T1[3][3], T2[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      T1[a][b] = Bb[a][0] * Ai2[0][b] + Bb[a][1] * Ai2[1][b] + Bb[a][2] * Ai2[2][b];  // Bbar A^-2
+      T2[a][b] = Bb[a][0] * Ai[0][b] + Bb[a][1] * Ai[1][b] + Bb[a][2] * Ai[2][b];     // Bbar A^-1
+    }
+  const double mw = mw_dev[0], sl = slam_dev[0];
+  const double Jbar = (delta[i] - mw) * (lam[i] - sl);
+  double Ab[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      const double t = Ai[a][0] * T1[0][b] + Ai[a][1] * T1[1][b] + Ai[a][2] * T1[2][b] +
+                       Ai2[a][0] * T2[0][b] + Ai2[a][1] * T2[1][b] + Ai2[a][2] * T2[2][b];
+      const double AbB = J * inner * Ai[a][b] - J * t;
+      Ab[a][b] = Jbar * J * Ai[a][b] - AbB;
+    }
+  S[i] = Ab[0][0];
+  S[n + i] = Ab[1][1];
+  S[2 * n + i] = Ab[2][2];
+  S[3 * n + i] = Ab[0][1] + Ab[1][0];
+  S[4 * n + i] = Ab[0][2] + Ab[2][0];
+  S[5 * n + i] = Ab[1][2] + Ab[2][1];
+}
+
+// psi_bar = sum_a D_aa(S_aa) + sum_{a<b} D_ab(S_ab): the transpose of psi -> Hess psi,
+// each second-difference stencil being self-adjoint on the periodic mesh.
+__global__ void k_psibar_H(Dims d, const double* __restrict__ S, double h, double* __restrict__ out) {
+  const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y, z = blockIdx.z;
+  if (x >= d.nx || y >= d.ny) return;
+  const long long n = ncell(d);
+  const Nbhd nb(d, x, y, z);
+  auto C = [&](int k, int dx, int dy, int dz) { return S[k * n + nb(dx, dy, dz)]; };
+  const double ih2 = 1.0 / (h * h), iq = 0.25 / (h * h);
+  double v = (C(0, 1, 0, 0) - 2.0 * C(0, 0, 0, 0) + C(0, -1, 0, 0)) * ih2;
+  v += (C(1, 0, 1, 0) - 2.0 * C(1, 0, 0, 0) + C(1, 0, -1, 0)) * ih2;
+  v += (C(2, 0, 0, 1) - 2.0 * C(2, 0, 0, 0) + C(2, 0, 0, -1)) * ih2;
+  v += (C(3, 1, 1, 0) - C(3, 1, -1, 0) - C(3, -1, 1, 0) + C(3, -1, -1, 0)) * iq;
+  v += (C(4, 1, 0, 1) - C(4, 1, 0, -1) - C(4, -1, 0, 1) + C(4, -1, 0, -1)) * iq;
+  v += (C(5, 0, 1, 1) - C(5, 0, 1, -1) - C(5, 0, -1, 1) + C(5, 0, -1, -1)) * iq;
+  out[nb(0, 0, 0)] = v;
+}
+
+// out = J (lam - s) in FP64 from a double-float lam (delta_bar of the curvilinear adjoint).
+__global__ void k_jscale(long long n, const float2* __restrict__ lam, const float* __restrict__ J,
+                         const double* __restrict__ s_dev, double* __restrict__ out, double* __restrict__ lam64) {
+  const double s = s_dev ? s_dev[0] : 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double l = df_to_f64(lam[i]);
+    if (lam64) lam64[i] = l;
+    if (out) out[i] = (double)J[i] * (l - s);
+  }
+}
+}  // namespace
+
+cudaError_t launch_psibar(cudaStream_t st, Dims d, const double* psi, const double* phi, const double* lam,
+                          const double* delta, const double* mw_dev, const double* slam_dev, double h, double* S,
+                          double* out) {
+  k_psibar_A<<<cell_grid(d), dim3(BX, BY), 0, st>>>(d, psi, phi, lam, delta, mw_dev, slam_dev, h, S);
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_psibar_H<<<cell_grid(d), dim3(BX, BY), 0, st>>>(d, S, h, out);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jscale(cudaStream_t st, long long n, const float2* lam, const float* J, const double* s_dev,
+                          double* out, double* lam64) {
+  k_jscale<<<(int)df_partial_count(n), 256, 0, st>>>(n, lam, J, s_dev, out, lam64);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_geom(cudaStream_t st, Dims d, const double* psi, double h, CurvCoefOut out) {
+  k_geom<<<cell_grid(d), dim3(BX, BY), 0, st>>>(d, psi, h, out);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_curv_apply(cudaStream_t st, Dims d, CurvCoef cf, const T* u, T* out, int transpose, int divide_J) {
+  k_curv_apply<T><<<cell_grid(d), dim3(BX, BY), 0, st>>>(d, cf, u, out, (T)(1.0 / cf.h2), transpose, divide_J);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_curv_residual(cudaStream_t st, Dims d, CurvCoef cf, const T* r, const T* u, T* out, int transpose,
+                                 double* partials) {
+  k_curv_residual<T><<<cell_grid(d), dim3(BX, BY), 0, st>>>(d, cf, r, u, out, (T)(1.0 / cf.h2), transpose, partials);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_curv_jacobi(cudaStream_t st, Dims d, CurvCoef cf, const T* r, const T* e_in, T* e_out, int transpose,
+                               T omega) {
+  k_curv_jacobi<T><<<cell_grid(d), dim3(BX, BY), 0, st>>>(d, cf, r, e_in, e_out, transpose, omega);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_curv_dense(cudaStream_t st, Dims d, CurvCoef cf, int transpose, double* out) {
+  const long long n = ncell(d);
+  k_curv_dense<<<(unsigned)((n * n + 255) / 256), 256, 0, st>>>(d, cf, transpose, out);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_curv_df_residual(cudaStream_t st, Dims d, CurvCoef cf, const float2* src, const double* m_dev,
+                                    int scale_J, const float2* u, int transpose, float* r, double* pr2, double* pf2) {
+  k_curv_df_residual<<<cell_grid(d), dim3(BX, BY), 0, st>>>(d, cf, src, m_dev, scale_J, u, transpose, r, pr2, pf2);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wsum(cudaStream_t st, long long n, const double* x, const float* J, double* pxj, double* pj) {
+  k_wsum<<<(int)df_partial_count(n), 256, 0, st>>>(n, x, J, pxj, pj);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ratio(cudaStream_t st, const double* a, const double* b, double* out) {
+  k_ratio<<<1, 32, 0, st>>>(a, b, out);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_curv_apply<float>(cudaStream_t, Dims, CurvCoef, const float*, float*, int, int);
+template cudaError_t launch_curv_apply<double>(cudaStream_t, Dims, CurvCoef, const double*, double*, int, int);
+template cudaError_t launch_curv_residual<float>(cudaStream_t, Dims, CurvCoef, const float*, const float*, float*, int, double*);
+template cudaError_t launch_curv_residual<double>(cudaStream_t, Dims, CurvCoef, const double*, const double*, double*, int, double*);
+template cudaError_t launch_curv_jacobi<float>(cudaStream_t, Dims, CurvCoef, const float*, const float*, float*, int, float);
+template cudaError_t launch_curv_jacobi<double>(cudaStream_t, Dims, CurvCoef, const double*, const double*, double*, int, double);
+
+}  // namespace gbmg

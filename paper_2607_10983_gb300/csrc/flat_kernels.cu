@@ -194,14 +194,15 @@ __global__ void k_finalize(const double* __restrict__ p, long long count, double
 __global__ void k_f64_to_df(long long n, const double* __restrict__ x, float2* __restrict__ out,
                             double* __restrict__ ps) {
   __shared__ double sh[32];
-  float s = 0.f;
+  DfAcc s{0.f, 0.f};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const float2 v = f64_to_df(x[i]);
     out[i] = v;
-    s += v.x;
+    s.add(v.x);
+    s.c += v.y;
   }
   if (ps) {
-    const double b = block_sum_f(s, sh);
+    const double b = block_sum_acc(s, sh);
     if (threadIdx.x == 0) ps[blockIdx.x] = b;
   }
 }
@@ -249,17 +250,18 @@ __global__ void k_df_residual(Dims d, const float2* __restrict__ F, const double
 __global__ void k_df_update(long long n, float2* __restrict__ phi, const float* __restrict__ e,
                             double* __restrict__ ps) {
   __shared__ double sh[32];
-  float s = 0.f;
+  DfAcc s{0.f, 0.f};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     float2 v = phi[i];
     if (e) {
       v = df_add_f(v, e[i]);
       phi[i] = v;
     }
-    s += v.x;
+    s.add(v.x);
+    s.c += v.y;
   }
   if (ps) {
-    const double b = block_sum_f(s, sh);
+    const double b = block_sum_acc(s, sh);
     if (threadIdx.x == 0) ps[blockIdx.x] = b;
   }
 }

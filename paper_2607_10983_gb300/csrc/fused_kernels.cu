@@ -41,7 +41,8 @@ struct Tile {
   static constexpr int NPOS = WX * WY;
   static constexpr int K = (NPOS + NT - 1) / NT;  // positions per thread
   static constexpr int PAD = WX + 1;              // padding so p +- 1, p +- WX stay in bounds
-  static constexpr int PLANE = NPOS + 2 * PAD;
+  // every thread slot (valid or not) owns a plane entry, so no slot needs a guard
+  static constexpr int PLANE = K * NT + 2 * PAD;
 };
 
 // Per-thread position bookkeeping: plane offset of each owned position in the
@@ -115,7 +116,7 @@ k_down_fused(Dims d, const float* __restrict__ r, float* __restrict__ e_out, flo
   {
     const long long base = (long long)wrapmod(tb, d.nz) * pst;
 #pragma unroll
-    for (int k = 0; k < K; ++k) rnext[k] = (P.vmask >> k & 1u) ? __ldg(r + base + P.goff[k]) : 0.f;
+    for (int k = 0; k < K; ++k) rnext[k] = __ldg(r + base + P.goff[k]);
   }
   for (int t = tb; t <= te; ++t) {
     const int cur = (t - tb) & 1, prv = cur ^ 1;
@@ -128,7 +129,7 @@ k_down_fused(Dims d, const float* __restrict__ r, float* __restrict__ e_out, flo
     if (t < te) {
       const long long base = (long long)wrapmod(t + 1, d.nz) * pst;
 #pragma unroll
-      for (int k = 0; k < K; ++k) rnext[k] = (P.vmask >> k & 1u) ? __ldg(r + base + P.goff[k]) : 0.f;
+      for (int k = 0; k < K; ++k) rnext[k] = __ldg(r + base + P.goff[k]);
     }
     float en[V + 1][K], dn[V + 1][K];
     // stage 1 (pointwise, e starts at zero): e_1 = d_1 = c2_0 D^-1 r
@@ -137,7 +138,7 @@ k_down_fused(Dims d, const float* __restrict__ r, float* __restrict__ e_out, flo
       float dd = 0.f;
       en[1][k] = cheb_step(0.f, rq[0][k], dd, dinv, cf.c1[0], cf.c2[0]);
       dn[1][k] = dd;
-      if (P.vmask >> k & 1u) plane(0, cur)[tid + k * NT] = en[1][k];
+      plane(0, cur)[tid + k * NT] = en[1][k];
     }
     // stages 2..V: Chebyshev steps with the stencil on e_{s-1}
 #pragma unroll
@@ -147,7 +148,7 @@ k_down_fused(Dims d, const float* __restrict__ r, float* __restrict__ e_out, flo
       const int zp = t - s + 1;
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        const int p = (P.vmask >> k & 1u) ? tid + k * NT : 0;  // invalid slots read in bounds
+        const int p = tid + k * NT;
         const float c = wc[s][k];
         const float res = resid_from_sum(rq[s - 1][k],
                                          nbr_sum(src[p - 1], src[p + 1], src[p - WX], src[p + WX], wp[s][k], en[s - 1][k]),
@@ -155,7 +156,7 @@ k_down_fused(Dims d, const float* __restrict__ r, float* __restrict__ e_out, flo
         float dd = dh[s][k];
         en[s][k] = cheb_step(c, res, dd, dinv, cf.c1[s - 1], cf.c2[s - 1]);
         dn[s][k] = dd;
-        if (P.vmask >> k & 1u) dst[p] = en[s][k];
+        dst[p] = en[s][k];
         if (s == V && (P.tmask >> k & 1u) && zp >= z0 && zp < zend) e_out[(long long)zp * pst + P.goff[k]] = en[s][k];
       }
     }
@@ -173,11 +174,11 @@ k_down_fused(Dims d, const float* __restrict__ r, float* __restrict__ e_out, flo
       const bool cz = ((c & 1) == 0) && c >= z0 && c < zend;
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        const int p = (P.vmask >> k & 1u) ? tid + k * NT : 0;  // invalid slots read in bounds
+        const int p = tid + k * NT;
         const float rn = resid_from_sum(rq[V][k],
                                         nbr_sum(src[p - 1], src[p + 1], src[p - WX], src[p + WX], wp[V + 1][k], en[V][k]),
                                         wc[V + 1][k], inv_h2);
-        if (cz && (P.vmask >> k & 1u)) zsd[p] = fw3(rsp[k], rsc[k], rn);
+        if (cz) zsd[p] = fw3(rsp[k], rsc[k], rn);
         rsp[k] = rsc[k];
         rsc[k] = rn;
       }
@@ -210,30 +211,79 @@ k_down_fused(Dims d, const float* __restrict__ r, float* __restrict__ e_out, flo
 
 // ------------------------------------------------------------------ up leg
 
+__device__ __forceinline__ int floor_half(int v) { return v >= 0 ? v / 2 : -((1 - v) / 2); }
+__device__ __forceinline__ int mod3(int v) {
+  const int r = v % 3;
+  return r < 0 ? r + 3 : r;
+}
+
+// Coarse tile of the up leg: the coarse nodes under a fine region of WX x WY cells
+// starting at fine (x0 - H, y0 - H), one node of margin for the +1 neighbour.
+template <int TX, int TY, int H>
+struct CoarseTile {
+  static constexpr int WX = TX + 2 * H, WY = TY + 2 * H;
+  static constexpr int CW = (WX + 3) / 2 + 1;
+  static constexpr int CH = (WY + 3) / 2 + 1;
+  static constexpr int CN = CW * CH;
+};
+
 template <int V, int TX, int TY, int NT>
 __global__ void __launch_bounds__(NT, 1)
 k_up_fused(Dims d, const float* __restrict__ e_in, const float* __restrict__ ec, const float* __restrict__ r,
            float* __restrict__ e_out, int zc, float inv_h2, float dinv, Coef cf) {
   constexpr int H = V;
   using TL = Tile<TX, TY, H, NT>;
+  using CT = CoarseTile<TX, TY, H>;
   constexpr int WX = TL::WX, K = TL::K, PLANE = TL::PLANE, PAD = TL::PAD;
+  constexpr int CW = CT::CW, CN = CT::CN, CL = (CN + NT - 1) / NT;
   extern __shared__ float sm[];
-  // plane(s, b): e_s for s = 0..V-1 (e_0 = e + P e_c)
+  // plane(s, b): e_s for s = 0..V-1 (e_0 = e + P e_c); then three coarse planes
   auto plane = [&](int s, int b) -> float* { return sm + (s * 2 + b) * PLANE + PAD; };
+  float* cring = sm + V * 2 * PLANE;
 
   const int tid = threadIdx.x;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * zc;
   const int zend = min(z0 + zc, d.nz);
   const long long pst = (long long)d.nx * d.ny;
   const Dims dc{d.nx / 2, d.ny / 2, d.nz / 2};
+  const long long cpst = (long long)dc.nx * dc.ny;
   Positions<TX, TY, H, NT> P;
   P.init(d, x0, y0);
-  int gx[K], gy[K];
+  // coarse node under each position (local offset in the coarse tile) and the odd flags
+  const int CX0 = floor_half(x0 - H), CY0 = floor_half(y0 - H);
+  int co[K];
+  unsigned oddx = 0, oddy = 0;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    gx[k] = P.goff[k] % d.nx;
-    gy[k] = P.goff[k] / d.nx;
+    const int p = tid + k * NT;
+    co[k] = 0;
+    if (p < TL::NPOS) {
+      const int ux = x0 - H + p % WX, uy = y0 - H + p / WX;
+      const int I = floor_half(ux), J = floor_half(uy);
+      co[k] = (J - CY0) * CW + (I - CX0);
+      oddx |= (unsigned)(ux - 2 * I) << k;
+      oddy |= (unsigned)(uy - 2 * J) << k;
+    }
   }
+  // coarse tile cells this thread loads
+  int cgo[CL];
+#pragma unroll
+  for (int j = 0; j < CL; ++j) {
+    const int q = tid + j * NT;
+    cgo[j] = -1;
+    if (q < CN) cgo[j] = wrapmod(CX0 + q % CW, dc.nx) + wrapmod(CY0 + q / CW, dc.ny) * dc.nx;
+  }
+  auto load_coarse = [&](int Ku, float (&vals)[CL]) {
+    const long long base = (long long)wrapmod(Ku, dc.nz) * cpst;
+#pragma unroll
+    for (int j = 0; j < CL; ++j) vals[j] = cgo[j] >= 0 ? __ldg(ec + base + cgo[j]) : 0.f;
+  };
+  auto store_coarse = [&](int Ku, const float (&vals)[CL]) {
+    float* dst = cring + mod3(Ku) * CN;
+#pragma unroll
+    for (int j = 0; j < CL; ++j)
+      if (cgo[j] >= 0) dst[tid + j * NT] = vals[j];
+  };
 
   float rq[V + 1][K];
   float wp[V + 1][K], wc[V + 1][K];
@@ -249,16 +299,29 @@ k_up_fused(Dims d, const float* __restrict__ e_in, const float* __restrict__ ec,
     const long long base = (long long)wrapmod(t, d.nz) * pst;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      const bool v = P.vmask >> k & 1u;
-      rnext[k] = v ? __ldg(r + base + P.goff[k]) : 0.f;
-      enext[k] = v ? __ldg(e_in + base + P.goff[k]) : 0.f;
+      rnext[k] = __ldg(r + base + P.goff[k]);
+      enext[k] = __ldg(e_in + base + P.goff[k]);
     }
   };
+  {
+    float cv[CL];
+    const int K0 = floor_half(tb);
+    load_coarse(K0, cv);
+    store_coarse(K0, cv);
+    load_coarse(K0 + 1, cv);
+    store_coarse(K0 + 1, cv);
+  }
   load(tb);
+  __syncthreads();
   for (int t = tb; t <= te; ++t) {
     const int cur = (t - tb) & 1, prv = cur ^ 1;
     float en[V + 1][K], dn[V + 1][K];
-    const int tz = wrapmod(t, d.nz);
+    const int Ku = floor_half(t);
+    const bool zodd = (t - 2 * Ku) != 0;
+    // next coarse plane (needed from the next even t on), stored at the end of this iteration
+    float cv[CL];
+    const bool need_c = zodd && t < te;
+    if (need_c) load_coarse(Ku + 2, cv);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
 #pragma unroll
@@ -267,12 +330,27 @@ k_up_fused(Dims d, const float* __restrict__ e_in, const float* __restrict__ ec,
       en[0][k] = enext[k];
     }
     if (t < te) load(t + 1);
-    // stage 0: e_0 = e + P e_c (pointwise)
+    // stage 0: e_0 = e + P e_c (pointwise), P from the coarse planes Ku and Ku + 1
+    {
+      const float* c0 = cring + mod3(Ku) * CN;
+      const float* c1 = cring + mod3(Ku + 1) * CN;
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      if (P.vmask >> k & 1u) {
-        en[0][k] = t_add(en[0][k], prolong_value(ec, dc, gx[k], gy[k], tz));
-        plane(0, cur)[tid + k * NT] = en[0][k];
+      for (int k = 0; k < K; ++k) {
+        {
+          const bool dx = oddx >> k & 1u, dy = oddy >> k & 1u;
+          auto cxv = [&](const float* cp, int off) -> float {
+            const float v0 = cp[off];
+            return dx ? half_sum(v0, cp[off + 1]) : v0;
+          };
+          auto cyv = [&](const float* cp) -> float {
+            const float v0 = cxv(cp, co[k]);
+            return dy ? half_sum(v0, cxv(cp, co[k] + CW)) : v0;
+          };
+          const float v0 = cyv(c0);
+          const float pv = zodd ? half_sum(v0, cyv(c1)) : v0;
+          en[0][k] = t_add(en[0][k], pv);
+          plane(0, cur)[tid + k * NT] = en[0][k];
+        }
       }
     }
     // stages 1..V: Chebyshev post-smoothing steps at plane t - s
@@ -282,7 +360,7 @@ k_up_fused(Dims d, const float* __restrict__ e_in, const float* __restrict__ ec,
       const int zp = t - s;
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        const int p = (P.vmask >> k & 1u) ? tid + k * NT : 0;  // invalid slots read in bounds
+        const int p = tid + k * NT;
         const float c = wc[s][k];
         const float res = resid_from_sum(rq[s][k],
                                          nbr_sum(src[p - 1], src[p + 1], src[p - WX], src[p + WX], wp[s][k], en[s - 1][k]),
@@ -291,7 +369,7 @@ k_up_fused(Dims d, const float* __restrict__ e_in, const float* __restrict__ ec,
         en[s][k] = cheb_step(c, res, dd, dinv, cf.c1[s - 1], cf.c2[s - 1]);
         dn[s][k] = dd;
         if (s < V) {
-          if (P.vmask >> k & 1u) plane(s, cur)[p] = en[s][k];
+          plane(s, cur)[p] = en[s][k];
         } else if ((P.tmask >> k & 1u) && zp >= z0 && zp < zend) {
           e_out[(long long)zp * pst + P.goff[k]] = en[s][k];
         }
@@ -307,6 +385,7 @@ k_up_fused(Dims d, const float* __restrict__ e_in, const float* __restrict__ ec,
 #pragma unroll
       for (int s = 2; s <= V; ++s) dh[s][k] = dn[s - 1][k];
     }
+    if (need_c) store_coarse(Ku + 2, cv);
     __syncthreads();
   }
 }
@@ -315,6 +394,7 @@ k_up_fused(Dims d, const float* __restrict__ e_in, const float* __restrict__ ec,
 
 // phi' = phi + e (double-float) on the tile plus a one-cell halo, then
 // r' = F - m - A phi' on the tile; block partial sums of r'^2 and of phi'.
+// Loads of the next plane are issued before the current plane is processed.
 template <int TX, int TY, int NT>
 __global__ void __launch_bounds__(NT)
 k_df_update_residual(Dims d, const float2* __restrict__ phi_in, const float* __restrict__ e,
@@ -333,24 +413,49 @@ k_df_update_residual(Dims d, const float2* __restrict__ phi_in, const float* __r
   P.init(d, x0, y0);
   const float2 m = f64_to_df(m_dev[0]);
   float2 wp[K], wc[K];
-  float r2 = 0.f, ps = 0.f;
+  float2 nphi[K], fq[K];
+  float ne[K];
+  float r2 = 0.f;
+  DfAcc ps{0.f, 0.f};
 #pragma unroll
-  for (int k = 0; k < K; ++k) wp[k] = wc[k] = make_float2(0.f, 0.f);
+  for (int k = 0; k < K; ++k) wp[k] = wc[k] = fq[k] = make_float2(0.f, 0.f);
   const int tb = z0 - 1, te = zend;
+  auto load = [&](int t) {
+    const long long base = (long long)wrapmod(t, d.nz) * pst;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const bool v = P.vmask >> k & 1u;
+      nphi[k] = v ? phi_in[base + P.goff[k]] : make_float2(0.f, 0.f);
+      ne[k] = v ? __ldg(e + base + P.goff[k]) : 0.f;
+    }
+  };
+  load(tb);
   for (int t = tb; t <= te; ++t) {
     const int cur = (t - tb) & 1, prv = cur ^ 1;
     const long long base = (long long)wrapmod(t, d.nz) * pst;
     float2 pn[K];
+    float2 fcur[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      pn[k] = make_float2(0.f, 0.f);
+      pn[k] = df_add_f(nphi[k], ne[k]);
+      fcur[k] = fq[k];
+    }
+    if (t < te) {
+      load(t + 1);
+      // F of the plane whose residual the next iteration computes (plane t)
+      if (t >= z0 && t < zend) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) fq[k] = (P.tmask >> k & 1u) ? F[base + P.goff[k]] : make_float2(0.f, 0.f);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
       if (P.vmask >> k & 1u) {
-        const long long gi = base + P.goff[k];
-        pn[k] = df_add_f(phi_in[gi], __ldg(e + gi));
         sp[cur][PAD + tid + k * NT] = pn[k];
         if ((P.tmask >> k & 1u) && t >= z0 && t < zend) {
-          phi_out[gi] = pn[k];
-          ps += pn[k].x;
+          phi_out[base + P.goff[k]] = pn[k];
+          ps.add(pn[k].x);
+          ps.c += pn[k].y;
         }
       }
     }
@@ -361,9 +466,9 @@ k_df_update_residual(Dims d, const float2* __restrict__ phi_in, const float* __r
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         if (P.tmask >> k & 1u) {
-          const int p = (P.vmask >> k & 1u) ? tid + k * NT : 0;  // invalid slots read in bounds
+          const int p = tid + k * NT;
           const long long gi = pbase + P.goff[k];
-          const float rv = df_resid(wc[k], src[p - 1], src[p + 1], src[p - WX], src[p + WX], wp[k], pn[k], F[gi], m);
+          const float rv = df_resid(wc[k], src[p - 1], src[p + 1], src[p - WX], src[p + WX], wp[k], pn[k], fcur[k], m);
           r_out[gi] = rv;
           r2 += rv * rv;
         }
@@ -377,7 +482,7 @@ k_df_update_residual(Dims d, const float2* __restrict__ phi_in, const float* __r
     __syncthreads();
   }
   const double b2 = block_sum_f(r2, shr);
-  const double bs = block_sum_f(ps, shr);
+  const double bs = block_sum_acc(ps, shr);
   if (tid == 0) {
     const int bid = block_linear_id();
     pr2[bid] = b2;
@@ -395,7 +500,7 @@ size_t down_smem() {
 }
 template <int V>
 size_t up_smem() {
-  return (size_t)V * 2 * Tile<UTX, UTY, V, UNT>::PLANE * sizeof(float);
+  return ((size_t)V * 2 * Tile<UTX, UTY, V, UNT>::PLANE + 3 * CoarseTile<UTX, UTY, V>::CN) * sizeof(float);
 }
 
 Coef make_coef(const double* c1, const double* c2, int v) {
@@ -444,12 +549,21 @@ cudaError_t up_v(cudaStream_t st, Dims d, const float* e_in, const float* ec, co
 bool fused_degree_supported(int degree) { return degree >= 1 && degree <= 4; }
 
 int fused_zchunk(Dims d) {
-  // z chunk: enough CTAs to fill the GPU several times while keeping the
-  // redundant warm-up planes of each chunk small.
+  // z chunk minimising (waves of CTAs) x (iterations per CTA), one CTA per SM:
+  // long chunks amortise the 2V+2 warm-up planes, short ones fill the 152 SMs.
   const long long tiles = (long long)((d.nx + DTX - 1) / DTX) * ((d.ny + DTY - 1) / DTY);
-  int zc = d.nz;
-  while (zc > 16 && tiles * ((d.nz + zc - 1) / zc) < 4 * 152) zc /= 2;
-  return zc;
+  int best = d.nz;
+  long long best_cost = -1;
+  for (int zc = d.nz; zc >= 8; zc = (zc + 1) / 2) {
+    const long long ctas = tiles * ((d.nz + zc - 1) / zc);
+    const long long cost = ((ctas + 151) / 152) * (zc + 8);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = zc;
+    }
+    if (zc == 8) break;
+  }
+  return best;
 }
 
 cudaError_t launch_down_fused(cudaStream_t st, int degree, Dims d, const float* r, float* e, float* rc, float inv_h2,
@@ -478,14 +592,23 @@ cudaError_t launch_up_fused(cudaStream_t st, int degree, Dims d, const float* e_
   return cudaErrorInvalidValue;
 }
 
+// z chunk of the double-float update: at least four waves of three CTAs per SM, so
+// that enough loads are in flight; the warm-up costs one plane per chunk.
+int df_zchunk(Dims d) {
+  const long long tiles = (long long)((d.nx + FTX - 1) / FTX) * ((d.ny + FTY - 1) / FTY);
+  int zc = d.nz;
+  while (zc > 16 && tiles * ((d.nz + zc - 1) / zc) < 4 * 3 * 152) zc = (zc + 1) / 2;
+  return zc;
+}
+
 long long df_update_residual_partials(Dims d) {
-  const int zc = fused_zchunk(d);
+  const int zc = df_zchunk(d);
   return (long long)((d.nx + FTX - 1) / FTX) * ((d.ny + FTY - 1) / FTY) * ((d.nz + zc - 1) / zc);
 }
 
 cudaError_t launch_df_update_residual(cudaStream_t st, Dims d, const float2* phi_in, const float* e, const float2* F,
                                       const double* m_dev, float2* phi_out, float* r_out, double* pr2, double* psum) {
-  const int zc = fused_zchunk(d);
+  const int zc = df_zchunk(d);
   const dim3 grid((d.nx + FTX - 1) / FTX, (d.ny + FTY - 1) / FTY, (d.nz + zc - 1) / zc);
   k_df_update_residual<FTX, FTY, FNT><<<grid, FNT, 0, st>>>(d, phi_in, e, F, m_dev, phi_out, r_out, pr2, psum, zc);
   note_launch();

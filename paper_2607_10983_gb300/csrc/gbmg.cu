@@ -201,7 +201,11 @@ extern "C" gbmg_status mg_setup(gbmg_ctx** out, int nx, int ny, int nz, int leve
   gbmg_default_opts(&o);
   if (opts) o = *opts;
   if (smoother_degree > 0) o.degree = smoother_degree;
-  if (o.op != GBMG_OP_FLAT7) return fail(GBMG_ERR_INVALID_ARG, "mg_setup: unsupported operator");
+  if (o.op != GBMG_OP_FLAT7 && o.op != GBMG_OP_CURV19) return fail(GBMG_ERR_INVALID_ARG, "mg_setup: unsupported operator");
+  if (o.op == GBMG_OP_CURV19 && o.smoother != GBMG_SMOOTH_JACOBI)
+    return fail(GBMG_ERR_INVALID_ARG, "mg_setup: the curvilinear operator uses the weighted-Jacobi smoother");
+  if (o.op == GBMG_OP_CURV19 && o.prec != GBMG_MIXED)
+    return fail(GBMG_ERR_INVALID_ARG, "mg_setup: the curvilinear operator runs in mixed precision");
   if (o.prec != GBMG_FP64 && o.prec != GBMG_MIXED) return fail(GBMG_ERR_INVALID_ARG, "mg_setup: bad precision");
   if (o.smoother != GBMG_SMOOTH_CHEBYSHEV && o.smoother != GBMG_SMOOTH_JACOBI)
     return fail(GBMG_ERR_INVALID_ARG, "mg_setup: bad smoother");
@@ -209,8 +213,10 @@ extern "C" gbmg_status mg_setup(gbmg_ctx** out, int nx, int ny, int nz, int leve
   if (!(o.alpha > 1.0)) return fail(GBMG_ERR_INVALID_ARG, "mg_setup: alpha must be > 1");
   if (o.nu1 < 0 || o.nu2 < 0 || o.nu1 > 64 || o.nu2 > 64) return fail(GBMG_ERR_INVALID_ARG, "mg_setup: bad nu1/nu2");
   if (!(o.omega > 0.0 && o.omega < 2.0)) return fail(GBMG_ERR_INVALID_ARG, "mg_setup: omega must be in (0, 2)");
-  if (o.fused && !(o.prec == GBMG_MIXED && o.smoother == GBMG_SMOOTH_CHEBYSHEV && fused_degree_supported(o.degree)))
+  if (o.fused && !(o.op == GBMG_OP_FLAT7 && o.prec == GBMG_MIXED && o.smoother == GBMG_SMOOTH_CHEBYSHEV &&
+                   fused_degree_supported(o.degree)))
     o.fused = 0;
+  const bool curv = o.op == GBMG_OP_CURV19;
 
   std::vector<Dims> dims = level_dims(nx, ny, nz, levels);
   const Dims dc = dims.back();
@@ -228,6 +234,7 @@ extern "C" gbmg_status mg_setup(gbmg_ctx** out, int nx, int ny, int nz, int leve
   c->o = o;
   c->L = (int)dims.size();
   c->nc = (int)nc;
+  c->fused_all = o.fused == 2;
   chebyshev_schedule(o.degree, o.alpha, c->cc1, c->cc2);
 
   const size_t esz = o.prec == GBMG_FP64 ? sizeof(double) : sizeof(float);
@@ -243,9 +250,14 @@ extern "C" gbmg_status mg_setup(gbmg_ctx** out, int nx, int ny, int nz, int leve
     size_t r, e, e2, dv, t;
   };
   std::vector<Offs> lo(dims.size());
+  std::vector<size_t> lpsi(dims.size()), lcoef(dims.size());
   for (size_t l = 0; l < dims.size(); ++l) {
     const size_t b = (size_t)ncell(dims[l]) * esz;
     lo[l] = Offs{take(b), take(b), take(b), take(b), take(b)};
+    if (curv) {
+      lpsi[l] = take((size_t)ncell(dims[l]) * sizeof(double));
+      lcoef[l] = take((size_t)ncell(dims[l]) * 7 * sizeof(float));
+    }
   }
   size_t oF = 0, oP = 0, oP2 = 0, oR = 0;
   if (o.prec == GBMG_MIXED) {
@@ -260,6 +272,12 @@ extern "C" gbmg_status mg_setup(gbmg_ctx** out, int nx, int ny, int nz, int leve
   const size_t oScal = take(64 * sizeof(double));
   const size_t oG64 = take((size_t)nc * nc * sizeof(double));
   const size_t oG32 = take((size_t)nc * nc * sizeof(float));
+  size_t oG64T = 0, oG32T = 0, oDense = 0;
+  if (curv) {
+    oG64T = take((size_t)nc * nc * sizeof(double));
+    oG32T = take((size_t)nc * nc * sizeof(float));
+    oDense = take((size_t)nc * nc * sizeof(double));
+  }
   c->arena_bytes = off;
   e = cudaMalloc((void**)&c->arena, off);
   if (e != cudaSuccess) {
@@ -282,6 +300,19 @@ extern "C" gbmg_status mg_setup(gbmg_ctx** out, int nx, int ny, int nz, int leve
     L.e2 = a + lo[l].e2;
     L.dv = a + lo[l].dv;
     L.t = a + lo[l].t;
+    if (curv) {
+      L.psi = (double*)(a + lpsi[l]);
+      float* cb = (float*)(a + lcoef[l]);
+      const long long nl = ncell(dims[l]);
+      L.cc.J = cb;
+      for (int k = 0; k < 6; ++k) L.cc.B[k] = cb + (k + 1) * nl;
+      L.cc.h2 = (float)(L.h * L.h);
+    }
+  }
+  if (curv) {
+    c->G64T = (double*)(a + oG64T);
+    c->G32T = (float*)(a + oG32T);
+    c->dense = (double*)(a + oDense);
   }
   if (o.prec == GBMG_MIXED) {
     c->F_df = (float2*)(a + oF);
@@ -295,6 +326,17 @@ extern "C" gbmg_status mg_setup(gbmg_ctx** out, int nx, int ny, int nz, int leve
   c->G64 = (double*)(a + oG64);
   c->G32 = (float*)(a + oG32);
 
+  if (curv) {
+    // the coarsest pseudo-inverse depends on the geometry: built by mg_set_geometry
+    e = cudaMemset(c->scal, 0, 64 * sizeof(double));
+    if (e != cudaSuccess) {
+      delete c;
+      return cuda_fail(e, "mg_setup: memset");
+    }
+    std::memset(&c->last, 0, sizeof(c->last));
+    *out = c;
+    return GBMG_OK;
+  }
   // coarsest-level pseudo-inverse of the rediscretised 7-point operator
   std::vector<double> A = dense_flat(dc, c->lv.back().h), G;
   std::vector<double> w((size_t)nc, 1.0);

@@ -9,51 +9,7 @@
 
 using namespace gbmg;
 
-#define TRY(call)                                  \
-  do {                                             \
-    cudaError_t e_ = (call);                       \
-    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
-  } while (0)
-#define TRYS(call)                  \
-  do {                              \
-    gbmg_status s_ = (call);        \
-    if (s_ != GBMG_OK) return s_;   \
-  } while (0)
-
 namespace {
-
-struct DeviceGuard {
-  int prev = -1;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
-    else prev = -1;
-  }
-  ~DeviceGuard() {
-    if (prev >= 0) cudaSetDevice(prev);
-  }
-};
-
-// Brackets one launch with CUDA events on the context's stream when its kernel
-// family is being timed (mg_profile_begin); no effect otherwise.
-struct ProfScope {
-  gbmg_ctx* c;
-  int f;
-  bool on = false;
-  ProfScope(gbmg_ctx* ctx, int family) : c(ctx), f(family) {
-    if (family <= GBMG_PROF_OFF || family > 7 || !(c->prof_mask >> family & 1)) return;
-    std::vector<cudaEvent_t>& ev = c->prof_ev[f];
-    const size_t need = 2 * (size_t)c->prof_n[f] + 2;
-    while (ev.size() < need) {
-      cudaEvent_t e;
-      if (cudaEventCreate(&e) != cudaSuccess) return;
-      ev.push_back(e);
-    }
-    on = cudaEventRecord(ev[2 * c->prof_n[f]], c->stream) == cudaSuccess;
-  }
-  ~ProfScope() {
-    if (on && cudaEventRecord(c->prof_ev[f][2 * c->prof_n[f] + 1], c->stream) == cudaSuccess) c->prof_n[f] += 1;
-  }
-};
 
 template <typename T>
 const T* coarse_G(const gbmg_ctx* c);
@@ -110,10 +66,13 @@ gbmg_status vcycle_unfused(gbmg_ctx* c, int l, T*& e, T*& eo, const T* r) {
   return GBMG_OK;
 }
 
-// Levels at least this large in every direction use the temporally blocked kernels.
+// Levels of at least 2^21 cells (128^3) use the temporally blocked kernels; below
+// that a level visit is latency-bound and the one-kernel-per-operation chain is
+// faster (a blocked CTA streams its planes one after another).
 bool level_fused(const gbmg_ctx* c, int l) {
   const Dims d = c->lv[l].d;
-  return c->o.fused && l < c->L - 1 && d.nx >= 16 && d.ny >= 16 && d.nz >= 16;
+  return c->o.fused && l < c->L - 1 && d.nx >= 16 && d.ny >= 16 && d.nz >= 16 &&
+         (ncell(d) >= (1ll << 21) || c->fused_all);
 }
 
 // V-cycle in FP32 with the temporally blocked kernels on large levels (one launch per
@@ -147,57 +106,6 @@ gbmg_status vcycle_fused(gbmg_ctx* c, int l, float*& e, const float* r) {
   e = (float*)L.e2;
   return GBMG_OK;
 }
-
-// Reads ||F||^2 and ||r||^2 back and returns the relative residual.
-gbmg_status read_rel(gbmg_ctx* c, double& rel) {
-  TRY(cudaMemcpyAsync(c->host_scal, c->scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  TRY(cudaStreamSynchronize(c->stream));
-  const double f2 = c->host_scal[S_F2], r2 = c->host_scal[S_R2];
-  rel = f2 > 0.0 ? std::sqrt(r2 / f2) : std::sqrt(r2);
-  return GBMG_OK;
-}
-
-// Convergence bookkeeping shared by the solve drivers: stop at tol, at max_vcycles,
-// on a non-finite residual, or when the residual grew tenfold over two cycles.
-struct Monitor {
-  gbmg_stats& st;
-  double tol;
-  int maxv;
-  std::vector<double> hist;  // hist[k] = relative residual after k cycles
-  Monitor(gbmg_stats& s, double t, int m) : st(s), tol(t), maxv(m) {}
-  void start(double rel) {
-    st.rel_res0 = rel;
-    st.rel_res = rel;
-    st.cycles = 0;
-    st.status = GBMG_OK;
-    hist.assign(1, rel);
-  }
-  bool done() {
-    if (!std::isfinite(st.rel_res)) {
-      st.status = GBMG_ERR_NONFINITE;
-      return true;
-    }
-    if (st.rel_res <= tol) return true;
-    if (st.cycles >= maxv) {
-      st.status = GBMG_ERR_NOT_CONVERGED;
-      return true;
-    }
-    return false;
-  }
-  // record the residual after one more cycle; true if the solve must stop (diverged)
-  bool record(double rel) {
-    if (st.cycles < 64) st.res_hist[st.cycles] = rel;
-    st.cycles += 1;
-    st.rel_res = rel;
-    hist.push_back(rel);
-    const size_t k = hist.size() - 1;
-    if (k >= 2 && std::isfinite(rel) && rel > 10.0 * hist[k - 2]) {
-      st.status = GBMG_ERR_DIVERGED;
-      return true;
-    }
-    return false;
-  }
-};
 
 gbmg_status solve_fp64(gbmg_ctx* c, const double* F, double* phi, double tol, int maxv, gbmg_stats& st) {
   const Level& L0 = c->lv[0];
@@ -323,17 +231,28 @@ gbmg_status comp_scratch(gbmg_ctx* c, int dtype, void** out) {
 
 // ------------------------------------------------------------------ solve
 
-extern "C" gbmg_status mg_solve(gbmg_ctx* ctx, const double* source_dev, const float* coeffs_dev,
+extern "C" gbmg_status mg_solve(gbmg_ctx* ctx, const double* source_dev, const double* coeffs_dev,
                                 double* phi_inout_dev, double tol, int max_vcycles, gbmg_stats* stats) {
   g_last_error.clear();
   if (!ctx || !source_dev || !phi_inout_dev) return fail(GBMG_ERR_INVALID_ARG, "mg_solve: NULL argument");
-  if (coeffs_dev) return fail(GBMG_ERR_INVALID_ARG, "mg_solve: coeffs must be NULL for the flat operator");
+  if (coeffs_dev && ctx->o.op != GBMG_OP_CURV19)
+    return fail(GBMG_ERR_INVALID_ARG, "mg_solve: coeffs must be NULL for the flat operator");
   if (!(tol >= 0.0)) return fail(GBMG_ERR_INVALID_ARG, "mg_solve: tol must be >= 0");
   DeviceGuard g(ctx->device);
   gbmg_stats st;
   std::memset(&st, 0, sizeof(st));
-  gbmg_status s = ctx->o.prec == GBMG_FP64 ? solve_fp64(ctx, source_dev, phi_inout_dev, tol, max_vcycles, st)
-                                           : solve_mixed(ctx, source_dev, phi_inout_dev, tol, max_vcycles, st);
+  gbmg_status s;
+  if (ctx->o.op == GBMG_OP_CURV19) {
+    if (coeffs_dev) {
+      s = mg_set_geometry(ctx, coeffs_dev);
+      if (s != GBMG_OK) return s;
+    }
+    if (!ctx->geom_ready) return fail(GBMG_ERR_STATE, "mg_solve: curvilinear solve before mg_set_geometry");
+    s = curv_solve(ctx, source_dev, phi_inout_dev, tol, max_vcycles, st);
+  } else {
+    s = ctx->o.prec == GBMG_FP64 ? solve_fp64(ctx, source_dev, phi_inout_dev, tol, max_vcycles, st)
+                                 : solve_mixed(ctx, source_dev, phi_inout_dev, tol, max_vcycles, st);
+  }
   if (s != GBMG_OK) return s;
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(e, "mg_solve");

@@ -1,10 +1,12 @@
 // Internal definition of the solver context shared by the host translation units.
 #pragma once
+#include <cmath>
 #include <string>
 #include <vector>
 
 #include "common.cuh"
 #include "gbmg.h"
+#include "kernels.h"
 
 namespace gbmg {
 
@@ -17,6 +19,8 @@ struct Level {
   void* e2;
   void* dv;       // Chebyshev direction
   void* t;        // residual scratch
+  double* psi = nullptr;  // curvilinear: deformation potential restricted to this level (FP64)
+  CurvCoef cc{};          // curvilinear: J and B of this level (FP32)
 };
 
 gbmg_status fail(gbmg_status s, const std::string& msg);
@@ -24,6 +28,8 @@ gbmg_status cuda_fail(cudaError_t e, const char* what);
 extern thread_local std::string g_last_error;
 
 std::vector<Dims> level_dims(int nx, int ny, int nz, int levels);
+// curvilinear / adjoint drivers (curv_solve.cu)
+gbmg_status curv_solve(gbmg_ctx* c, const double* F, double* phi, double tol, int maxv, gbmg_stats& st);
 bool dense_pinv(int n, const std::vector<double>& Lm, const std::vector<double>& w, std::vector<double>& G);
 std::vector<double> dense_flat(Dims d, double h);
 void chebyshev_schedule(int degree, double alpha, std::vector<double>& c1, std::vector<double>& c2);
@@ -52,6 +58,13 @@ struct gbmg_ctx {
   int nc = 0;                   // cells on the coarsest level
   double* G64 = nullptr;        // coarsest pseudo-inverse, row-major nc x nc
   float* G32 = nullptr;
+  double* G64T = nullptr;       // curvilinear: pseudo-inverse of the transposed-solve operator
+  float* G32T = nullptr;
+  double* dense = nullptr;      // curvilinear: nc x nc scratch for the coarsest operator
+  bool geom_ready = false;      // curvilinear: mg_set_geometry has run
+  bool fused_all = false;       // testing: blocked kernels on every level of at least 16^3
+  double* adj_S = nullptr;      // adjoint scratch (6 finest fields), allocated on first use
+  double* adj_lam = nullptr;    // adjoint scratch (1 finest field)
   float2* F_df = nullptr;       // mixed precision: source as double-float
   float2* phi_df = nullptr;     // mixed precision: potential as double-float
   float2* phi_df2 = nullptr;    // mixed precision: second potential buffer (fused update)
@@ -71,3 +84,104 @@ struct gbmg_ctx {
   double* stage_phi = nullptr;
   ~gbmg_ctx();
 };
+
+namespace gbmg {
+
+#define TRY(call)                                  \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+#define TRYS(call)                  \
+  do {                              \
+    gbmg_status s_ = (call);        \
+    if (s_ != GBMG_OK) return s_;   \
+  } while (0)
+
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+// Brackets one launch with CUDA events on the context's stream when its kernel
+// family is being timed (mg_profile_begin); no effect otherwise.
+struct ProfScope {
+  gbmg_ctx* c;
+  int f;
+  bool on = false;
+  ProfScope(gbmg_ctx* ctx, int family) : c(ctx), f(family) {
+    if (family <= GBMG_PROF_OFF || family > 7 || !(c->prof_mask >> family & 1)) return;
+    std::vector<cudaEvent_t>& ev = c->prof_ev[f];
+    const size_t need = 2 * (size_t)c->prof_n[f] + 2;
+    while (ev.size() < need) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return;
+      ev.push_back(e);
+    }
+    on = cudaEventRecord(ev[2 * c->prof_n[f]], c->stream) == cudaSuccess;
+  }
+  ~ProfScope() {
+    if (on && cudaEventRecord(c->prof_ev[f][2 * c->prof_n[f] + 1], c->stream) == cudaSuccess) c->prof_n[f] += 1;
+  }
+};
+
+// Reads ||F||^2 and ||r||^2 back and returns the relative residual.
+inline gbmg_status read_rel(gbmg_ctx* c, double& rel) {
+  TRY(cudaMemcpyAsync(c->host_scal, c->scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  TRY(cudaStreamSynchronize(c->stream));
+  const double f2 = c->host_scal[S_F2], r2 = c->host_scal[S_R2];
+  rel = f2 > 0.0 ? std::sqrt(r2 / f2) : std::sqrt(r2);
+  return GBMG_OK;
+}
+
+// Convergence bookkeeping shared by the solve drivers: stop at tol, at max_vcycles,
+// on a non-finite residual, or when the residual grew tenfold over two cycles.
+struct Monitor {
+  gbmg_stats& st;
+  double tol;
+  int maxv;
+  std::vector<double> hist;  // hist[k] = relative residual after k cycles
+  Monitor(gbmg_stats& s, double t, int m) : st(s), tol(t), maxv(m) {}
+  void start(double rel) {
+    st.rel_res0 = rel;
+    st.rel_res = rel;
+    st.cycles = 0;
+    st.status = GBMG_OK;
+    hist.assign(1, rel);
+  }
+  bool done() {
+    if (!std::isfinite(st.rel_res)) {
+      st.status = GBMG_ERR_NONFINITE;
+      return true;
+    }
+    if (st.rel_res <= tol) return true;
+    if (st.cycles >= maxv) {
+      st.status = GBMG_ERR_NOT_CONVERGED;
+      return true;
+    }
+    return false;
+  }
+  // record the residual after one more cycle; true if the solve must stop (diverged)
+  bool record(double rel) {
+    if (st.cycles < 64) st.res_hist[st.cycles] = rel;
+    st.cycles += 1;
+    st.rel_res = rel;
+    hist.push_back(rel);
+    const size_t k = hist.size() - 1;
+    if (k >= 2 && std::isfinite(rel) && rel > 10.0 * hist[k - 2]) {
+      st.status = GBMG_ERR_DIVERGED;
+      return true;
+    }
+    return false;
+  }
+};
+
+
+}  // namespace gbmg

@@ -165,7 +165,7 @@ def test_fixed_cycle_iterates_match_oracle(gb):
     assert np.linalg.norm(phim.cpu().numpy() - ref) / np.linalg.norm(ref) < 1e-5
 
 
-@pytest.mark.parametrize("fused", [False, True])
+@pytest.mark.parametrize("fused", [0, 2])
 @pytest.mark.parametrize("shape", [(32, 32, 32), (64, 64, 64), (16, 8, 32), (48, 48, 48)])
 def test_mixed_solve_to_1e6(gb, shape, fused):
     F = grf(shape, 15)
@@ -232,7 +232,7 @@ def test_error_statuses(gb):
 def test_fused_vcycle_bit_identical_to_unfused(gb, shape, degree):
     # the temporally blocked kernels round exactly like the one-kernel-per-operation chain
     r = to_dev(grf(shape, 19), torch.float32)
-    a = gb.Solver(shape, prec="mixed", fused=True, degree=degree).vcycle(r)
+    a = gb.Solver(shape, prec="mixed", fused=2, degree=degree).vcycle(r)
     b = gb.Solver(shape, prec="mixed", fused=False, degree=degree).vcycle(r)
     torch.cuda.synchronize()
     assert torch.equal(a, b)
@@ -241,7 +241,7 @@ def test_fused_vcycle_bit_identical_to_unfused(gb, shape, degree):
 @pytest.mark.parametrize("shape", [(64, 64, 64), (32, 48, 64)])
 def test_fused_solve_iterates_match_unfused(gb, shape):
     F = to_dev(grf(shape, 20))
-    pa, sa = gb.Solver(shape, prec="mixed", fused=True).solve(F, tol=0.0, max_vcycles=4)
+    pa, sa = gb.Solver(shape, prec="mixed", fused=2).solve(F, tol=0.0, max_vcycles=4)
     pb, sb = gb.Solver(shape, prec="mixed", fused=False).solve(F, tol=0.0, max_vcycles=4)
     assert sa.cycles == sb.cycles == 4
     diff = (pa - pb).abs().max().item()
