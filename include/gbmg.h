@@ -236,6 +236,31 @@ gbmg_status mg_df_to_f64(gbmg_ctx* ctx, long long n, const float* df_dev, double
 gbmg_status mg_df_residual(gbmg_ctx* ctx, const float* F_df_dev, double m, const float* phi_df_dev,
                            float* r_dev);
 
+/* ---------------------------------------------------------------------------------
+ * Allocation-free call (the paper has no counterpart).  For callers that must not
+ * allocate device memory: a time-step loop that runs inside a fixed, pre-reserved
+ * memory budget, or code hosted by another framework whose allocator owns the
+ * device.  It needs no context and no mg_setup.
+ *
+ * Writes rel_out_dev[0] = ||F - m - A phi|| / ||F - m|| (a device double), with
+ * F = source_dev, phi = phi_dev (nx*ny*nz doubles on the current device),
+ * m = mean(F) and A the 7-point periodic Laplacian with unit spacing: the quantity
+ * mg_solve reports as rel_res0.  The residual is evaluated in double-float.
+ *
+ * Scratch: one fixed array of 2 * GBMG_NOALLOC_MAX_NZ + 8 doubles (about 64 KiB) in
+ * the library's own device memory, held by every GPU that loads the library until
+ * the process exits.  nz above GBMG_NOALLOC_MAX_NZ (or a side below 4) is rejected
+ * with GBMG_ERR_INVALID_ARG.  The first call on a device looks the array's address
+ * up on that device, with that device current; make that first call before any
+ * stream capture.  Every call overwrites the scratch entries it reads (nothing has
+ * to start at zero) and the array keeps the last call's contents; all calls share
+ * it, so calls that overlap on the GPU (unordered streams) race.  The work is
+ * queued on cuda_stream (NULL = legacy default stream); the call does not wait.
+ * No memory is allocated or freed. */
+#define GBMG_NOALLOC_MAX_NZ 4096
+gbmg_status mg_rel_residual_noalloc(int nx, int ny, int nz, const double* source_dev, const double* phi_dev,
+                                    double* rel_out_dev, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

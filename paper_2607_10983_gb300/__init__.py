@@ -100,6 +100,7 @@ _SIGS = {
     "mg_profile_read": (_S, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "mg_profile_end": (_S, [_P]),
     "mg_launch_count": (_LL, []),
+    "mg_rel_residual_noalloc": (_S, [_I, _I, _I, _P, _P, _P, _P]),
 }
 
 PROF = {"down0": 1, "up0": 2, "df0": 3, "smooth0": 4}
