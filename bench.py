@@ -322,6 +322,9 @@ def run_ours(args):
     if not args.no_extras and rank == 0:
         line["e2e"] = e2e_leg(args, solver, host_src)
         line["baselines"] = baseline_legs(args, F, dev)
+        del F
+        torch.cuda.empty_cache()
+        line["batched_48"] = batched_leg(args)
         line["cpu_baseline"] = oracle_sample(n, seq, args.tol)
     if rank == 0:
         print(json.dumps(line))
@@ -405,6 +408,58 @@ def baseline_legs(args, F, dev):
         out[name] = {"solves_per_s": 3 / (ev0.elapsed_time(ev1) / 1000.0),
                      "note": "rfftn, divide by the 7-point symbol, irfftn; inputs resident"}
         del srcs
+    return out
+
+
+def batched_leg(args):
+    """48 independent cold solves, 16 each at 64^3, 96^3 and 128^3 (seeds 1000..1047), tol 1e-6:
+    one persistent launch for all vs the same solves one at a time."""
+    import numpy as np
+    import torch
+
+    import paper_2607_10983_gb300 as gb
+    from synth import grf
+    shapes = [(64,) * 3] * 16 + [(96,) * 3] * 16 + [(128,) * 3] * 16
+    F = [torch.from_numpy(grf(s, 1000 + i)).cuda() for i, s in enumerate(shapes)]
+    phis = [torch.zeros_like(f) for f in F]
+    batch = gb.Batch(shapes, degree=args.degree)
+    blocks = batch.autotune(F, phis, tol=args.tol, max_vcycles=args.max_vcycles)
+    reps = 3
+    lat, total = [], 0.0
+    for _ in range(reps):
+        for p in phis:
+            p.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        stats, times = batch.solve(F, phis, tol=args.tol, max_vcycles=args.max_vcycles)
+        total += time.perf_counter() - t0
+        lat += times
+        if any(st.status != 0 for st in stats):
+            raise RuntimeError("batched solve did not converge")
+    out = {"batched": {"solves_per_s": len(shapes) * reps / total, "p50_ms": float(np.percentile(lat, 50)),
+                       "p99_ms": float(np.percentile(lat, 99)), "blocks": blocks,
+                       "cycles_per_solve": float(np.mean([st.cycles for st in stats]))}}
+    batch.close()
+    solvers = {s: gb.Solver(s, degree=args.degree) for s in set(shapes)}
+    seq_lat = []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for f, s in zip(F, shapes):          # warm-up
+        solvers[s].solve(f, torch.zeros_like(f), tol=args.tol, max_vcycles=args.max_vcycles)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        for f, s in zip(F, shapes):
+            ph = torch.zeros_like(f)
+            ev0.record()
+            solvers[s].solve(f, ph, tol=args.tol, max_vcycles=args.max_vcycles)
+            ev1.record()
+            ev1.synchronize()
+            seq_lat.append(ev0.elapsed_time(ev1))
+    dt = time.perf_counter() - t0
+    out["one_at_a_time"] = {"solves_per_s": len(shapes) * reps / dt, "p50_ms": float(np.percentile(seq_lat, 50)),
+                            "p99_ms": float(np.percentile(seq_lat, 99))}
+    out["workload"] = "48 cold solves to 1e-6: 16 x 64^3, 16 x 96^3, 16 x 128^3, GRF P(k)~k^-2, seeds 1000..1047"
+    for s in solvers.values():
+        s.close()
     return out
 
 

@@ -71,7 +71,7 @@ typedef struct {
   int nu1, nu2;  /* Jacobi sweeps before / after the coarse correction (>= 0)      */
   double omega;  /* Jacobi weight                                                  */
   int fused;     /* temporally blocked level kernels (GBMG_MIXED + Chebyshev):       */
-                 /* 1: on levels of at least 128^3 cells, 2: on every level of at  */
+                 /* 1: on levels of at least 2^23 cells, 2: on every level of at   */
                  /* least 16^3 (results are identical), 0: one kernel per operation */
 } gbmg_opts;
 
@@ -153,6 +153,35 @@ int mg_num_levels(const gbmg_ctx* ctx);
 gbmg_status mg_level_dims(const gbmg_ctx* ctx, int level, int* nx, int* ny, int* nz);
 
 /* ---------------------------------------------------------------------------------
+ * Batched solves: many independent flat problems, sizes may differ, solved in ONE
+ * persistent cooperative kernel launch (each operation of the V-cycle is a grid-wide
+ * phase over every active problem; converged problems drop out).  Each problem uses
+ * the hierarchy of its own context, which must be flat, GBMG_MIXED, Chebyshev,
+ * fused = 0, with at least two levels; all contexts share the smoother settings and
+ * the device.  A context must not be used by another call while its batch solves.
+ * Iterates equal those of mg_solve on each context up to the rounding of the means.
+ * --------------------------------------------------------------------------------- */
+typedef struct gbmg_batch gbmg_batch;
+
+/* Build the batch tables for ctxs[0..count-1] (device tables allocated here). */
+gbmg_status mg_batch_create(gbmg_batch** out, gbmg_ctx* const* ctxs, int count, void* cuda_stream);
+void mg_batch_destroy(gbmg_batch* batch);
+/* Persistent grid size in blocks (default and maximum: every block resident). */
+gbmg_status mg_batch_set_blocks(gbmg_batch* batch, int blocks);
+/* Time one solve with each candidate grid size (1..max blocks per SM times the SM
+ * count) and keep the fastest; fields as for mg_batch_solve (phi is overwritten).
+ * *blocks_out (nullable) receives the choice. */
+gbmg_status mg_batch_autotune(gbmg_batch* batch, const double* const* source_dev, double* const* phi_dev,
+                              double tol, int max_vcycles, int* blocks_out);
+/* Solve every problem: source_dev[i] / phi_dev[i] as for mg_solve on ctxs[i] (phi is
+ * the initial guess in and the solution out).  Waits for the stream.  stats (array of
+ * count, nullable) per problem; times_ms (array of count, nullable) receives each
+ * problem's completion time after the launch started, from the GPU clock.  Returns
+ * GBMG_OK if every problem converged, else the first problem's failure status. */
+gbmg_status mg_batch_solve(gbmg_batch* batch, const double* const* source_dev, double* const* phi_dev, double tol,
+                           int max_vcycles, gbmg_stats* stats, double* times_ms);
+
+/* ---------------------------------------------------------------------------------
  * Measurement.  While a kernel family is being timed, every launch of it is
  * bracketed by CUDA events on the context's stream (no extra synchronisation).
  * --------------------------------------------------------------------------------- */
@@ -226,6 +255,15 @@ gbmg_status mg_curv_geometry(gbmg_ctx* ctx, int level, float* J_dev, float* B_de
 /* One FP32 curvilinear V-cycle (weighted Jacobi nu1/nu2) on L e = r (transpose 0) or on
  * the transposed-solve operator M^T / J (transpose 1), from e = 0. */
 gbmg_status mg_curv_vcycle(gbmg_ctx* ctx, int transpose, const float* r_dev, float* e_dev);
+
+/* Finite-difference gradient on the finest level, spacing 1, periodic: order 4 is the
+ * one-exchange fourth-order stencil (-u_{i+2} + 8u_{i+1} - 8u_{i-1} + u_{i-2})/12 of
+ * the force evaluation (Sec. 3.4), order 2 the central difference (Sec. 4.1).
+ * transpose 0: in = u (n doubles), out = grad u (3n doubles, component-major x, y, z);
+ * transpose 1: in = w (3n floats, component-major), out = grad^T w (n doubles). */
+gbmg_status mg_grad(gbmg_ctx* ctx, int order, int transpose, const void* in_dev, double* out_dev);
+/* out_dev[0] = sum over cells and components of w . grad u (u n doubles, w 3n floats). */
+gbmg_status mg_grad_dot(gbmg_ctx* ctx, int order, const double* u_dev, const float* w_dev, double* out_dev);
 
 /* Double-float helpers of the mixed-precision path.  A double-float array stores each
  * value x as the float pair (hi, lo), hi = round(x), lo = round(x - hi): 2*n floats. */

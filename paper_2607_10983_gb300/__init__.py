@@ -101,6 +101,14 @@ _SIGS = {
     "mg_profile_end": (_S, [_P]),
     "mg_launch_count": (_LL, []),
     "mg_rel_residual_noalloc": (_S, [_I, _I, _I, _P, _P, _P, _P]),
+    "mg_grad": (_S, [_P, _I, _I, _P, _P]),
+    "mg_grad_dot": (_S, [_P, _I, _P, _P, _P]),
+    "mg_batch_create": (_S, [ctypes.POINTER(_P), ctypes.POINTER(_P), _I, _P]),
+    "mg_batch_destroy": (None, [_P]),
+    "mg_batch_set_blocks": (_S, [_P, _I]),
+    "mg_batch_autotune": (_S, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _D, _I, ctypes.POINTER(_I)]),
+    "mg_batch_solve": (_S, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _D, _I, ctypes.POINTER(_Stats),
+                            ctypes.POINTER(_D)]),
 }
 
 PROF = {"down0": 1, "up0": 2, "df0": 3, "smooth0": 4}
@@ -341,6 +349,22 @@ class Solver:
         _check(lib().mg_vcycle(self._c(), _ptr(r, self.work_dtype, self.shape), _ptr(out, self.work_dtype, self.shape)))
         return out
 
+    def grad(self, u: torch.Tensor, order: int = 4) -> torch.Tensor:
+        out = torch.empty((3,) + self.shape, dtype=torch.float64, device=u.device)
+        _check(lib().mg_grad(self._c(), order, 0, _ptr(u, torch.float64, self.shape), _ptr(out)))
+        return out
+
+    def grad_T(self, w: torch.Tensor, order: int = 4) -> torch.Tensor:
+        out = torch.empty(self.shape, dtype=torch.float64, device=w.device)
+        _check(lib().mg_grad(self._c(), order, 1, _ptr(w, torch.float32, (3,) + self.shape), _ptr(out)))
+        return out
+
+    def grad_dot(self, u: torch.Tensor, w: torch.Tensor, order: int = 4) -> torch.Tensor:
+        out = torch.empty(1, dtype=torch.float64, device=u.device)
+        _check(lib().mg_grad_dot(self._c(), order, _ptr(u, torch.float64, self.shape),
+                                 _ptr(w, torch.float32, (3,) + self.shape), _ptr(out)))
+        return out[0]
+
     def f64_to_df(self, x: torch.Tensor) -> torch.Tensor:
         out = torch.empty(x.shape + (2,), dtype=torch.float32, device=x.device)
         _check(lib().mg_f64_to_df(self._c(), x.numel(), _ptr(x, torch.float64), _ptr(out)))
@@ -355,6 +379,54 @@ class Solver:
         out = torch.empty(self.shape, dtype=torch.float32, device=F_df.device)
         _check(lib().mg_df_residual(self._c(), _ptr(F_df, torch.float32), float(m), _ptr(phi_df, torch.float32), _ptr(out)))
         return out
+
+
+class Batch:
+    """Independent flat solves of uneven sizes in one persistent launch (mg_batch_*)."""
+
+    def __init__(self, shapes, degree: int = 3, levels: int = 0):
+        self.solvers = [Solver(s, levels=levels, degree=degree, prec="mixed", fused=False) for s in shapes]
+        arr = (_P * len(self.solvers))(*[sv._ctx for sv in self.solvers])
+        b = _P()
+        _check(lib().mg_batch_create(ctypes.byref(b), arr, len(self.solvers),
+                                     torch.cuda.current_stream().cuda_stream))
+        self._b = b
+
+    def _ptrs(self, fields, dtype=torch.float64):
+        if len(fields) != len(self.solvers):
+            raise ValueError("one field per problem expected")
+        return (_P * len(fields))(*[_ptr(f, dtype, sv.shape) for f, sv in zip(fields, self.solvers)])
+
+    def autotune(self, sources, phis, tol=1e-6, max_vcycles=50) -> int:
+        blocks = _I()
+        _check(lib().mg_batch_autotune(self._b, self._ptrs(sources), self._ptrs(phis), float(tol), int(max_vcycles),
+                                       ctypes.byref(blocks)))
+        return blocks.value
+
+    def set_blocks(self, blocks: int):
+        _check(lib().mg_batch_set_blocks(self._b, int(blocks)))
+
+    def solve(self, sources, phis, tol=1e-6, max_vcycles=50):
+        """Solve all problems; phis are initial guesses in, solutions out.  Returns (stats, times_ms)."""
+        n = len(self.solvers)
+        st = (_Stats * n)()
+        times = (_D * n)()
+        s = lib().mg_batch_solve(self._b, self._ptrs(sources), self._ptrs(phis), float(tol), int(max_vcycles), st, times)
+        _check(s, allow_convergence=True)
+        return [Stats.from_c(x) for x in st], list(times)
+
+    def close(self):
+        if getattr(self, "_b", None):
+            lib().mg_batch_destroy(self._b)
+            self._b = None
+        for sv in getattr(self, "solvers", []):
+            sv.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---------------------------------------------------------------- autograd
@@ -396,3 +468,18 @@ class CurvMGSolve(torch.autograd.Function):
                                                    want_psi_bar=ctx.needs_input_grad[1], tol=ctx.tol,
                                                    max_vcycles=ctx.maxv)
         return d_bar, p_bar, None, None, None
+
+
+class GradDotLoss(torch.autograd.Function):
+    """loss = sum(w . grad_h phi) with the library's finite-difference gradient; d loss / d phi = grad_h^T w."""
+
+    @staticmethod
+    def forward(ctx, phi, w, solver, order):
+        ctx.solver, ctx.order = solver, order
+        ctx.save_for_backward(w)
+        return solver.grad_dot(phi.detach().contiguous(), w.contiguous(), order)
+
+    @staticmethod
+    def backward(ctx, g):
+        (w,) = ctx.saved_tensors
+        return g * ctx.solver.grad_T(w, ctx.order), None, None, None

@@ -1,0 +1,672 @@
+// Batched solves: many independent flat problems of uneven sizes solved in one
+// persistent cooperative launch (data-parallel form of the solve; the paper's
+// field-level-inference use case runs many such solves).
+//
+// Each problem keeps the hierarchy of its own context.  The kernel runs the whole
+// mixed-precision solve of every problem: prologue (double-float conversion, mean,
+// first residual), then V-cycles of the one-kernel-per-operation arithmetic (same
+// per-cell code, so each problem's iterates equal those of mg_solve with fused = 0),
+// each operation a grid-wide phase separated by grid.sync().  Work inside a phase is
+// split into chunks of CHUNK cells that belong to one problem, so per-problem sums
+// are deterministic (chunk partials summed in order).  A problem that has converged
+// (or failed) skips its chunks; the loop ends when none is active or max_vcycles is
+// reached.  Per-problem completion times come from %globaltimer.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "kernels.h"
+#include "solver.h"
+#include "stencil.cuh"
+
+namespace cg = cooperative_groups;
+using namespace gbmg;
+
+namespace {
+
+constexpr int BMAXL = 16;
+constexpr int CHUNK = 4096;
+constexpr int BT = 256;
+
+// per-problem scalars
+enum { P_MEAN = 0, P_F2 = 1, P_R2 = 2, P_REL = 3, P_PREV1 = 4, P_PREV2 = 5, P_MPHI = 6, P_N = 8 };
+// status codes inside the kernel: 0 = still iterating, -1 = converged, else a gbmg_status
+enum { ST_ACTIVE = 0, ST_CONVERGED = -1 };
+
+struct BProb {
+  int L, nc;
+  Dims d[BMAXL];
+  float* r[BMAXL];
+  float* ea[BMAXL];
+  float* eb[BMAXL];
+  float* dv[BMAXL];
+  float* t[BMAXL];
+  const float* G;
+  float2* F;
+  float2* phi;
+  const double* src;
+  double* out;
+  int c0, nch;  // first level-0 chunk and count
+};
+
+struct BDesc {
+  int count, maxL, degree, maxv;
+  double tol;
+  float c1[16];
+  double c2[16];
+  BProb* p;
+  // chunk tables per level: problem index and first cell
+  int* cprob[BMAXL];
+  long long* cstart[BMAXL];
+  int nchunk[BMAXL];
+  double* part0;  // per level-0 chunk partials
+  double* part1;
+  double* sc;     // count * P_N scalars
+  int* status;    // count: ST_ACTIVE, then a gbmg_status
+  int* cycles;    // count
+  double* hist;   // count * 64
+  double* rel0;   // count
+  unsigned long long* tdone;  // count, %globaltimer at completion
+  unsigned long long* tstart;
+  int* any_active;
+};
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void cell_xyz(Dims d, long long i, int& x, int& y, int& z) {
+  x = (int)(i % d.nx);
+  const long long q = i / d.nx;
+  y = (int)(q % d.ny);
+  z = (int)(q / d.ny);
+}
+
+template <typename V>
+__device__ __forceinline__ V nsum_at(const V* u, Dims d, int x, int y, int z, long long i) {
+  const long long sy = d.nx, sz = (long long)d.nx * d.ny;
+  const V xm = u[i + ((x == 0 ? d.nx - 1 : x - 1) - x)];
+  const V xp = u[i + ((x == d.nx - 1 ? 0 : x + 1) - x)];
+  const V ym = u[i + (long long)((y == 0 ? d.ny - 1 : y - 1) - y) * sy];
+  const V yp = u[i + (long long)((y == d.ny - 1 ? 0 : y + 1) - y) * sy];
+  const V zm = u[i + (long long)((z == 0 ? d.nz - 1 : z - 1) - z) * sz];
+  const V zp = u[i + (long long)((z == d.nz - 1 ? 0 : z + 1) - z) * sz];
+  return nbr_sum(xm, xp, ym, yp, zm, zp);
+}
+
+// Run `op(P, l, i)` over every cell of level l of every active problem for which
+// `want(P, l)` holds.
+template <typename Want, typename Op>
+__device__ __forceinline__ void phase(const BDesc& B, int l, Want want, Op op) {
+  for (int c = blockIdx.x; c < B.nchunk[l]; c += gridDim.x) {
+    const int pi = B.cprob[l][c];
+    if (B.status[pi] != ST_ACTIVE) continue;
+    const BProb& P = B.p[pi];
+    if (!want(P, l)) continue;
+    const long long s0 = B.cstart[l][c];
+    const long long n = ncell(P.d[l]);
+    const long long s1 = s0 + CHUNK < n ? s0 + CHUNK : n;
+    for (long long i = s0 + threadIdx.x; i < s1; i += blockDim.x) op(P, l, i);
+  }
+}
+
+// Level-0 phase with a per-chunk partial sum of the float returned by op.
+template <typename Op>
+__device__ __forceinline__ void phase0_sum(const BDesc& B, double* part, double* sh, bool all, Op op) {
+  for (int c = blockIdx.x; c < B.nchunk[0]; c += gridDim.x) {
+    const int pi = B.cprob[0][c];
+    if (!all && B.status[pi] != ST_ACTIVE) continue;
+    const BProb& P = B.p[pi];
+    const long long s0 = B.cstart[0][c];
+    const long long n = ncell(P.d[0]);
+    const long long s1 = s0 + CHUNK < n ? s0 + CHUNK : n;
+    DfAcc acc{0.f, 0.f};
+    for (long long i = s0 + threadIdx.x; i < s1; i += blockDim.x) op(P, i, acc);
+    const double b = block_sum_acc(acc, sh);
+    if (threadIdx.x == 0) part[c] = b;
+  }
+}
+
+__device__ __forceinline__ double chunk_total(const BDesc& B, const BProb& P, const double* part) {
+  double s = 0.0;
+  for (int k = 0; k < P.nch; ++k) s += part[P.c0 + k];
+  return s;
+}
+
+__global__ void __launch_bounds__(BT) k_batched_solve(BDesc B) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ double sh[32];
+  const int V = B.degree;
+  const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+  if (lead) *B.tstart = globaltimer();
+  // ---- prologue: double-float copies and the mean of F
+  phase0_sum(B, B.part0, sh, true, [&](const BProb& P, long long i, DfAcc& acc) {
+    const float2 f = f64_to_df(P.src[i]);
+    P.F[i] = f;
+    P.phi[i] = f64_to_df(P.out[i]);
+    acc.add(f.x);
+    acc.c += f.y;
+  });
+  grid.sync();
+  for (int pi = blockIdx.x * blockDim.x + threadIdx.x; pi < B.count; pi += gridDim.x * blockDim.x) {
+    const BProb& P = B.p[pi];
+    B.sc[pi * P_N + P_MEAN] = chunk_total(B, P, B.part0) / (double)ncell(P.d[0]);
+  }
+  grid.sync();
+  // residual of the initial guess and ||F - mean||^2
+  auto df_residual_phase = [&](bool with_f2) {
+    for (int c = blockIdx.x; c < B.nchunk[0]; c += gridDim.x) {
+      const int pi = B.cprob[0][c];
+      if (B.status[pi] != ST_ACTIVE) continue;
+      const BProb& P = B.p[pi];
+      const Dims d = P.d[0];
+      const float2 m = f64_to_df(B.sc[pi * P_N + P_MEAN]);
+      const long long s0 = B.cstart[0][c];
+      const long long n = ncell(d);
+      const long long s1 = s0 + CHUNK < n ? s0 + CHUNK : n;
+      float r2 = 0.f, f2 = 0.f;
+      for (long long i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
+        int x, y, z;
+        cell_xyz(d, i, x, y, z);
+        const long long sy = d.nx, sz = (long long)d.nx * d.ny;
+        const float2* u = P.phi;
+        const float2 f = P.F[i];
+        const float rv = df_resid(u[i], u[i + ((x == 0 ? d.nx - 1 : x - 1) - x)], u[i + ((x == d.nx - 1 ? 0 : x + 1) - x)],
+                                  u[i + (long long)((y == 0 ? d.ny - 1 : y - 1) - y) * sy],
+                                  u[i + (long long)((y == d.ny - 1 ? 0 : y + 1) - y) * sy],
+                                  u[i + (long long)((z == 0 ? d.nz - 1 : z - 1) - z) * sz],
+                                  u[i + (long long)((z == d.nz - 1 ? 0 : z + 1) - z) * sz], f, m);
+        P.r[0][i] = rv;
+        r2 += rv * rv;
+        const float fv = __fadd_rn(__fsub_rn(f.x, m.x), __fsub_rn(f.y, m.y));
+        f2 += fv * fv;
+      }
+      const double br = block_sum_f(r2, sh);
+      if (threadIdx.x == 0) B.part0[c] = br;
+      if (with_f2) {
+        const double bf = block_sum_f(f2, sh);
+        if (threadIdx.x == 0) B.part1[c] = bf;
+      }
+    }
+  };
+  // relative residual of every active problem, history and status
+  auto finalize = [&](bool first) {
+    for (int pi = blockIdx.x * blockDim.x + threadIdx.x; pi < B.count; pi += gridDim.x * blockDim.x) {
+      if (B.status[pi] != ST_ACTIVE) continue;
+      const BProb& P = B.p[pi];
+      double* s = B.sc + pi * P_N;
+      if (first) s[P_F2] = chunk_total(B, P, B.part1);
+      const double r2 = chunk_total(B, P, B.part0);
+      const double rel = s[P_F2] > 0.0 ? sqrt(r2 / s[P_F2]) : sqrt(r2);
+      int cyc = B.cycles[pi];
+      if (first) {
+        B.rel0[pi] = rel;
+        s[P_PREV1] = s[P_PREV2] = -1.0;
+      } else {
+        if (cyc < 64) B.hist[pi * 64 + cyc] = rel;
+        cyc += 1;
+        B.cycles[pi] = cyc;
+      }
+      s[P_REL] = rel;
+      int st = ST_ACTIVE;
+      if (!isfinite(rel)) st = GBMG_ERR_NONFINITE;
+      else if (rel <= B.tol) st = ST_CONVERGED;
+      else if (!first && s[P_PREV2] > 0.0 && rel > 10.0 * s[P_PREV2]) st = GBMG_ERR_DIVERGED;
+      else if (cyc >= B.maxv) st = GBMG_ERR_NOT_CONVERGED;
+      s[P_PREV2] = s[P_PREV1];
+      s[P_PREV1] = rel;
+      if (st != ST_ACTIVE) {
+        B.status[pi] = st;  // ST_CONVERGED is reported as GBMG_OK by the host
+        B.tdone[pi] = globaltimer();
+      }
+    }
+  };
+  df_residual_phase(true);
+  grid.sync();
+  finalize(true);
+  grid.sync();
+  // ---- V-cycles
+  for (int cycle = 0; cycle < B.maxv; ++cycle) {
+    if (lead) {
+      int a = 0;
+      for (int pi = 0; pi < B.count; ++pi) a += B.status[pi] == ST_ACTIVE;
+      *B.any_active = a;
+    }
+    grid.sync();
+    if (*((volatile int*)B.any_active) == 0) break;
+    // down: levels 0 .. maxL-2, then the coarsest solves
+    for (int l = 0; l + 1 < B.maxL; ++l) {
+      auto smoothed = [&](const BProb& P, int lv) { return lv < P.L - 1; };
+      bool cur_a = true;  // current e in ea
+      for (int k = 0; k < V; ++k) {
+        const bool from_zero = k == 0;
+        const float c1 = B.c1[k];
+        const double c2 = B.c2[k];
+        phase(B, l, smoothed, [&](const BProb& P, int lv, long long i) {
+          const Dims d = P.d[lv];
+          const double h = (double)(1 << lv);
+          const double ad = c2 * (-(h * h) / 6.0);
+          const float a = (float)ad, b = (float)(ad * (1.0 / (h * h)));
+          const float* e = cur_a ? P.ea[lv] : P.eb[lv];
+          float* eo = cur_a ? P.eb[lv] : P.ea[lv];
+          float c = 0.f, s = 0.f;
+          if (!from_zero) {
+            int x, y, z;
+            cell_xyz(d, i, x, y, z);
+            c = e[i];
+            s = nsum_at(e, d, x, y, z, i);
+          }
+          float dd = from_zero ? 0.f : P.dv[lv][i];
+          eo[i] = cheb_step(c, P.r[lv][i], s, c, dd, a, b, c1);
+          P.dv[lv][i] = dd;
+        });
+        cur_a = !cur_a;
+        grid.sync();
+      }
+      // residual, then full weighting to the next level
+      phase(B, l, smoothed, [&](const BProb& P, int lv, long long i) {
+        const Dims d = P.d[lv];
+        const float ih2 = (float)(1.0 / ((double)(1 << lv) * (double)(1 << lv)));
+        const float* e = cur_a ? P.ea[lv] : P.eb[lv];
+        int x, y, z;
+        cell_xyz(d, i, x, y, z);
+        P.t[lv][i] = resid_from_sum(P.r[lv][i], nsum_at(e, d, x, y, z, i), e[i], ih2);
+      });
+      grid.sync();
+      if (l + 1 < B.maxL) {
+        phase(B, l + 1, [&](const BProb& P, int lv) { return lv - 1 < P.L - 1; },
+              [&](const BProb& P, int lv, long long I) {
+                const Dims df = P.d[lv - 1], dc = P.d[lv];
+                int X, Y, Z;
+                cell_xyz(dc, I, X, Y, Z);
+                const float* f = P.t[lv - 1];
+                int xs[3], ys[3], zs[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                  xs[k] = wrapi(2 * X + k - 1, df.nx);
+                  ys[k] = wrapi(2 * Y + k - 1, df.ny);
+                  zs[k] = wrapi(2 * Z + k - 1, df.nz);
+                }
+                float yv[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                  float zv[3];
+#pragma unroll
+                  for (int b = 0; b < 3; ++b)
+                    zv[b] = fw3(f[lin(df, xs[a], ys[b], zs[0])], f[lin(df, xs[a], ys[b], zs[1])],
+                                f[lin(df, xs[a], ys[b], zs[2])]);
+                  yv[a] = fw3(zv[0], zv[1], zv[2]);
+                }
+                P.r[lv][I] = fw3(yv[0], yv[1], yv[2]);
+              });
+      }
+      grid.sync();
+      // coarsest solves of the problems whose hierarchy ends at level l + 1
+      if (l + 1 < B.maxL) {
+        const int warps = blockDim.x / 32, lane = threadIdx.x & 31;
+        for (int pi = blockIdx.x; pi < B.count; pi += gridDim.x) {
+          const BProb& P = B.p[pi];
+          if (B.status[pi] != ST_ACTIVE || P.L - 1 != l + 1) continue;
+          const float* r = P.r[l + 1];
+          float* e = P.ea[l + 1];
+          for (int row = threadIdx.x / 32; row < P.nc; row += warps) {
+            float acc = 0.f;
+            for (int j = lane; j < P.nc; j += 32) acc = t_fma(P.G[(long long)row * P.nc + j], r[j], acc);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc = t_add(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+            if (lane == 0) e[row] = acc;
+          }
+        }
+      }
+      grid.sync();
+    }
+    // up: levels maxL-2 .. 0.  Pre-smoothing from zero leaves e in eb when V is odd
+    // and in ea when V is even; V more steps then always end in ea, which is where
+    // the coarser level's correction is read from and where the coarsest solve writes.
+    for (int l = B.maxL - 2; l >= 0; --l) {
+      auto smoothed = [&](const BProb& P, int lv) { return lv < P.L - 1; };
+      bool cur_a = (V % 2) == 0;
+      phase(B, l, smoothed, [&](const BProb& P, int lv, long long i) {
+        const Dims d = P.d[lv];
+        int x, y, z;
+        cell_xyz(d, i, x, y, z);
+        float* e = cur_a ? P.ea[lv] : P.eb[lv];
+        e[i] = t_add(e[i], prolong_value(P.ea[lv + 1], P.d[lv + 1], x, y, z));
+      });
+      grid.sync();
+      for (int k = 0; k < V; ++k) {
+        const float c1 = B.c1[k];
+        const double c2 = B.c2[k];
+        phase(B, l, smoothed, [&](const BProb& P, int lv, long long i) {
+          const Dims d = P.d[lv];
+          const double h = (double)(1 << lv);
+          const double ad = c2 * (-(h * h) / 6.0);
+          const float a = (float)ad, b = (float)(ad * (1.0 / (h * h)));
+          const float* e = cur_a ? P.ea[lv] : P.eb[lv];
+          float* eo = cur_a ? P.eb[lv] : P.ea[lv];
+          int x, y, z;
+          cell_xyz(d, i, x, y, z);
+          const float c = e[i];
+          float dd = k == 0 ? 0.f : P.dv[lv][i];
+          eo[i] = cheb_step(c, P.r[lv][i], nsum_at(e, d, x, y, z, i), c, dd, a, b, c1);
+          P.dv[lv][i] = dd;
+        });
+        cur_a = !cur_a;
+        grid.sync();
+      }
+    }
+    // phi += e, next residual, convergence
+    phase(B, 0, [&](const BProb&, int) { return true; },
+          [&](const BProb& P, int, long long i) { P.phi[i] = df_add_f(P.phi[i], P.ea[0][i]); });
+    grid.sync();
+    df_residual_phase(false);
+    grid.sync();
+    finalize(false);
+    grid.sync();
+  }
+  // problems still active after max_vcycles
+  for (int pi = blockIdx.x * blockDim.x + threadIdx.x; pi < B.count; pi += gridDim.x * blockDim.x) {
+    if (B.status[pi] == ST_ACTIVE) {
+      B.status[pi] = GBMG_ERR_NOT_CONVERGED;
+      B.tdone[pi] = globaltimer();
+    }
+  }
+  grid.sync();
+  // ---- epilogue: gauge and FP64 output for every problem
+  phase0_sum(B, B.part0, sh, true, [&](const BProb& P, long long i, DfAcc& acc) {
+    const float2 v = P.phi[i];
+    acc.add(v.x);
+    acc.c += v.y;
+  });
+  grid.sync();
+  for (int pi = blockIdx.x * blockDim.x + threadIdx.x; pi < B.count; pi += gridDim.x * blockDim.x) {
+    const BProb& P = B.p[pi];
+    B.sc[pi * P_N + P_MPHI] = chunk_total(B, P, B.part0) / (double)ncell(P.d[0]);
+  }
+  grid.sync();
+  for (int c = blockIdx.x; c < B.nchunk[0]; c += gridDim.x) {
+    const int pi = B.cprob[0][c];
+    const BProb& P = B.p[pi];
+    float2 ms = f64_to_df(B.sc[pi * P_N + P_MPHI]);
+    ms.x = -ms.x;
+    ms.y = -ms.y;
+    const long long s0 = B.cstart[0][c];
+    const long long n = ncell(P.d[0]);
+    const long long s1 = s0 + CHUNK < n ? s0 + CHUNK : n;
+    for (long long i = s0 + threadIdx.x; i < s1; i += blockDim.x) P.out[i] = df_to_f64(df_add(P.phi[i], ms));
+  }
+}
+
+}  // namespace
+
+struct gbmg_batch {
+  std::vector<gbmg_ctx*> ctx;
+  int count = 0, maxL = 0, blocks = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  char* mem = nullptr;  // device memory of the descriptor tables and results
+  BDesc desc{};
+  BProb* hprob = nullptr;  // pinned host copy of the problem table
+  int* hstatus = nullptr;  // pinned host results
+  int* hcycles = nullptr;
+  double* hhist = nullptr;
+  double* hrel0 = nullptr;
+  double* hsc = nullptr;
+  unsigned long long* htime = nullptr;
+  unsigned long long* htstart = nullptr;
+  size_t res_bytes = 0;
+  ~gbmg_batch() {
+    if (mem) cudaFree(mem);
+    if (hprob) cudaFreeHost(hprob);
+    if (hstatus) cudaFreeHost(hstatus);
+  }
+};
+
+extern "C" gbmg_status mg_batch_create(gbmg_batch** out, gbmg_ctx* const* ctxs, int count, void* cuda_stream) {
+  g_last_error.clear();
+  if (!out || !ctxs || count < 1) return fail(GBMG_ERR_INVALID_ARG, "mg_batch_create: bad argument");
+  for (int i = 0; i < count; ++i) {
+    const gbmg_ctx* c = ctxs[i];
+    if (!c) return fail(GBMG_ERR_INVALID_ARG, "mg_batch_create: NULL context");
+    if (c->o.op != GBMG_OP_FLAT7 || c->o.prec != GBMG_MIXED || c->o.smoother != GBMG_SMOOTH_CHEBYSHEV || c->o.fused)
+      return fail(GBMG_ERR_INVALID_ARG,
+                  "mg_batch_create: contexts must be flat, mixed precision, Chebyshev, fused = 0");
+    if (c->L > BMAXL || c->L < 2) return fail(GBMG_ERR_INVALID_ARG, "mg_batch_create: each problem needs 2 to 16 levels");
+    if (c->o.degree != ctxs[0]->o.degree || c->o.alpha != ctxs[0]->o.alpha)
+      return fail(GBMG_ERR_INVALID_ARG, "mg_batch_create: all contexts need the same smoother");
+    if (c->device != ctxs[0]->device) return fail(GBMG_ERR_INVALID_ARG, "mg_batch_create: contexts on different devices");
+  }
+  DeviceGuard g(ctxs[0]->device);
+  auto* b = new (std::nothrow) gbmg_batch();
+  if (!b) return fail(GBMG_ERR_OOM, "mg_batch_create: host allocation");
+  b->ctx.assign(ctxs, ctxs + count);
+  b->count = count;
+  b->stream = (cudaStream_t)cuda_stream;
+  b->device = ctxs[0]->device;
+  int maxL = 0;
+  for (auto* c : b->ctx) maxL = std::max(maxL, c->L);
+  b->maxL = maxL;
+  // chunk tables
+  std::vector<std::vector<int>> cprob(maxL);
+  std::vector<std::vector<long long>> cstart(maxL);
+  std::vector<int> c0(count), nch(count);
+  for (int l = 0; l < maxL; ++l)
+    for (int i = 0; i < count; ++i) {
+      const gbmg_ctx* c = b->ctx[i];
+      if (l >= c->L) continue;
+      const long long n = ncell(c->lv[l].d);
+      if (l == 0) c0[i] = (int)cprob[0].size();
+      for (long long s = 0; s < n; s += CHUNK) {
+        cprob[l].push_back(i);
+        cstart[l].push_back(s);
+      }
+      if (l == 0) nch[i] = (int)cprob[0].size() - c0[i];
+    }
+  // device layout
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += (bytes + 255) & ~(size_t)255;
+    return o;
+  };
+  const size_t oP = take(sizeof(BProb) * count);
+  std::vector<size_t> ocp(maxL), ocs(maxL);
+  for (int l = 0; l < maxL; ++l) {
+    ocp[l] = take(sizeof(int) * cprob[l].size());
+    ocs[l] = take(sizeof(long long) * cstart[l].size());
+  }
+  const size_t n0 = cprob[0].size();
+  const size_t oP0 = take(sizeof(double) * n0), oP1 = take(sizeof(double) * n0);
+  const size_t oSc = take(sizeof(double) * P_N * count);
+  // results block (copied back together): status, cycles, hist, rel0, times
+  const size_t oRes = off;
+  const size_t oSt = take(sizeof(int) * count), oCy = take(sizeof(int) * count);
+  const size_t oHi = take(sizeof(double) * 64 * count), oR0 = take(sizeof(double) * count);
+  const size_t oTd = take(sizeof(unsigned long long) * count), oTs = take(sizeof(unsigned long long));
+  const size_t resEnd = off;
+  const size_t oAny = take(sizeof(int));
+  cudaError_t e = cudaMalloc((void**)&b->mem, off);
+  if (e != cudaSuccess) {
+    delete b;
+    return cuda_fail(e, "mg_batch_create: device allocation");
+  }
+  b->res_bytes = resEnd - oRes;
+  e = cudaMallocHost((void**)&b->hprob, sizeof(BProb) * count);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->hstatus, b->res_bytes + 8 * P_N * count);
+  if (e != cudaSuccess) {
+    delete b;
+    return cuda_fail(e, "mg_batch_create: pinned allocation");
+  }
+  char* base = (char*)b->hstatus;
+  b->hcycles = (int*)(base + (oCy - oRes));
+  b->hhist = (double*)(base + (oHi - oRes));
+  b->hrel0 = (double*)(base + (oR0 - oRes));
+  b->htime = (unsigned long long*)(base + (oTd - oRes));
+  b->htstart = (unsigned long long*)(base + (oTs - oRes));
+  b->hsc = (double*)(base + b->res_bytes);
+  char* m = b->mem;
+  BDesc& D = b->desc;
+  D.count = count;
+  D.maxL = maxL;
+  D.degree = ctxs[0]->o.degree;
+  for (int k = 0; k < D.degree && k < 16; ++k) {
+    D.c1[k] = (float)ctxs[0]->cc1[k];
+    D.c2[k] = ctxs[0]->cc2[k];
+  }
+  D.p = (BProb*)(m + oP);
+  for (int l = 0; l < maxL; ++l) {
+    D.cprob[l] = (int*)(m + ocp[l]);
+    D.cstart[l] = (long long*)(m + ocs[l]);
+    D.nchunk[l] = (int)cprob[l].size();
+  }
+  D.part0 = (double*)(m + oP0);
+  D.part1 = (double*)(m + oP1);
+  D.sc = (double*)(m + oSc);
+  D.status = (int*)(m + oSt);
+  D.cycles = (int*)(m + oCy);
+  D.hist = (double*)(m + oHi);
+  D.rel0 = (double*)(m + oR0);
+  D.tdone = (unsigned long long*)(m + oTd);
+  D.tstart = (unsigned long long*)(m + oTs);
+  D.any_active = (int*)(m + oAny);
+  for (int i = 0; i < count; ++i) {
+    const gbmg_ctx* c = b->ctx[i];
+    BProb& P = b->hprob[i];
+    std::memset(&P, 0, sizeof(P));
+    P.L = c->L;
+    P.nc = c->nc;
+    for (int l = 0; l < c->L; ++l) {
+      P.d[l] = c->lv[l].d;
+      P.r[l] = (float*)c->lv[l].r;
+      P.ea[l] = (float*)c->lv[l].e;
+      P.eb[l] = (float*)c->lv[l].e2;
+      P.dv[l] = (float*)c->lv[l].dv;
+      P.t[l] = (float*)c->lv[l].t;
+    }
+    P.G = c->G32;
+    P.F = c->F_df;
+    P.phi = c->phi_df;
+    P.c0 = c0[i];
+    P.nch = nch[i];
+  }
+  for (int l = 0; l < maxL; ++l) {
+    e = cudaMemcpy(D.cprob[l], cprob[l].data(), sizeof(int) * cprob[l].size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(D.cstart[l], cstart[l].data(), sizeof(long long) * cstart[l].size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      delete b;
+      return cuda_fail(e, "mg_batch_create: upload");
+    }
+  }
+  // persistent grid: every block resident at once (cooperative launch)
+  int per_sm = 0, sms = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched_solve, BT, 0);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+  if (e != cudaSuccess || per_sm < 1) {
+    delete b;
+    return e != cudaSuccess ? cuda_fail(e, "mg_batch_create: occupancy") : fail(GBMG_ERR_CUDA, "mg_batch_create: kernel does not fit");
+  }
+  b->blocks = per_sm * sms;
+  *out = b;
+  return GBMG_OK;
+}
+
+extern "C" void mg_batch_destroy(gbmg_batch* b) { delete b; }
+
+extern "C" gbmg_status mg_batch_set_blocks(gbmg_batch* b, int blocks) {
+  if (!b || blocks < 1) return fail(GBMG_ERR_INVALID_ARG, "mg_batch_set_blocks: bad argument");
+  int per_sm = 0, sms = 0;
+  DeviceGuard g(b->device);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched_solve, BT, 0) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess)
+    return fail(GBMG_ERR_CUDA, "mg_batch_set_blocks: occupancy query failed");
+  if (blocks > per_sm * sms) return fail(GBMG_ERR_INVALID_ARG, "mg_batch_set_blocks: more blocks than can be resident");
+  b->blocks = blocks;
+  return GBMG_OK;
+}
+
+extern "C" gbmg_status mg_batch_solve(gbmg_batch* b, const double* const* src_dev, double* const* phi_dev, double tol,
+                                      int max_vcycles, gbmg_stats* stats, double* times_ms) {
+  g_last_error.clear();
+  if (!b || !src_dev || !phi_dev) return fail(GBMG_ERR_INVALID_ARG, "mg_batch_solve: NULL argument");
+  if (!(tol >= 0.0)) return fail(GBMG_ERR_INVALID_ARG, "mg_batch_solve: tol must be >= 0");
+  DeviceGuard g(b->device);
+  for (int i = 0; i < b->count; ++i) {
+    if (!src_dev[i] || !phi_dev[i]) return fail(GBMG_ERR_INVALID_ARG, "mg_batch_solve: NULL field");
+    b->hprob[i].src = src_dev[i];
+    b->hprob[i].out = phi_dev[i];
+  }
+  BDesc D = b->desc;
+  D.tol = tol;
+  D.maxv = max_vcycles < 0 ? 0 : max_vcycles;
+  TRY(cudaMemcpyAsync(D.p, b->hprob, sizeof(BProb) * b->count, cudaMemcpyHostToDevice, b->stream));
+  TRY(cudaMemsetAsync(D.status, 0, sizeof(int) * b->count, b->stream));
+  TRY(cudaMemsetAsync(D.cycles, 0, sizeof(int) * b->count, b->stream));
+  void* args[] = {&D};
+  TRY(cudaLaunchCooperativeKernel((void*)k_batched_solve, dim3(b->blocks), dim3(BT), args, 0, b->stream));
+  note_launch();
+  TRY(cudaMemcpyAsync(b->hstatus, D.status, b->res_bytes, cudaMemcpyDeviceToHost, b->stream));
+  TRY(cudaMemcpyAsync(b->hsc, D.sc, sizeof(double) * P_N * b->count, cudaMemcpyDeviceToHost, b->stream));
+  TRY(cudaStreamSynchronize(b->stream));
+  gbmg_status worst = GBMG_OK;
+  const unsigned long long t0 = *b->htstart;
+  for (int i = 0; i < b->count; ++i) {
+    const int s = b->hstatus[i];
+    const gbmg_status st = s == ST_CONVERGED ? GBMG_OK : (gbmg_status)s;
+    if (st != GBMG_OK && worst == GBMG_OK) worst = st;
+    if (stats) {
+      gbmg_stats& S = stats[i];
+      std::memset(&S, 0, sizeof(S));
+      S.cycles = b->hcycles[i];
+      S.status = st;
+      S.rel_res0 = b->hrel0[i];
+      S.rel_res = b->hsc[i * P_N + P_REL];
+      for (int k = 0; k < S.cycles && k < 64; ++k) S.res_hist[k] = b->hhist[i * 64 + k];
+    }
+    if (times_ms) times_ms[i] = (double)(b->htime[i] - t0) * 1e-6;
+  }
+  return worst;
+}
+
+extern "C" gbmg_status mg_batch_autotune(gbmg_batch* b, const double* const* src_dev, double* const* phi_dev,
+                                         double tol, int max_vcycles, int* blocks_out) {
+  if (!b) return fail(GBMG_ERR_INVALID_ARG, "mg_batch_autotune: NULL batch");
+  DeviceGuard g(b->device);
+  int per_sm = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched_solve, BT, 0) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess)
+    return fail(GBMG_ERR_CUDA, "mg_batch_autotune: occupancy query failed");
+  cudaEvent_t e0, e1;
+  TRY(cudaEventCreate(&e0));
+  TRY(cudaEventCreate(&e1));
+  int best = b->blocks;
+  float best_ms = -1.f;
+  for (int k = 1; k <= per_sm; ++k) {
+    b->blocks = k * sms;
+    TRY(cudaEventRecord(e0, b->stream));
+    const gbmg_status s = mg_batch_solve(b, src_dev, phi_dev, tol, max_vcycles, nullptr, nullptr);
+    if (s == GBMG_ERR_CUDA || s == GBMG_ERR_INVALID_ARG) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return s;
+    }
+    TRY(cudaEventRecord(e1, b->stream));
+    TRY(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    TRY(cudaEventElapsedTime(&ms, e0, e1));
+    if (best_ms < 0.f || ms < best_ms) {
+      best_ms = ms;
+      best = b->blocks;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->blocks = best;
+  if (blocks_out) *blocks_out = best;
+  return GBMG_OK;
+}

@@ -81,26 +81,24 @@ __global__ void k_residual(Dims d, const T* __restrict__ f, const T* __restrict_
 
 template <typename T>
 __global__ void k_cheb_step(Dims d, const T* __restrict__ r, const T* __restrict__ e_in, T* __restrict__ e_out,
-                            T* __restrict__ dvec, T inv_h2, T dinv, T c1, T c2) {
+                            T* __restrict__ dvec, T a, T b, T c1) {
   const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y, z = blockIdx.z;
   if (x >= d.nx || y >= d.ny) return;
   const long long i = lin(d, x, y, z);
   const T c = e_in[i];
-  const T res = resid_from_sum(r[i], nsum(load_nbrs(e_in, d, x, y, z, i)), c, inv_h2);
   T dv = c1 == T(0) ? T(0) : dvec[i];
-  e_out[i] = cheb_step(c, res, dv, dinv, c1, c2);
+  e_out[i] = cheb_step(c, r[i], nsum(load_nbrs(e_in, d, x, y, z, i)), c, dv, a, b, c1);
   dvec[i] = dv;
 }
 
 template <typename T>
 __global__ void k_jacobi(Dims d, const T* __restrict__ r, const T* __restrict__ e_in, T* __restrict__ e_out,
-                         T inv_h2, T w_dinv) {
+                         T wa, T wb) {
   const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y, z = blockIdx.z;
   if (x >= d.nx || y >= d.ny) return;
   const long long i = lin(d, x, y, z);
   const T c = e_in[i];
-  const T res = resid_from_sum(r[i], nsum(load_nbrs(e_in, d, x, y, z, i)), c, inv_h2);
-  e_out[i] = jacobi_step(c, res, w_dinv);
+  e_out[i] = jacobi_step(c, r[i], nsum(load_nbrs(e_in, d, x, y, z, i)), c, wa, wb);
 }
 
 // Full weighting, one thread per coarse cell: z-axis weights first, then y, then x
@@ -288,15 +286,14 @@ cudaError_t launch_residual(cudaStream_t st, Dims d, const T* f, const T* u, T* 
   return cudaGetLastError();
 }
 template <typename T>
-cudaError_t launch_cheb_step(cudaStream_t st, Dims d, const T* r, const T* e_in, T* e_out, T* dvec, T inv_h2,
-                             T dinv, T c1, T c2) {
-  k_cheb_step<T><<<cell_grid(d), dim3(BX, BY), 0, st>>>(d, r, e_in, e_out, dvec, inv_h2, dinv, c1, c2);
+cudaError_t launch_cheb_step(cudaStream_t st, Dims d, const T* r, const T* e_in, T* e_out, T* dvec, T a, T b, T c1) {
+  k_cheb_step<T><<<cell_grid(d), dim3(BX, BY), 0, st>>>(d, r, e_in, e_out, dvec, a, b, c1);
   note_launch();
   return cudaGetLastError();
 }
 template <typename T>
-cudaError_t launch_jacobi(cudaStream_t st, Dims d, const T* r, const T* e_in, T* e_out, T inv_h2, T w_dinv) {
-  k_jacobi<T><<<cell_grid(d), dim3(BX, BY), 0, st>>>(d, r, e_in, e_out, inv_h2, w_dinv);
+cudaError_t launch_jacobi(cudaStream_t st, Dims d, const T* r, const T* e_in, T* e_out, T wa, T wb) {
+  k_jacobi<T><<<cell_grid(d), dim3(BX, BY), 0, st>>>(d, r, e_in, e_out, wa, wb);
   note_launch();
   return cudaGetLastError();
 }
@@ -365,7 +362,7 @@ cudaError_t launch_df_update(cudaStream_t st, long long n, float2* phi, const fl
 #define GBMG_INSTANTIATE(T)                                                                           \
   template cudaError_t launch_apply<T>(cudaStream_t, Dims, const T*, T*, T);                         \
   template cudaError_t launch_residual<T>(cudaStream_t, Dims, const T*, const T*, T*, T, double*);   \
-  template cudaError_t launch_cheb_step<T>(cudaStream_t, Dims, const T*, const T*, T*, T*, T, T, T, T); \
+  template cudaError_t launch_cheb_step<T>(cudaStream_t, Dims, const T*, const T*, T*, T*, T, T, T);  \
   template cudaError_t launch_jacobi<T>(cudaStream_t, Dims, const T*, const T*, T*, T, T);           \
   template cudaError_t launch_restrict<T>(cudaStream_t, Dims, const T*, T*);                         \
   template cudaError_t launch_prolong_add<T>(cudaStream_t, Dims, const T*, T*);                      \

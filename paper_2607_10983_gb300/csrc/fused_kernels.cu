@@ -68,36 +68,31 @@ struct Positions {
   }
 };
 
+// Folded Chebyshev constants of one level: c1 and a = c2 D^-1, b = a / h^2 per step.
 struct Coef {
   float c1[16];
-  float c2[16];
+  float a[16];
+  float b[16];
 };
 
 // ------------------------------------------------------------------ down leg
 
 template <int V, int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT, 1)
-k_down_fused(Dims d, const float* __restrict__ r, float* __restrict__ e_out, float* __restrict__ rc, int zc,
-             float inv_h2, float dinv, Coef cf) {
+__device__ __forceinline__ void down_segment(Dims d, const float* __restrict__ r, float* __restrict__ e_out,
+                                             float* __restrict__ rc, int x0, int y0, int z0, int zend,
+                                             float inv_h2, const Coef& cf, float* sm) {
   constexpr int H = V + 1;
   using TL = Tile<TX, TY, H, NT>;
   constexpr int WX = TL::WX, K = TL::K, PLANE = TL::PLANE, PAD = TL::PAD;
-  static_assert(NT == (TX / 2) * (TY / 2), "one coarse output per thread");
-  extern __shared__ float sm[];
+  constexpr int NCO = (TX / 2) * (TY / 2);  // coarse outputs per tile plane
   // plane(s, b): s = 0..V-1 holds e_{s+1}, s = V holds the z-weighted residual
   auto plane = [&](int s, int b) -> float* { return sm + (s * 2 + b) * PLANE + PAD; };
 
   const int tid = threadIdx.x;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * zc;
-  const int zend = min(z0 + zc, d.nz);
   const long long pst = (long long)d.nx * d.ny;
   Positions<TX, TY, H, NT> P;
   P.init(d, x0, y0);
   const Dims dc{d.nx / 2, d.ny / 2, d.nz / 2};
-  const int ccx = tid % (TX / 2), ccy = tid / (TX / 2);
-  const int cX = x0 / 2 + ccx, cY = y0 / 2 + ccy;
-  const bool cvalid = cX < dc.nx && cY < dc.ny;
-  const int cp = (H + 2 * ccy) * WX + H + 2 * ccx;
 
   float rq[V + 1][K];              // rq[j][k] = r at plane t - j
   float wp[V + 2][K], wc[V + 2][K];  // stage s input window: planes p-1, p
@@ -112,7 +107,9 @@ k_down_fused(Dims d, const float* __restrict__ r, float* __restrict__ e_out, flo
     for (int s = 0; s < V + 2; ++s) wp[s][k] = 0.f, wc[s][k] = 0.f;
     rsp[k] = rsc[k] = 0.f;
   }
-  const int tb = z0 - H, te = zend + V;
+  // last iteration: the coarse plane c = zend - 1 (a segment may end on an odd plane)
+  // is written at t = c + V + 2
+  const int tb = z0 - H, te = zend + V + 1;
   {
     const long long base = (long long)wrapmod(tb, d.nz) * pst;
 #pragma unroll
@@ -136,7 +133,7 @@ k_down_fused(Dims d, const float* __restrict__ r, float* __restrict__ e_out, flo
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       float dd = 0.f;
-      en[1][k] = cheb_step(0.f, rq[0][k], dd, dinv, cf.c1[0], cf.c2[0]);
+      en[1][k] = cheb_step(0.f, rq[0][k], 0.f, 0.f, dd, cf.a[0], cf.b[0], cf.c1[0]);
       dn[1][k] = dd;
       plane(0, cur)[tid + k * NT] = en[1][k];
     }
@@ -150,11 +147,9 @@ k_down_fused(Dims d, const float* __restrict__ r, float* __restrict__ e_out, flo
       for (int k = 0; k < K; ++k) {
         const int p = tid + k * NT;
         const float c = wc[s][k];
-        const float res = resid_from_sum(rq[s - 1][k],
-                                         nbr_sum(src[p - 1], src[p + 1], src[p - WX], src[p + WX], wp[s][k], en[s - 1][k]),
-                                         c, inv_h2);
+        const float sn = nbr_sum(src[p - 1], src[p + 1], src[p - WX], src[p + WX], wp[s][k], en[s - 1][k]);
         float dd = dh[s][k];
-        en[s][k] = cheb_step(c, res, dd, dinv, cf.c1[s - 1], cf.c2[s - 1]);
+        en[s][k] = cheb_step(c, rq[s - 1][k], sn, c, dd, cf.a[s - 1], cf.b[s - 1], cf.c1[s - 1]);
         dn[s][k] = dd;
         dst[p] = en[s][k];
         if (s == V && (P.tmask >> k & 1u) && zp >= z0 && zp < zend) e_out[(long long)zp * pst + P.goff[k]] = en[s][k];
@@ -186,12 +181,19 @@ k_down_fused(Dims d, const float* __restrict__ r, float* __restrict__ e_out, flo
     // coarse output from the z-weighted plane of the previous iteration
     {
       const int c = t - V - 2;
-      if (((c & 1) == 0) && c >= z0 && c < zend && cvalid) {
+      if (((c & 1) == 0) && c >= z0 && c < zend) {
         const float* zs = plane(V, prv);
-        float yv[3];
+        for (int q = tid; q < NCO; q += NT) {
+          const int ccx = q % (TX / 2), ccy = q / (TX / 2);
+          const int cX = x0 / 2 + ccx, cY = y0 / 2 + ccy;
+          if (cX < dc.nx && cY < dc.ny) {
+            const int cp = (H + 2 * ccy) * WX + H + 2 * ccx;
+            float yv[3];
 #pragma unroll
-        for (int a = -1; a <= 1; ++a) yv[a + 1] = fw3(zs[cp + a - WX], zs[cp + a], zs[cp + a + WX]);
-        rc[((long long)(c >> 1) * dc.ny + cY) * dc.nx + cX] = fw3(yv[0], yv[1], yv[2]);
+            for (int a = -1; a <= 1; ++a) yv[a + 1] = fw3(zs[cp + a - WX], zs[cp + a], zs[cp + a + WX]);
+            rc[((long long)(c >> 1) * dc.ny + cY) * dc.nx + cX] = fw3(yv[0], yv[1], yv[2]);
+          }
+        }
       }
     }
     // advance the z windows
@@ -205,6 +207,31 @@ k_down_fused(Dims d, const float* __restrict__ r, float* __restrict__ e_out, flo
 #pragma unroll
       for (int s = 2; s <= V; ++s) dh[s][k] = dn[s - 1][k];
     }
+    __syncthreads();
+  }
+}
+
+// Persistent schedule: the tiles' planes form one list (tile-major); CTA b takes the
+// contiguous range [b T / G, (b+1) T / G) and runs it as one segment per tile touched.
+struct Sched {
+  int tiles_x;
+  long long total;  // tiles * nz
+};
+
+template <int V, int TX, int TY, int NT>
+__global__ void __maxnreg__(65536 / ((NT + 127) / 128 * 128) / 8 * 8)
+k_down_fused(Dims d, const float* __restrict__ r, float* __restrict__ e_out, float* __restrict__ rc, Sched sc,
+             float inv_h2, Coef cf) {
+  extern __shared__ float sm[];
+  long long a = (long long)blockIdx.x * sc.total / gridDim.x;
+  const long long b = (long long)(blockIdx.x + 1) * sc.total / gridDim.x;
+  while (a < b) {
+    const long long tile = a / d.nz;
+    const int z0 = (int)(a % d.nz);
+    const int zend = (int)(z0 + (b - a) < d.nz ? z0 + (b - a) : d.nz);
+    down_segment<V, TX, TY, NT>(d, r, e_out, rc, (int)(tile % sc.tiles_x) * TX, (int)(tile / sc.tiles_x) * TY, z0,
+                                zend, inv_h2, cf, sm);
+    a += zend - z0;
     __syncthreads();
   }
 }
@@ -228,22 +255,19 @@ struct CoarseTile {
 };
 
 template <int V, int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT, 1)
-k_up_fused(Dims d, const float* __restrict__ e_in, const float* __restrict__ ec, const float* __restrict__ r,
-           float* __restrict__ e_out, int zc, float inv_h2, float dinv, Coef cf) {
+__device__ __forceinline__ void up_segment(Dims d, const float* __restrict__ e_in, const float* __restrict__ ec,
+                                           const float* __restrict__ r, float* __restrict__ e_out, int x0, int y0,
+                                           int z0, int zend, float inv_h2, const Coef& cf, float* sm) {
   constexpr int H = V;
   using TL = Tile<TX, TY, H, NT>;
   using CT = CoarseTile<TX, TY, H>;
   constexpr int WX = TL::WX, K = TL::K, PLANE = TL::PLANE, PAD = TL::PAD;
   constexpr int CW = CT::CW, CN = CT::CN, CL = (CN + NT - 1) / NT;
-  extern __shared__ float sm[];
   // plane(s, b): e_s for s = 0..V-1 (e_0 = e + P e_c); then three coarse planes
   auto plane = [&](int s, int b) -> float* { return sm + (s * 2 + b) * PLANE + PAD; };
   float* cring = sm + V * 2 * PLANE;
 
   const int tid = threadIdx.x;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * zc;
-  const int zend = min(z0 + zc, d.nz);
   const long long pst = (long long)d.nx * d.ny;
   const Dims dc{d.nx / 2, d.ny / 2, d.nz / 2};
   const long long cpst = (long long)dc.nx * dc.ny;
@@ -362,11 +386,9 @@ k_up_fused(Dims d, const float* __restrict__ e_in, const float* __restrict__ ec,
       for (int k = 0; k < K; ++k) {
         const int p = tid + k * NT;
         const float c = wc[s][k];
-        const float res = resid_from_sum(rq[s][k],
-                                         nbr_sum(src[p - 1], src[p + 1], src[p - WX], src[p + WX], wp[s][k], en[s - 1][k]),
-                                         c, inv_h2);
+        const float sn = nbr_sum(src[p - 1], src[p + 1], src[p - WX], src[p + WX], wp[s][k], en[s - 1][k]);
         float dd = s == 1 ? 0.f : dh[s][k];
-        en[s][k] = cheb_step(c, res, dd, dinv, cf.c1[s - 1], cf.c2[s - 1]);
+        en[s][k] = cheb_step(c, rq[s][k], sn, c, dd, cf.a[s - 1], cf.b[s - 1], cf.c1[s - 1]);
         dn[s][k] = dd;
         if (s < V) {
           plane(s, cur)[p] = en[s][k];
@@ -390,6 +412,24 @@ k_up_fused(Dims d, const float* __restrict__ e_in, const float* __restrict__ ec,
   }
 }
 
+template <int V, int TX, int TY, int NT>
+__global__ void __maxnreg__(65536 / ((NT + 127) / 128 * 128) / 8 * 8)
+k_up_fused(Dims d, const float* __restrict__ e_in, const float* __restrict__ ec, const float* __restrict__ r,
+           float* __restrict__ e_out, Sched sc, float inv_h2, Coef cf) {
+  extern __shared__ float sm[];
+  long long a = (long long)blockIdx.x * sc.total / gridDim.x;
+  const long long b = (long long)(blockIdx.x + 1) * sc.total / gridDim.x;
+  while (a < b) {
+    const long long tile = a / d.nz;
+    const int z0 = (int)(a % d.nz);
+    const int zend = (int)(z0 + (b - a) < d.nz ? z0 + (b - a) : d.nz);
+    up_segment<V, TX, TY, NT>(d, e_in, ec, r, e_out, (int)(tile % sc.tiles_x) * TX, (int)(tile / sc.tiles_x) * TY, z0,
+                              zend, inv_h2, cf, sm);
+    a += zend - z0;
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------------ finest level, double-float
 
 // phi' = phi + e (double-float) on the tile plus a one-cell halo, then
@@ -399,7 +439,8 @@ template <int TX, int TY, int NT>
 __global__ void __launch_bounds__(NT)
 k_df_update_residual(Dims d, const float2* __restrict__ phi_in, const float* __restrict__ e,
                      const float2* __restrict__ F, const double* __restrict__ m_dev, float2* __restrict__ phi_out,
-                     float* __restrict__ r_out, double* __restrict__ pr2, double* __restrict__ psum, int zc) {
+                     float* __restrict__ r_out, double* __restrict__ pr2, double* __restrict__ psum,
+                     double* __restrict__ pf2, int zc) {
   constexpr int H = 1;
   using TL = Tile<TX, TY, H, NT>;
   constexpr int WX = TL::WX, K = TL::K, PLANE = TL::PLANE, PAD = TL::PAD;
@@ -415,10 +456,12 @@ k_df_update_residual(Dims d, const float2* __restrict__ phi_in, const float* __r
   float2 wp[K], wc[K];
   float2 nphi[K], fq[K];
   float ne[K];
-  float r2 = 0.f;
+  float r2 = 0.f, f2 = 0.f;
   DfAcc ps{0.f, 0.f};
 #pragma unroll
   for (int k = 0; k < K; ++k) wp[k] = wc[k] = fq[k] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int k = 0; k < K; ++k) ne[k] = 0.f;
   const int tb = z0 - 1, te = zend;
   auto load = [&](int t) {
     const long long base = (long long)wrapmod(t, d.nz) * pst;
@@ -426,7 +469,7 @@ k_df_update_residual(Dims d, const float2* __restrict__ phi_in, const float* __r
     for (int k = 0; k < K; ++k) {
       const bool v = P.vmask >> k & 1u;
       nphi[k] = v ? phi_in[base + P.goff[k]] : make_float2(0.f, 0.f);
-      ne[k] = v ? __ldg(e + base + P.goff[k]) : 0.f;
+      if (e) ne[k] = v ? __ldg(e + base + P.goff[k]) : 0.f;
     }
   };
   load(tb);
@@ -437,7 +480,7 @@ k_df_update_residual(Dims d, const float2* __restrict__ phi_in, const float* __r
     float2 fcur[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      pn[k] = df_add_f(nphi[k], ne[k]);
+      pn[k] = e ? df_add_f(nphi[k], ne[k]) : nphi[k];
       fcur[k] = fq[k];
     }
     if (t < te) {
@@ -453,7 +496,7 @@ k_df_update_residual(Dims d, const float2* __restrict__ phi_in, const float* __r
       if (P.vmask >> k & 1u) {
         sp[cur][PAD + tid + k * NT] = pn[k];
         if ((P.tmask >> k & 1u) && t >= z0 && t < zend) {
-          phi_out[base + P.goff[k]] = pn[k];
+          if (phi_out) phi_out[base + P.goff[k]] = pn[k];
           ps.add(pn[k].x);
           ps.c += pn[k].y;
         }
@@ -471,6 +514,8 @@ k_df_update_residual(Dims d, const float2* __restrict__ phi_in, const float* __r
           const float rv = df_resid(wc[k], src[p - 1], src[p + 1], src[p - WX], src[p + WX], wp[k], pn[k], fcur[k], m);
           r_out[gi] = rv;
           r2 += rv * rv;
+          const float fv = __fadd_rn(__fsub_rn(fcur[k].x, m.x), __fsub_rn(fcur[k].y, m.y));
+          f2 += fv * fv;
         }
       }
     }
@@ -483,15 +528,19 @@ k_df_update_residual(Dims d, const float2* __restrict__ phi_in, const float* __r
   }
   const double b2 = block_sum_f(r2, shr);
   const double bs = block_sum_acc(ps, shr);
+  const double bf = pf2 ? block_sum_f(f2, shr) : 0.0;
   if (tid == 0) {
     const int bid = block_linear_id();
     pr2[bid] = b2;
     psum[bid] = bs;
+    if (pf2) pf2[bid] = bf;
   }
 }
 
-constexpr int DTX = 64, DTY = 32, DNT = 512;   // down-leg tile
-constexpr int UTX = 64, UTY = 32, UNT = 512;   // up-leg tile
+// Block sizes are multiples of 128 threads: registers are granted to groups of four
+// warps, so e.g. 448 threads at 144 registers would not fit in the 64K register file.
+constexpr int DTX = 64, DTY = 32, DNT = 512;   // down-leg tile: 72 x 40 region, 6 slots per thread
+constexpr int UTX = 64, UTY = 32, UNT = 384;   // up-leg tile: 70 x 38 region, 7 slots per thread
 constexpr int FTX = 64, FTY = 16, FNT = 256;   // double-float update tile
 
 template <int V>
@@ -503,18 +552,40 @@ size_t up_smem() {
   return ((size_t)V * 2 * Tile<UTX, UTY, V, UNT>::PLANE + 3 * CoarseTile<UTX, UTY, V>::CN) * sizeof(float);
 }
 
-Coef make_coef(const double* c1, const double* c2, int v) {
+Coef make_coef(const double* c1, const double* c2, int v, double h) {
   Coef cf{};
   for (int i = 0; i < v && i < 16; ++i) {
+    double a, b;
+    cheb_constants(c2[i], h, a, b);
     cf.c1[i] = (float)c1[i];
-    cf.c2[i] = (float)c2[i];
+    cf.a[i] = (float)a;
+    cf.b[i] = (float)b;
   }
   return cf;
 }
 
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+      n = 152;
+  }
+  return n;
+}
+
+template <int TX, int TY>
+Sched make_sched(Dims d, int& ctas) {
+  Sched sc;
+  sc.tiles_x = (d.nx + TX - 1) / TX;
+  sc.total = (long long)sc.tiles_x * ((d.ny + TY - 1) / TY) * d.nz;
+  const long long g = sc.total < sm_count() ? sc.total : sm_count();
+  ctas = (int)g;
+  return sc;
+}
+
 template <int V>
-cudaError_t down_v(cudaStream_t st, Dims d, const float* r, float* e, float* rc, int zc, float ih2, float dinv,
-                   const Coef& cf) {
+cudaError_t down_v(cudaStream_t st, Dims d, const float* r, float* e, float* rc, float ih2, const Coef& cf) {
   static bool attr = false;
   const size_t sm = down_smem<V>();
   if (!attr) {
@@ -522,15 +593,16 @@ cudaError_t down_v(cudaStream_t st, Dims d, const float* r, float* e, float* rc,
     if (err != cudaSuccess) return err;
     attr = true;
   }
-  const dim3 grid((d.nx + DTX - 1) / DTX, (d.ny + DTY - 1) / DTY, (d.nz + zc - 1) / zc);
-  k_down_fused<V, DTX, DTY, DNT><<<grid, DNT, sm, st>>>(d, r, e, rc, zc, ih2, dinv, cf);
+  int ctas = 0;
+  const Sched sc = make_sched<DTX, DTY>(d, ctas);
+  k_down_fused<V, DTX, DTY, DNT><<<ctas, DNT, sm, st>>>(d, r, e, rc, sc, ih2, cf);
   note_launch();
   return cudaGetLastError();
 }
 
 template <int V>
-cudaError_t up_v(cudaStream_t st, Dims d, const float* e_in, const float* ec, const float* r, float* e_out, int zc,
-                 float ih2, float dinv, const Coef& cf) {
+cudaError_t up_v(cudaStream_t st, Dims d, const float* e_in, const float* ec, const float* r, float* e_out,
+                 float ih2, const Coef& cf) {
   static bool attr = false;
   const size_t sm = up_smem<V>();
   if (!attr) {
@@ -538,8 +610,9 @@ cudaError_t up_v(cudaStream_t st, Dims d, const float* e_in, const float* ec, co
     if (err != cudaSuccess) return err;
     attr = true;
   }
-  const dim3 grid((d.nx + UTX - 1) / UTX, (d.ny + UTY - 1) / UTY, (d.nz + zc - 1) / zc);
-  k_up_fused<V, UTX, UTY, UNT><<<grid, UNT, sm, st>>>(d, e_in, ec, r, e_out, zc, ih2, dinv, cf);
+  int ctas = 0;
+  const Sched sc = make_sched<UTX, UTY>(d, ctas);
+  k_up_fused<V, UTX, UTY, UNT><<<ctas, UNT, sm, st>>>(d, e_in, ec, r, e_out, sc, ih2, cf);
   note_launch();
   return cudaGetLastError();
 }
@@ -548,49 +621,33 @@ cudaError_t up_v(cudaStream_t st, Dims d, const float* e_in, const float* ec, co
 
 bool fused_degree_supported(int degree) { return degree >= 1 && degree <= 4; }
 
-int fused_zchunk(Dims d) {
-  // z chunk minimising (waves of CTAs) x (iterations per CTA), one CTA per SM:
-  // long chunks amortise the 2V+2 warm-up planes, short ones fill the 152 SMs.
-  const long long tiles = (long long)((d.nx + DTX - 1) / DTX) * ((d.ny + DTY - 1) / DTY);
-  int best = d.nz;
-  long long best_cost = -1;
-  for (int zc = d.nz; zc >= 8; zc = (zc + 1) / 2) {
-    const long long ctas = tiles * ((d.nz + zc - 1) / zc);
-    const long long cost = ((ctas + 151) / 152) * (zc + 8);
-    if (best_cost < 0 || cost < best_cost) {
-      best_cost = cost;
-      best = zc;
-    }
-    if (zc == 8) break;
-  }
-  return best;
-}
-
-cudaError_t launch_down_fused(cudaStream_t st, int degree, Dims d, const float* r, float* e, float* rc, float inv_h2,
-                              float dinv, const double* c1, const double* c2) {
-  const Coef cf = make_coef(c1, c2, degree);
-  const int zc = fused_zchunk(d);
+cudaError_t launch_down_fused(cudaStream_t st, int degree, Dims d, const float* r, float* e, float* rc, double h,
+                              const double* c1, const double* c2) {
+  const Coef cf = make_coef(c1, c2, degree, h);
+  const float ih2 = (float)(1.0 / (h * h));
   switch (degree) {
-    case 1: return down_v<1>(st, d, r, e, rc, zc, inv_h2, dinv, cf);
-    case 2: return down_v<2>(st, d, r, e, rc, zc, inv_h2, dinv, cf);
-    case 3: return down_v<3>(st, d, r, e, rc, zc, inv_h2, dinv, cf);
-    case 4: return down_v<4>(st, d, r, e, rc, zc, inv_h2, dinv, cf);
+    case 1: return down_v<1>(st, d, r, e, rc, ih2, cf);
+    case 2: return down_v<2>(st, d, r, e, rc, ih2, cf);
+    case 3: return down_v<3>(st, d, r, e, rc, ih2, cf);
+    case 4: return down_v<4>(st, d, r, e, rc, ih2, cf);
   }
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_up_fused(cudaStream_t st, int degree, Dims d, const float* e_in, const float* ec, const float* r,
-                            float* e_out, float inv_h2, float dinv, const double* c1, const double* c2) {
-  const Coef cf = make_coef(c1, c2, degree);
-  const int zc = fused_zchunk(d);
+                            float* e_out, double h, const double* c1, const double* c2) {
+  const Coef cf = make_coef(c1, c2, degree, h);
+  const float ih2 = (float)(1.0 / (h * h));
   switch (degree) {
-    case 1: return up_v<1>(st, d, e_in, ec, r, e_out, zc, inv_h2, dinv, cf);
-    case 2: return up_v<2>(st, d, e_in, ec, r, e_out, zc, inv_h2, dinv, cf);
-    case 3: return up_v<3>(st, d, e_in, ec, r, e_out, zc, inv_h2, dinv, cf);
-    case 4: return up_v<4>(st, d, e_in, ec, r, e_out, zc, inv_h2, dinv, cf);
+    case 1: return up_v<1>(st, d, e_in, ec, r, e_out, ih2, cf);
+    case 2: return up_v<2>(st, d, e_in, ec, r, e_out, ih2, cf);
+    case 3: return up_v<3>(st, d, e_in, ec, r, e_out, ih2, cf);
+    case 4: return up_v<4>(st, d, e_in, ec, r, e_out, ih2, cf);
   }
   return cudaErrorInvalidValue;
 }
+
+// ---- double-float update
 
 // z chunk of the double-float update: at least four waves of three CTAs per SM, so
 // that enough loads are in flight; the warm-up costs one plane per chunk.
@@ -607,10 +664,11 @@ long long df_update_residual_partials(Dims d) {
 }
 
 cudaError_t launch_df_update_residual(cudaStream_t st, Dims d, const float2* phi_in, const float* e, const float2* F,
-                                      const double* m_dev, float2* phi_out, float* r_out, double* pr2, double* psum) {
+                                      const double* m_dev, float2* phi_out, float* r_out, double* pr2, double* psum,
+                                      double* pf2) {
   const int zc = df_zchunk(d);
   const dim3 grid((d.nx + FTX - 1) / FTX, (d.ny + FTY - 1) / FTY, (d.nz + zc - 1) / zc);
-  k_df_update_residual<FTX, FTY, FNT><<<grid, FNT, 0, st>>>(d, phi_in, e, F, m_dev, phi_out, r_out, pr2, psum, zc);
+  k_df_update_residual<FTX, FTY, FNT><<<grid, FNT, 0, st>>>(d, phi_in, e, F, m_dev, phi_out, r_out, pr2, psum, pf2, zc);
   note_launch();
   return cudaGetLastError();
 }

@@ -20,12 +20,18 @@ cudaError_t launch_apply(cudaStream_t st, Dims d, const T* u, T* out, T inv_h2);
 template <typename T>
 cudaError_t launch_residual(cudaStream_t st, Dims d, const T* f, const T* u, T* out, T inv_h2,
                             double* partials_sq);
+// Chebyshev step with folded constants a = c2 D^-1, b = a / h^2 (see cheb_step).
 template <typename T>
-cudaError_t launch_cheb_step(cudaStream_t st, Dims d, const T* r, const T* e_in, T* e_out, T* dvec,
-                             T inv_h2, T dinv, T c1, T c2);
+cudaError_t launch_cheb_step(cudaStream_t st, Dims d, const T* r, const T* e_in, T* e_out, T* dvec, T a, T b, T c1);
+// Weighted Jacobi with wa = omega D^-1, wb = wa / h^2.
 template <typename T>
-cudaError_t launch_jacobi(cudaStream_t st, Dims d, const T* r, const T* e_in, T* e_out, T inv_h2,
-                          T w_dinv);
+cudaError_t launch_jacobi(cudaStream_t st, Dims d, const T* r, const T* e_in, T* e_out, T wa, T wb);
+// Folded Chebyshev constants of step k on a level of spacing h.
+inline void cheb_constants(double c2, double h, double& a, double& b) {
+  const double dinv = -(h * h) / 6.0;
+  a = c2 * dinv;
+  b = a * (1.0 / (h * h));
+}
 template <typename T>
 cudaError_t launch_restrict(cudaStream_t st, Dims fine, const T* f, T* c);
 template <typename T>
@@ -56,20 +62,19 @@ long long df_partial_count(long long n);
 
 // ---- temporally blocked FP32 level kernels (Chebyshev smoother) ----
 bool fused_degree_supported(int degree);
-int fused_zchunk(Dims d);
 // e = Chebyshev pre-smoothing of A e = r from e = 0; rc = R (r - A e) on the next level.
 cudaError_t launch_down_fused(cudaStream_t st, int degree, Dims d, const float* r, float* e, float* rc,
-                              float inv_h2, float dinv, const double* c1, const double* c2);
+                              double h, const double* c1, const double* c2);
 // e_out = Chebyshev post-smoothing of A e = r starting from e_in + P ec.
 cudaError_t launch_up_fused(cudaStream_t st, int degree, Dims d, const float* e_in, const float* ec,
-                            const float* r, float* e_out, float inv_h2, float dinv, const double* c1,
-                            const double* c2);
+                            const float* r, float* e_out, double h, const double* c1, const double* c2);
 // Finest level: phi_out = phi_in + e (double-float), r_out = F - m - A phi_out, with block partials
-// of ||r_out||^2 and sum(phi_out) (df_update_residual_partials(d) of each).
+// of ||r_out||^2, sum(phi_out) and (pf2 nullable) ||F - m||^2, df_update_residual_partials(d) each.
+// e NULL: no update (phi_out may then be NULL: not written).
 long long df_update_residual_partials(Dims d);
 cudaError_t launch_df_update_residual(cudaStream_t st, Dims d, const float2* phi_in, const float* e,
                                       const float2* F, const double* m_dev, float2* phi_out, float* r_out,
-                                      double* partials_r2, double* partials_sum);
+                                      double* partials_r2, double* partials_sum, double* partials_f2);
 
 // ---- curvilinear operator (moving mesh) ----
 // Per-level geometry: J = det A and the packed symmetric B = J A^-2 (xx, yy, zz, xy, xz, yz).

@@ -23,19 +23,20 @@ const double* coarse_G<double>(const gbmg_ctx* c) { return c->G64; }
 template <typename T>
 gbmg_status smooth_pass(gbmg_ctx* c, int l, T*& e, T*& eo, const T* r, T* dv, bool post) {
   const Level& L = c->lv[l];
-  const T inv_h2 = (T)(1.0 / (L.h * L.h));
-  const double dinv = -(L.h * L.h) / 6.0;
   if (c->o.smoother == GBMG_SMOOTH_CHEBYSHEV) {
     for (int k = 0; k < c->o.degree; ++k) {
       ProfScope ps(c, l == 0 ? GBMG_PROF_SMOOTH0 : GBMG_PROF_OFF);
-      TRY(launch_cheb_step<T>(c->stream, L.d, r, e, eo, dv, inv_h2, (T)dinv, (T)c->cc1[k], (T)c->cc2[k]));
+      double a, b;
+      cheb_constants(c->cc2[k], L.h, a, b);
+      TRY(launch_cheb_step<T>(c->stream, L.d, r, e, eo, dv, (T)a, (T)b, (T)c->cc1[k]));
       std::swap(e, eo);
     }
   } else {
     const int nu = post ? c->o.nu2 : c->o.nu1;
-    const T wd = (T)(c->o.omega * dinv);
+    const double wa = c->o.omega * (-(L.h * L.h) / 6.0);
+    const double wb = wa * (1.0 / (L.h * L.h));
     for (int k = 0; k < nu; ++k) {
-      TRY(launch_jacobi<T>(c->stream, L.d, r, e, eo, inv_h2, wd));
+      TRY(launch_jacobi<T>(c->stream, L.d, r, e, eo, (T)wa, (T)wb));
       std::swap(e, eo);
     }
   }
@@ -66,13 +67,13 @@ gbmg_status vcycle_unfused(gbmg_ctx* c, int l, T*& e, T*& eo, const T* r) {
   return GBMG_OK;
 }
 
-// Levels of at least 2^21 cells (128^3) use the temporally blocked kernels; below
-// that a level visit is latency-bound and the one-kernel-per-operation chain is
-// faster (a blocked CTA streams its planes one after another).
+// Levels of at least 2^23 cells (about 203^3) use the temporally blocked kernels;
+// below that a level visit is latency-bound and the one-kernel-per-operation chain
+// is faster (each CTA of a blocked kernel streams its planes one after another).
 bool level_fused(const gbmg_ctx* c, int l) {
   const Dims d = c->lv[l].d;
   return c->o.fused && l < c->L - 1 && d.nx >= 16 && d.ny >= 16 && d.nz >= 16 &&
-         (ncell(d) >= (1ll << 21) || c->fused_all);
+         (ncell(d) >= (1ll << 23) || c->fused_all);
 }
 
 // V-cycle in FP32 with the temporally blocked kernels on large levels (one launch per
@@ -88,19 +89,17 @@ gbmg_status vcycle_fused(gbmg_ctx* c, int l, float*& e, const float* r) {
     e = ee;
     return GBMG_OK;
   }
-  const float ih2 = (float)(1.0 / (L.h * L.h));
-  const float dinv = (float)(-(L.h * L.h) / 6.0);
   const Level& C = c->lv[l + 1];
   {
     ProfScope ps(c, l == 0 ? GBMG_PROF_DOWN0 : GBMG_PROF_OFF);
-    TRY(launch_down_fused(c->stream, c->o.degree, L.d, r, (float*)L.e, (float*)C.r, ih2, dinv, c->cc1.data(),
+    TRY(launch_down_fused(c->stream, c->o.degree, L.d, r, (float*)L.e, (float*)C.r, L.h, c->cc1.data(),
                           c->cc2.data()));
   }
   float* ce = nullptr;
   TRYS(vcycle_fused(c, l + 1, ce, (const float*)C.r));
   {
     ProfScope ps(c, l == 0 ? GBMG_PROF_UP0 : GBMG_PROF_OFF);
-    TRY(launch_up_fused(c->stream, c->o.degree, L.d, (const float*)L.e, ce, r, (float*)L.e2, ih2, dinv,
+    TRY(launch_up_fused(c->stream, c->o.degree, L.d, (const float*)L.e, ce, r, (float*)L.e2, L.h,
                         c->cc1.data(), c->cc2.data()));
   }
   e = (float*)L.e2;
@@ -157,9 +156,17 @@ gbmg_status solve_mixed(gbmg_ctx* c, const double* F, double* phi, double tol, i
   TRY(launch_finalize(c->stream, part, pr, sc + S_MEAN_F, 1.0 / (double)n));
   TRY(launch_f64_to_df(c->stream, n, phi, c->phi_df, nullptr));
   float* r0 = (float*)L0.r;
-  TRY(launch_df_residual(c->stream, L0.d, c->F_df, sc + S_MEAN_F, c->phi_df, r0, part, part1));
-  TRY(launch_finalize(c->stream, part, pc, sc + S_R2, 1.0));
-  TRY(launch_finalize(c->stream, part1, pc, sc + S_F2, 1.0));
+  const long long pu = df_update_residual_partials(L0.d);
+  if (c->o.fused) {
+    TRY(launch_df_update_residual(c->stream, L0.d, c->phi_df, nullptr, c->F_df, sc + S_MEAN_F, nullptr, r0, part,
+                                  part2, part1));
+    TRY(launch_finalize(c->stream, part, pu, sc + S_R2, 1.0));
+    TRY(launch_finalize(c->stream, part1, pu, sc + S_F2, 1.0));
+  } else {
+    TRY(launch_df_residual(c->stream, L0.d, c->F_df, sc + S_MEAN_F, c->phi_df, r0, part, part1));
+    TRY(launch_finalize(c->stream, part, pc, sc + S_R2, 1.0));
+    TRY(launch_finalize(c->stream, part1, pc, sc + S_F2, 1.0));
+  }
   double rel;
   TRYS(read_rel(c, rel));
   Monitor mon(st, tol, maxv);
@@ -167,8 +174,7 @@ gbmg_status solve_mixed(gbmg_ctx* c, const double* F, double* phi, double tol, i
   float2* phi_cur = c->phi_df;
   float2* phi_nxt = c->phi_df2;
   float* r_alt = c->r_alt;
-  const long long pu = df_update_residual_partials(L0.d);
-  bool have_sum = false;
+  bool have_sum = c->o.fused;  // the fused residual kernels also sum phi
   while (!mon.done()) {
     if (c->o.fused) {
       float* e = nullptr;
@@ -176,12 +182,11 @@ gbmg_status solve_mixed(gbmg_ctx* c, const double* F, double* phi, double tol, i
       {
         ProfScope ps(c, GBMG_PROF_DF0);
         TRY(launch_df_update_residual(c->stream, L0.d, phi_cur, e, c->F_df, sc + S_MEAN_F, phi_nxt, r_alt, part,
-                                      part2));
+                                      part2, nullptr));
       }
       std::swap(phi_cur, phi_nxt);
       std::swap(r0, r_alt);
       TRY(launch_finalize(c->stream, part, pu, sc + S_R2, 1.0));
-      have_sum = true;
     } else {
       float* e = (float*)L0.e;
       float* eo = (float*)L0.e2;

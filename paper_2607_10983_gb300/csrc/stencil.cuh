@@ -31,26 +31,29 @@ __device__ __forceinline__ T lap_from_sum(T s, T c, T inv_h2) {
   return t_mul(t_fma(T(-6), c, s), inv_h2);
 }
 
-// r - A_l u
+// r - A_l u = r - (s - 6c) / h^2
 template <typename T>
 __device__ __forceinline__ T resid_from_sum(T r, T s, T c, T inv_h2) {
-  return t_sub(r, lap_from_sum(s, c, inv_h2));
+  return t_fma(-inv_h2, t_fma(T(-6), c, s), r);
 }
 
-// One Chebyshev step (Sec. 2.3, Eq. flat_chebyshev, semi-iteration form):
-//   z = D^-1 (r - A e);  d = c1 d + c2 z;  e += d.
-// The first step of a pass uses c1 = 0 (d = z / theta).  Returns the new e, updates d.
+// One Chebyshev step (Sec. 2.3, Eq. flat_chebyshev, semi-iteration form)
+//   z = D^-1 (r - A e);  d = c1 d + c2 z;  e += d,
+// evaluated with the constants folded: a = c2 D^-1, b = a / h^2 (each rounded once
+// on the host), q = a r - b (s - 6c), d = c1 d + q.  The first step of a pass has
+// c1 = 0 (d = z / theta).  Returns the new e, updates d.
 template <typename T>
-__device__ __forceinline__ T cheb_step(T e, T res, T& d, T dinv, T c1, T c2) {
-  const T z = t_mul(dinv, res);
-  d = t_fma(c1, d, t_mul(c2, z));
+__device__ __forceinline__ T cheb_step(T e, T r, T s, T c, T& d, T a, T b, T c1) {
+  const T q = t_fma(-b, t_fma(T(-6), c, s), t_mul(a, r));
+  d = t_fma(c1, d, q);
   return t_add(e, d);
 }
 
-// Weighted Jacobi (Sec. 2.3, Eq. flat_jacobi): e + (omega D^-1) (r - A e)
+// Weighted Jacobi (Sec. 2.3, Eq. flat_jacobi): e + omega D^-1 (r - A e), with
+// wa = omega D^-1 and wb = wa / h^2: e + wa r - wb (s - 6c).
 template <typename T>
-__device__ __forceinline__ T jacobi_step(T e, T res, T w_dinv) {
-  return t_fma(w_dinv, res, e);
+__device__ __forceinline__ T jacobi_step(T e, T r, T s, T c, T wa, T wb) {
+  return t_fma(-wb, t_fma(T(-6), c, s), t_fma(wa, r, e));
 }
 
 // One axis of full weighting: (a + c)/4 + b/2 (Appendix B).
