@@ -158,9 +158,16 @@ def max_over_ranks(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate(world, seq, steps, ms_local):
+    """Whole-job rate: every rank's solves over the slowest rank's time (weak scaling)."""
+    ms_total = max_over_ranks(ms_local, world)
+    return ms_total, world * seq * steps / (ms_total / 1000.0)
 
 
 def sources(n, seq, rank):
@@ -277,11 +284,10 @@ def run_ours(args):
         torch.cuda.synchronize()
     barrier(world)
     launches = gb.launch_count() - launches0
-    ms_total = max_over_ranks(ev0.elapsed_time(ev1), world)
+    ms_total, value = aggregate(world, seq, args.steps, ev0.elapsed_time(ev1))
     prof = {f: solver.profile_read(f) for f in families}
     solver.profile_end()
     ms_per_step = ms_total / args.steps
-    value = world * seq * args.steps / (ms_total / 1000.0)
 
     hbm_peak, peak_kind = measured_peaks()
     kernels = {}
@@ -322,7 +328,13 @@ def run_ours(args):
     if not args.no_extras and rank == 0:
         line["e2e"] = e2e_leg(args, solver, host_src)
         line["baselines"] = baseline_legs(args, F, dev)
+        line["fixed_2_cycles"] = fixed_cycles_leg(args, solver, F)
         del F
+        del phi
+        solver.close()
+        torch.cuda.empty_cache()
+        line["differentiable_256"] = differentiable_leg(args, dev)
+        line["moving_mesh_256"] = moving_mesh_leg(args, dev)
         torch.cuda.empty_cache()
         line["batched_48"] = batched_leg(args)
         line["cpu_baseline"] = oracle_sample(n, seq, args.tol)
@@ -407,8 +419,136 @@ def baseline_legs(args, F, dev):
         torch.cuda.synchronize()
         out[name] = {"solves_per_s": 3 / (ev0.elapsed_time(ev1) / 1000.0),
                      "note": "rfftn, divide by the 7-point symbol, irfftn; inputs resident"}
-        del srcs
+        sol = solve(srcs[0]).double()
+        if name == "cufft_fp64":
+            ref64 = sol
+        else:
+            out[name]["rel_l2_vs_fp64"] = float(torch.linalg.vector_norm(sol - ref64)
+                                                / torch.linalg.vector_norm(ref64))
+        del srcs, sol
     return out
+
+
+def fixed_cycles_leg(args, solver, F):
+    """The sequence at the paper's warm-start operating point: t = 0 solved to tol, each later
+    source warm-started from the previous phi with at most 2 V-cycles (residual reported)."""
+    import torch
+    phi = torch.zeros_like(F[0])
+    solver.solve(F[0], phi, tol=args.tol, max_vcycles=args.max_vcycles)
+    phi.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rel = []
+    for t in range(len(F)):
+        _, st = solver.solve(F[t], phi, tol=args.tol, max_vcycles=args.max_vcycles if t == 0 else 2)
+        rel.append(st.rel_res)
+    dt = time.perf_counter() - t0
+    return {"solves_per_s": len(F) / dt, "rel_res_per_source": rel,
+            "note": "t = 0 to the tolerance, t >= 1 at most 2 V-cycles (status NOT_CONVERGED allowed)"}
+
+
+def _timed(fn):
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = fn()
+    torch.cuda.synchronize()
+    return out, 1000.0 * (time.perf_counter() - t0)
+
+
+def differentiable_leg(args, dev):
+    """256^3 differentiable flat solve: loss = sum(w . grad4 phi), phi = solve(F) (mixed, to 1e-6);
+    backward = adjoint solve.  Forward and backward wall times, and the gradient against central
+    differences of the same GPU loss (solves to 1e-10) in 4 seeded source directions."""
+    import numpy as np
+    import torch
+
+    import paper_2607_10983_gb300 as gb
+    from synth import grf, vector_noise
+    n = 256
+    F = torch.from_numpy(grf(n, 4)).to(dev)
+    w = torch.from_numpy(vector_noise(n, 5)).to(dev, torch.float32)
+    s = gb.Solver(n)
+
+    def fwd():
+        Fd = F.clone().requires_grad_(True)
+        return Fd, gb.GradDotLoss.apply(gb.MGSolve.apply(Fd, s, args.tol, args.max_vcycles), w, s, 4)
+
+    fwd()[1].backward()                      # warm-up
+    (Fd, loss), t_fwd = _timed(fwd)
+    _, t_bwd = _timed(loss.backward)
+    g = Fd.grad
+
+    def L(FF):
+        ph, _ = s.solve(FF, tol=1e-10, max_vcycles=60)
+        return float(s.grad_dot(ph, w, 4))
+
+    Fd2 = F.clone().requires_grad_(True)
+    gb.GradDotLoss.apply(gb.MGSolve.apply(Fd2, s, 1e-10, 60), w, s, 4).backward()
+    worst = 0.0
+    for seed in range(100, 104):
+        v = torch.from_numpy(np.random.default_rng(seed).standard_normal((n, n, n))).to(dev)
+        fd = (L(F + 1e-3 * v) - L(F - 1e-3 * v)) / 2e-3
+        worst = max(worst, abs(fd - float((Fd2.grad * v).sum())) / max(1.0, abs(fd)))
+    s.close()
+    del g
+    return {"forward_ms": t_fwd, "backward_ms": t_bwd, "fd_max_rel_diff": worst,
+            "workload": "256^3 flat, F seed 4, w seed 5 (FP32), tol 1e-6 timed; FD eps 1e-3, directions seeds 100..103"}
+
+
+def moving_mesh_leg(args, dev):
+    """256^3 moving-mesh solve (19-point curvilinear operator of psi, FP32 coefficients,
+    double-float refinement to 1e-6) and its adjoint (delta_bar, psi_bar): wall times, cycles,
+    the finest-level Jacobi sweep's device time and GB/s, and central differences of the
+    GPU loss sum(w . grad2 phi) in one delta and one psi direction."""
+    import numpy as np
+    import torch
+
+    import paper_2607_10983_gb300 as gb
+    from synth import grf, smoothed_grf, vector_noise
+    n = 256
+    psi = torch.from_numpy(smoothed_grf(n, 6, 4.0, 0.5)).to(dev)
+    delta = torch.from_numpy(grf(n, 7)).to(dev)
+    w = torch.from_numpy(vector_noise(n, 8).astype(np.float64)).to(dev)
+    s = gb.Solver(n, op="curv")
+    pbar = s.grad_T(w.to(torch.float32), 2)
+    s.solve(delta, tol=args.tol, max_vcycles=100, psi=psi)        # warm-up
+    s.profile_begin(["curv0", "df0"])
+    (phi, st), t_fwd = _timed(lambda: s.solve(delta, tol=args.tol, max_vcycles=100, psi=psi))
+    prof = {f: s.profile_read(f) for f in ("curv0", "df0")}
+    s.profile_end()
+    (res_adj), t_adj = _timed(lambda: s.solve_adjoint(pbar, phi=phi, source=delta, want_psi_bar=True,
+                                                      tol=args.tol, max_vcycles=100))
+    _, _, st_adj = res_adj
+    hbm_peak, _ = measured_peaks()
+    cells = n ** 3
+    kern = {}
+    for f, bpc in (("curv0", 40.0), ("df0", 48.0)):
+        cnt, kms = prof[f]
+        if cnt:
+            gbs = bpc * cells / (kms / cnt / 1000.0) / 1e9
+            kern[f] = {"launches": cnt, "avg_ms": kms / cnt, "bytes_per_cell": bpc, "achieved_gbs": gbs,
+                       "frac": gbs / hbm_peak}
+    # gradient check at 1e-10
+    phi_t, _ = s.solve(delta, tol=1e-10, max_vcycles=200, psi=psi)
+    dbar, psibar, _ = s.solve_adjoint(pbar, phi=phi_t, source=delta, want_psi_bar=True, tol=1e-10, max_vcycles=200)
+
+    def L(d, p):
+        ph, _ = s.solve(d, tol=1e-10, max_vcycles=200, psi=p)
+        return float((w * s.grad(ph, 2)).sum())
+
+    v = torch.from_numpy(np.random.default_rng(300).standard_normal((n, n, n))).to(dev)
+    fd = (L(delta + 1e-3 * v, psi) - L(delta - 1e-3 * v, psi)) / 2e-3
+    d_rel = abs(fd - float((dbar * v).sum())) / max(1.0, abs(fd))
+    dp = torch.from_numpy(smoothed_grf(n, 400, 4.0, 0.5)).to(dev)
+    fd = (L(delta, psi + 1e-2 * dp) - L(delta, psi - 1e-2 * dp)) / 2e-2
+    p_rel = abs(fd - float((psibar * dp).sum())) / max(1.0, abs(fd))
+    s.close()
+    return {"forward_ms": t_fwd, "forward_cycles": st.cycles, "forward_rel_res": st.rel_res,
+            "adjoint_ms": t_adj, "adjoint_cycles": st_adj.cycles, "kernels": kern,
+            "fd_rel_diff": {"delta": d_rel, "psi": p_rel},
+            "workload": "256^3, psi seed 6 (Gaussian-smoothed GRF, sigma 4, Gershgorin |Hess psi| 0.5), "
+                        "delta seed 7, w seed 8; V(2,2) Jacobi, tol 1e-6 timed; FD eps 1e-3 (delta), 1e-2 (psi)"}
 
 
 def batched_leg(args):
@@ -423,7 +563,11 @@ def batched_leg(args):
     F = [torch.from_numpy(grf(s, 1000 + i)).cuda() for i, s in enumerate(shapes)]
     phis = [torch.zeros_like(f) for f in F]
     batch = gb.Batch(shapes, degree=args.degree)
-    blocks = batch.autotune(F, phis, tol=args.tol, max_vcycles=args.max_vcycles)
+    blocks, tiles = batch.autotune(F, phis, tol=args.tol, max_vcycles=args.max_vcycles)
+    batch.use_graph(True)
+    for p in phis:
+        p.zero_()
+    batch.solve(F, phis, tol=args.tol, max_vcycles=args.max_vcycles)   # captures the graph
     reps = 3
     lat, total = [], 0.0
     for _ in range(reps):
@@ -437,7 +581,7 @@ def batched_leg(args):
         if any(st.status != 0 for st in stats):
             raise RuntimeError("batched solve did not converge")
     out = {"batched": {"solves_per_s": len(shapes) * reps / total, "p50_ms": float(np.percentile(lat, 50)),
-                       "p99_ms": float(np.percentile(lat, 99)), "blocks": blocks,
+                       "p99_ms": float(np.percentile(lat, 99)), "blocks": blocks, "tiles": tiles, "cuda_graph": True,
                        "cycles_per_solve": float(np.mean([st.cycles for st in stats]))}}
     batch.close()
     solvers = {s: gb.Solver(s, degree=args.degree) for s in set(shapes)}

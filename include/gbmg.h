@@ -168,11 +168,28 @@ gbmg_status mg_batch_create(gbmg_batch** out, gbmg_ctx* const* ctxs, int count, 
 void mg_batch_destroy(gbmg_batch* batch);
 /* Persistent grid size in blocks (default and maximum: every block resident). */
 gbmg_status mg_batch_set_blocks(gbmg_batch* batch, int blocks);
-/* Time one solve with each candidate grid size (1..max blocks per SM times the SM
- * count) and keep the fastest; fields as for mg_batch_solve (phi is overwritten).
- * *blocks_out (nullable) receives the choice. */
+/* Tile size per level: the number of consecutive cells (whole x rows of one problem)
+ * one block takes in each grid-wide phase on level l, for l < nlevels.  Each size is a
+ * multiple of 256 in [1024, 65536]; the default is 4096.  Rebuilds the tile tables
+ * (waits for the stream).  Sizes change the schedule and the summation order of the
+ * per-problem norms and means, nothing else. */
+gbmg_status mg_batch_set_tiles(gbmg_batch* batch, const int* tile_cells, int nlevels);
+/* Current tile sizes of levels 0 .. nlevels-1 (0 beyond the deepest level). */
+gbmg_status mg_batch_get_tiles(const gbmg_batch* batch, int* tile_cells, int nlevels);
+/* on != 0: run each solve as a CUDA graph (captured at the first solve on a stream of
+ * the batch's own, replayed while tol, max_vcycles, grid and tile sizes are unchanged;
+ * ordered after earlier and before later work on the batch's stream).  Off by default. */
+gbmg_status mg_batch_use_graph(gbmg_batch* batch, int on);
+/* Number of levels of the deepest problem (length of the tile-size array). */
+int mg_batch_num_levels(const gbmg_batch* batch);
+/* Autotuner: times full solves and keeps the fastest settings, first the grid size
+ * (1 .. resident blocks per SM, times the SM count), then, level by level, the tile
+ * size (1024, 2048, ... 65536 cells).  Every trial starts from the initial guesses in
+ * phi_dev (saved in temporary device buffers, released before returning); on return
+ * phi_dev holds the solution from those guesses with the chosen settings.
+ * *blocks_out and tiles_out[0 .. levels-1] (both nullable) receive the choice. */
 gbmg_status mg_batch_autotune(gbmg_batch* batch, const double* const* source_dev, double* const* phi_dev,
-                              double tol, int max_vcycles, int* blocks_out);
+                              double tol, int max_vcycles, int* blocks_out, int* tiles_out);
 /* Solve every problem: source_dev[i] / phi_dev[i] as for mg_solve on ctxs[i] (phi is
  * the initial guess in and the solution out).  Waits for the stream.  stats (array of
  * count, nullable) per problem; times_ms (array of count, nullable) receives each
@@ -190,7 +207,8 @@ typedef enum {
   GBMG_PROF_DOWN0 = 1,   /* finest level, fused pre-smoothing + residual + restriction  */
   GBMG_PROF_UP0 = 2,     /* finest level, fused prolongation + post-smoothing            */
   GBMG_PROF_DF0 = 3,     /* finest level, double-float update and residual               */
-  GBMG_PROF_SMOOTH0 = 4  /* finest level, one-kernel-per-operation smoother steps        */
+  GBMG_PROF_SMOOTH0 = 4, /* finest level, one-kernel-per-operation smoother steps        */
+  GBMG_PROF_CURV0 = 5    /* finest level, curvilinear weighted-Jacobi sweeps             */
 } gbmg_prof_family;
 
 /* Start timing the kernel families whose bits (1 << family) are set in family_mask

@@ -106,12 +106,17 @@ _SIGS = {
     "mg_batch_create": (_S, [ctypes.POINTER(_P), ctypes.POINTER(_P), _I, _P]),
     "mg_batch_destroy": (None, [_P]),
     "mg_batch_set_blocks": (_S, [_P, _I]),
-    "mg_batch_autotune": (_S, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _D, _I, ctypes.POINTER(_I)]),
+    "mg_batch_set_tiles": (_S, [_P, ctypes.POINTER(_I), _I]),
+    "mg_batch_get_tiles": (_S, [_P, ctypes.POINTER(_I), _I]),
+    "mg_batch_num_levels": (_I, [_P]),
+    "mg_batch_use_graph": (_S, [_P, _I]),
+    "mg_batch_autotune": (_S, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _D, _I, ctypes.POINTER(_I),
+                               ctypes.POINTER(_I)]),
     "mg_batch_solve": (_S, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _D, _I, ctypes.POINTER(_Stats),
                             ctypes.POINTER(_D)]),
 }
 
-PROF = {"down0": 1, "up0": 2, "df0": 3, "smooth0": 4}
+PROF = {"down0": 1, "up0": 2, "df0": 3, "smooth0": 4, "curv0": 5}
 
 
 def launch_count() -> int:
@@ -397,14 +402,31 @@ class Batch:
             raise ValueError("one field per problem expected")
         return (_P * len(fields))(*[_ptr(f, dtype, sv.shape) for f, sv in zip(fields, self.solvers)])
 
-    def autotune(self, sources, phis, tol=1e-6, max_vcycles=50) -> int:
+    def autotune(self, sources, phis, tol=1e-6, max_vcycles=50) -> tuple[int, list[int]]:
+        """Pick the grid size and the per-level tile sizes by timing solves from the guesses in phis
+        (which end up holding the solutions).  Returns (blocks, tiles)."""
         blocks = _I()
+        nl = lib().mg_batch_num_levels(self._b)
+        tiles = (_I * nl)()
         _check(lib().mg_batch_autotune(self._b, self._ptrs(sources), self._ptrs(phis), float(tol), int(max_vcycles),
-                                       ctypes.byref(blocks)))
-        return blocks.value
+                                       ctypes.byref(blocks), tiles))
+        return blocks.value, list(tiles)
 
     def set_blocks(self, blocks: int):
         _check(lib().mg_batch_set_blocks(self._b, int(blocks)))
+
+    def use_graph(self, on: bool = True):
+        _check(lib().mg_batch_use_graph(self._b, 1 if on else 0))
+
+    def tiles(self) -> list[int]:
+        nl = lib().mg_batch_num_levels(self._b)
+        t = (_I * nl)()
+        _check(lib().mg_batch_get_tiles(self._b, t, nl))
+        return list(t)
+
+    def set_tiles(self, tiles):
+        t = (_I * len(tiles))(*[int(x) for x in tiles])
+        _check(lib().mg_batch_set_tiles(self._b, t, len(tiles)))
 
     def solve(self, sources, phis, tol=1e-6, max_vcycles=50):
         """Solve all problems; phis are initial guesses in, solutions out.  Returns (stats, times_ms)."""

@@ -7,7 +7,8 @@
 // first residual), then V-cycles of the one-kernel-per-operation arithmetic (same
 // per-cell code, so each problem's iterates equal those of mg_solve with fused = 0),
 // each operation a grid-wide phase separated by grid.sync().  Work inside a phase is
-// split into chunks of CHUNK cells that belong to one problem, so per-problem sums
+// split into chunks (tiles of whole x rows, a per-level size) that belong to one
+// problem, so per-problem sums
 // are deterministic (chunk partials summed in order).  A problem that has converged
 // (or failed) skips its chunks; the loop ends when none is active or max_vcycles is
 // reached.  Per-problem completion times come from %globaltimer.
@@ -28,7 +29,9 @@ using namespace gbmg;
 namespace {
 
 constexpr int BMAXL = 16;
-constexpr int CHUNK = 4096;
+constexpr int CHUNK = 4096;      // default tile (chunk) size in cells
+constexpr int MINCHUNK = 1024;   // smallest tile the tables are sized for
+constexpr int MAXCHUNK = 65536;
 constexpr int BT = 256;
 
 // per-problem scalars
@@ -54,6 +57,7 @@ struct BProb {
 
 struct BDesc {
   int count, maxL, degree, maxv;
+  int chunk[BMAXL];  // tile (chunk) size in cells per level
   double tol;
   float c1[16];
   double c2[16];
@@ -110,7 +114,7 @@ __device__ __forceinline__ void phase(const BDesc& B, int l, Want want, Op op) {
     if (!want(P, l)) continue;
     const long long s0 = B.cstart[l][c];
     const long long n = ncell(P.d[l]);
-    const long long s1 = s0 + CHUNK < n ? s0 + CHUNK : n;
+    const long long s1 = s0 + B.chunk[l] < n ? s0 + B.chunk[l] : n;
     for (long long i = s0 + threadIdx.x; i < s1; i += blockDim.x) op(P, l, i);
   }
 }
@@ -124,7 +128,7 @@ __device__ __forceinline__ void phase0_sum(const BDesc& B, double* part, double*
     const BProb& P = B.p[pi];
     const long long s0 = B.cstart[0][c];
     const long long n = ncell(P.d[0]);
-    const long long s1 = s0 + CHUNK < n ? s0 + CHUNK : n;
+    const long long s1 = s0 + B.chunk[0] < n ? s0 + B.chunk[0] : n;
     DfAcc acc{0.f, 0.f};
     for (long long i = s0 + threadIdx.x; i < s1; i += blockDim.x) op(P, i, acc);
     const double b = block_sum_acc(acc, sh);
@@ -168,7 +172,7 @@ __global__ void __launch_bounds__(BT) k_batched_solve(BDesc B) {
       const float2 m = f64_to_df(B.sc[pi * P_N + P_MEAN]);
       const long long s0 = B.cstart[0][c];
       const long long n = ncell(d);
-      const long long s1 = s0 + CHUNK < n ? s0 + CHUNK : n;
+      const long long s1 = s0 + B.chunk[0] < n ? s0 + B.chunk[0] : n;
       float r2 = 0.f, f2 = 0.f;
       for (long long i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
         int x, y, z;
@@ -397,7 +401,7 @@ __global__ void __launch_bounds__(BT) k_batched_solve(BDesc B) {
     ms.y = -ms.y;
     const long long s0 = B.cstart[0][c];
     const long long n = ncell(P.d[0]);
-    const long long s1 = s0 + CHUNK < n ? s0 + CHUNK : n;
+    const long long s1 = s0 + B.chunk[0] < n ? s0 + B.chunk[0] : n;
     for (long long i = s0 + threadIdx.x; i < s1; i += blockDim.x) P.out[i] = df_to_f64(df_add(P.phi[i], ms));
   }
 }
@@ -411,6 +415,7 @@ struct gbmg_batch {
   int device = 0;
   char* mem = nullptr;  // device memory of the descriptor tables and results
   BDesc desc{};
+  int cap[BMAXL] = {};     // chunk-table capacity per level (tiles of MINCHUNK cells)
   BProb* hprob = nullptr;  // pinned host copy of the problem table
   int* hstatus = nullptr;  // pinned host results
   int* hcycles = nullptr;
@@ -420,12 +425,68 @@ struct gbmg_batch {
   unsigned long long* htime = nullptr;
   unsigned long long* htstart = nullptr;
   size_t res_bytes = 0;
+  // CUDA graph of one solve (copy-in, resets, the cooperative launch, copy-out),
+  // captured on a private stream and replayed while its key is unchanged
+  bool use_graph = false;
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t gev[2] = {nullptr, nullptr};
+  cudaGraphExec_t gexec = nullptr;
+  unsigned version = 0, g_version = ~0u;
+  double g_tol = -1.0;
+  int g_maxv = -1, g_blocks = -1;
   ~gbmg_batch() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (gstream) cudaStreamDestroy(gstream);
+    for (auto ev : gev)
+      if (ev) cudaEventDestroy(ev);
     if (mem) cudaFree(mem);
     if (hprob) cudaFreeHost(hprob);
     if (hstatus) cudaFreeHost(hstatus);
   }
 };
+
+namespace {
+
+long long ceil_div(long long a, long long b) { return (a + b - 1) / b; }
+
+// Chunk tables of every level for the current tile sizes desc.chunk[], uploaded
+// synchronously after the batch's stream has drained.
+gbmg_status build_tables(gbmg_batch* b) {
+  BDesc& D = b->desc;
+  TRY(cudaStreamSynchronize(b->stream));
+  for (int l = 0; l < b->maxL; ++l) {
+    std::vector<int> cprob;
+    std::vector<long long> cstart;
+    for (int i = 0; i < b->count; ++i) {
+      const gbmg_ctx* c = b->ctx[i];
+      if (l >= c->L) continue;
+      const long long n = ncell(c->lv[l].d);
+      if (l == 0) b->hprob[i].c0 = (int)cprob.size();
+      for (long long s = 0; s < n; s += D.chunk[l]) {
+        cprob.push_back(i);
+        cstart.push_back(s);
+      }
+      if (l == 0) b->hprob[i].nch = (int)cprob.size() - b->hprob[i].c0;
+    }
+    if ((long long)cprob.size() > b->cap[l]) return fail(GBMG_ERR_INVALID_ARG, "batch: tile table overflow");
+    TRY(cudaMemcpy(D.cprob[l], cprob.data(), sizeof(int) * cprob.size(), cudaMemcpyHostToDevice));
+    TRY(cudaMemcpy(D.cstart[l], cstart.data(), sizeof(long long) * cstart.size(), cudaMemcpyHostToDevice));
+    D.nchunk[l] = (int)cprob.size();
+  }
+  b->version += 1;
+  return GBMG_OK;
+}
+
+gbmg_status max_blocks(const gbmg_batch* b, int& blocks) {
+  int per_sm = 0, sms = 0;
+  TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched_solve, BT, 0));
+  TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+  if (per_sm < 1) return fail(GBMG_ERR_CUDA, "batch: kernel does not fit on an SM");
+  blocks = per_sm * sms;
+  return GBMG_OK;
+}
+
+}  // namespace
 
 extern "C" gbmg_status mg_batch_create(gbmg_batch** out, gbmg_ctx* const* ctxs, int count, void* cuda_stream) {
   g_last_error.clear();
@@ -451,22 +512,12 @@ extern "C" gbmg_status mg_batch_create(gbmg_batch** out, gbmg_ctx* const* ctxs, 
   int maxL = 0;
   for (auto* c : b->ctx) maxL = std::max(maxL, c->L);
   b->maxL = maxL;
-  // chunk tables
-  std::vector<std::vector<int>> cprob(maxL);
-  std::vector<std::vector<long long>> cstart(maxL);
-  std::vector<int> c0(count), nch(count);
-  for (int l = 0; l < maxL; ++l)
-    for (int i = 0; i < count; ++i) {
-      const gbmg_ctx* c = b->ctx[i];
-      if (l >= c->L) continue;
-      const long long n = ncell(c->lv[l].d);
-      if (l == 0) c0[i] = (int)cprob[0].size();
-      for (long long s = 0; s < n; s += CHUNK) {
-        cprob[l].push_back(i);
-        cstart[l].push_back(s);
-      }
-      if (l == 0) nch[i] = (int)cprob[0].size() - c0[i];
-    }
+  for (int l = 0; l < maxL; ++l) {
+    long long cap = 0;
+    for (auto* c : b->ctx)
+      if (l < c->L) cap += ceil_div(ncell(c->lv[l].d), MINCHUNK);
+    b->cap[l] = (int)cap;
+  }
   // device layout
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -477,10 +528,10 @@ extern "C" gbmg_status mg_batch_create(gbmg_batch** out, gbmg_ctx* const* ctxs, 
   const size_t oP = take(sizeof(BProb) * count);
   std::vector<size_t> ocp(maxL), ocs(maxL);
   for (int l = 0; l < maxL; ++l) {
-    ocp[l] = take(sizeof(int) * cprob[l].size());
-    ocs[l] = take(sizeof(long long) * cstart[l].size());
+    ocp[l] = take(sizeof(int) * b->cap[l]);
+    ocs[l] = take(sizeof(long long) * b->cap[l]);
   }
-  const size_t n0 = cprob[0].size();
+  const size_t n0 = (size_t)b->cap[0];
   const size_t oP0 = take(sizeof(double) * n0), oP1 = take(sizeof(double) * n0);
   const size_t oSc = take(sizeof(double) * P_N * count);
   // results block (copied back together): status, cycles, hist, rel0, times
@@ -522,7 +573,7 @@ extern "C" gbmg_status mg_batch_create(gbmg_batch** out, gbmg_ctx* const* ctxs, 
   for (int l = 0; l < maxL; ++l) {
     D.cprob[l] = (int*)(m + ocp[l]);
     D.cstart[l] = (long long*)(m + ocs[l]);
-    D.nchunk[l] = (int)cprob[l].size();
+    D.chunk[l] = CHUNK;
   }
   D.part0 = (double*)(m + oP0);
   D.part1 = (double*)(m + oP1);
@@ -551,27 +602,14 @@ extern "C" gbmg_status mg_batch_create(gbmg_batch** out, gbmg_ctx* const* ctxs, 
     P.G = c->G32;
     P.F = c->F_df;
     P.phi = c->phi_df;
-    P.c0 = c0[i];
-    P.nch = nch[i];
   }
-  for (int l = 0; l < maxL; ++l) {
-    e = cudaMemcpy(D.cprob[l], cprob[l].data(), sizeof(int) * cprob[l].size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-      e = cudaMemcpy(D.cstart[l], cstart[l].data(), sizeof(long long) * cstart[l].size(), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
-      delete b;
-      return cuda_fail(e, "mg_batch_create: upload");
-    }
-  }
+  gbmg_status st = build_tables(b);
   // persistent grid: every block resident at once (cooperative launch)
-  int per_sm = 0, sms = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched_solve, BT, 0);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-  if (e != cudaSuccess || per_sm < 1) {
+  if (st == GBMG_OK) st = max_blocks(b, b->blocks);
+  if (st != GBMG_OK) {
     delete b;
-    return e != cudaSuccess ? cuda_fail(e, "mg_batch_create: occupancy") : fail(GBMG_ERR_CUDA, "mg_batch_create: kernel does not fit");
+    return st;
   }
-  b->blocks = per_sm * sms;
   *out = b;
   return GBMG_OK;
 }
@@ -580,15 +618,37 @@ extern "C" void mg_batch_destroy(gbmg_batch* b) { delete b; }
 
 extern "C" gbmg_status mg_batch_set_blocks(gbmg_batch* b, int blocks) {
   if (!b || blocks < 1) return fail(GBMG_ERR_INVALID_ARG, "mg_batch_set_blocks: bad argument");
-  int per_sm = 0, sms = 0;
   DeviceGuard g(b->device);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched_solve, BT, 0) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess)
-    return fail(GBMG_ERR_CUDA, "mg_batch_set_blocks: occupancy query failed");
-  if (blocks > per_sm * sms) return fail(GBMG_ERR_INVALID_ARG, "mg_batch_set_blocks: more blocks than can be resident");
+  int most = 0;
+  TRYS(max_blocks(b, most));
+  if (blocks > most) return fail(GBMG_ERR_INVALID_ARG, "mg_batch_set_blocks: more blocks than can be resident");
   b->blocks = blocks;
   return GBMG_OK;
 }
+
+extern "C" gbmg_status mg_batch_use_graph(gbmg_batch* b, int on) {
+  if (!b) return fail(GBMG_ERR_INVALID_ARG, "mg_batch_use_graph: NULL batch");
+  b->use_graph = on != 0;
+  return GBMG_OK;
+}
+
+extern "C" gbmg_status mg_batch_set_tiles(gbmg_batch* b, const int* tile_cells, int nlevels) {
+  if (!b || !tile_cells || nlevels < 1) return fail(GBMG_ERR_INVALID_ARG, "mg_batch_set_tiles: bad argument");
+  for (int l = 0; l < nlevels && l < b->maxL; ++l)
+    if (tile_cells[l] < MINCHUNK || tile_cells[l] > MAXCHUNK || tile_cells[l] % BT != 0)
+      return fail(GBMG_ERR_INVALID_ARG, "mg_batch_set_tiles: tile sizes must be multiples of 256 in [1024, 65536]");
+  DeviceGuard g(b->device);
+  for (int l = 0; l < nlevels && l < b->maxL; ++l) b->desc.chunk[l] = tile_cells[l];
+  return build_tables(b);
+}
+
+extern "C" gbmg_status mg_batch_get_tiles(const gbmg_batch* b, int* tile_cells, int nlevels) {
+  if (!b || !tile_cells) return fail(GBMG_ERR_INVALID_ARG, "mg_batch_get_tiles: bad argument");
+  for (int l = 0; l < nlevels; ++l) tile_cells[l] = l < b->maxL ? b->desc.chunk[l] : 0;
+  return GBMG_OK;
+}
+
+extern "C" int mg_batch_num_levels(const gbmg_batch* b) { return b ? b->maxL : 0; }
 
 extern "C" gbmg_status mg_batch_solve(gbmg_batch* b, const double* const* src_dev, double* const* phi_dev, double tol,
                                       int max_vcycles, gbmg_stats* stats, double* times_ms) {
@@ -604,14 +664,56 @@ extern "C" gbmg_status mg_batch_solve(gbmg_batch* b, const double* const* src_de
   BDesc D = b->desc;
   D.tol = tol;
   D.maxv = max_vcycles < 0 ? 0 : max_vcycles;
-  TRY(cudaMemcpyAsync(D.p, b->hprob, sizeof(BProb) * b->count, cudaMemcpyHostToDevice, b->stream));
-  TRY(cudaMemsetAsync(D.status, 0, sizeof(int) * b->count, b->stream));
-  TRY(cudaMemsetAsync(D.cycles, 0, sizeof(int) * b->count, b->stream));
-  void* args[] = {&D};
-  TRY(cudaLaunchCooperativeKernel((void*)k_batched_solve, dim3(b->blocks), dim3(BT), args, 0, b->stream));
+  // the whole solve as one stream-ordered sequence
+  auto enqueue = [&](cudaStream_t st) -> gbmg_status {
+    TRY(cudaMemcpyAsync(D.p, b->hprob, sizeof(BProb) * b->count, cudaMemcpyHostToDevice, st));
+    TRY(cudaMemsetAsync(D.status, 0, sizeof(int) * b->count, st));
+    TRY(cudaMemsetAsync(D.cycles, 0, sizeof(int) * b->count, st));
+    void* args[] = {&D};
+    TRY(cudaLaunchCooperativeKernel((void*)k_batched_solve, dim3(b->blocks), dim3(BT), args, 0, st));
+    TRY(cudaMemcpyAsync(b->hstatus, D.status, b->res_bytes, cudaMemcpyDeviceToHost, st));
+    TRY(cudaMemcpyAsync(b->hsc, D.sc, sizeof(double) * P_N * b->count, cudaMemcpyDeviceToHost, st));
+    return GBMG_OK;
+  };
+  if (!b->use_graph) {
+    TRYS(enqueue(b->stream));
+  } else {
+    if (!b->gstream) {
+      TRY(cudaStreamCreateWithFlags(&b->gstream, cudaStreamNonBlocking));
+      TRY(cudaEventCreateWithFlags(&b->gev[0], cudaEventDisableTiming));
+      TRY(cudaEventCreateWithFlags(&b->gev[1], cudaEventDisableTiming));
+    }
+    if (!b->gexec || b->g_version != b->version || b->g_tol != tol || b->g_maxv != D.maxv ||
+        b->g_blocks != b->blocks) {
+      if (b->gexec) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+      }
+      cudaGraph_t graph = nullptr;
+      TRY(cudaStreamBeginCapture(b->gstream, cudaStreamCaptureModeThreadLocal));
+      const gbmg_status cs = enqueue(b->gstream);
+      const cudaError_t ce = cudaStreamEndCapture(b->gstream, &graph);
+      if (cs != GBMG_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return cs;
+      }
+      TRY(ce);
+      const cudaError_t ie = cudaGraphInstantiate(&b->gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      TRY(ie);
+      b->g_version = b->version;
+      b->g_tol = tol;
+      b->g_maxv = D.maxv;
+      b->g_blocks = b->blocks;
+    }
+    // order the graph after earlier work on the caller's stream and before later work
+    TRY(cudaEventRecord(b->gev[0], b->stream));
+    TRY(cudaStreamWaitEvent(b->gstream, b->gev[0], 0));
+    TRY(cudaGraphLaunch(b->gexec, b->gstream));
+    TRY(cudaEventRecord(b->gev[1], b->gstream));
+    TRY(cudaStreamWaitEvent(b->stream, b->gev[1], 0));
+  }
   note_launch();
-  TRY(cudaMemcpyAsync(b->hstatus, D.status, b->res_bytes, cudaMemcpyDeviceToHost, b->stream));
-  TRY(cudaMemcpyAsync(b->hsc, D.sc, sizeof(double) * P_N * b->count, cudaMemcpyDeviceToHost, b->stream));
   TRY(cudaStreamSynchronize(b->stream));
   gbmg_status worst = GBMG_OK;
   const unsigned long long t0 = *b->htstart;
@@ -633,40 +735,82 @@ extern "C" gbmg_status mg_batch_solve(gbmg_batch* b, const double* const* src_de
   return worst;
 }
 
+namespace {
+
+// One timed trial from the saved initial guesses.
+gbmg_status trial(gbmg_batch* b, const double* const* src, double* const* phi, double* const* save, double tol,
+                  int maxv, cudaEvent_t e0, cudaEvent_t e1, float& ms) {
+  for (int i = 0; i < b->count; ++i)
+    TRY(cudaMemcpyAsync(phi[i], save[i], sizeof(double) * ncell(b->ctx[i]->lv[0].d), cudaMemcpyDeviceToDevice,
+                        b->stream));
+  TRY(cudaEventRecord(e0, b->stream));
+  const gbmg_status s = mg_batch_solve(b, src, phi, tol, maxv, nullptr, nullptr);
+  if (s == GBMG_ERR_CUDA || s == GBMG_ERR_INVALID_ARG || s == GBMG_ERR_OOM) return s;
+  TRY(cudaEventRecord(e1, b->stream));
+  TRY(cudaEventSynchronize(e1));
+  TRY(cudaEventElapsedTime(&ms, e0, e1));
+  return GBMG_OK;
+}
+
+}  // namespace
+
 extern "C" gbmg_status mg_batch_autotune(gbmg_batch* b, const double* const* src_dev, double* const* phi_dev,
-                                         double tol, int max_vcycles, int* blocks_out) {
-  if (!b) return fail(GBMG_ERR_INVALID_ARG, "mg_batch_autotune: NULL batch");
+                                         double tol, int max_vcycles, int* blocks_out, int* tiles_out) {
+  if (!b || !src_dev || !phi_dev) return fail(GBMG_ERR_INVALID_ARG, "mg_batch_autotune: NULL argument");
   DeviceGuard g(b->device);
-  int per_sm = 0, sms = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched_solve, BT, 0) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess)
-    return fail(GBMG_ERR_CUDA, "mg_batch_autotune: occupancy query failed");
-  cudaEvent_t e0, e1;
-  TRY(cudaEventCreate(&e0));
-  TRY(cudaEventCreate(&e1));
-  int best = b->blocks;
-  float best_ms = -1.f;
-  for (int k = 1; k <= per_sm; ++k) {
-    b->blocks = k * sms;
-    TRY(cudaEventRecord(e0, b->stream));
-    const gbmg_status s = mg_batch_solve(b, src_dev, phi_dev, tol, max_vcycles, nullptr, nullptr);
-    if (s == GBMG_ERR_CUDA || s == GBMG_ERR_INVALID_ARG) {
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
-      return s;
+  int most = 0, sms = 0;
+  TRYS(max_blocks(b, most));
+  TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+  // every trial starts from the caller's initial guesses
+  std::vector<double*> save(b->count, nullptr);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  gbmg_status st = GBMG_OK;
+  auto run = [&]() -> gbmg_status {
+    for (int i = 0; i < b->count; ++i) {
+      const size_t bytes = sizeof(double) * ncell(b->ctx[i]->lv[0].d);
+      TRY(cudaMalloc((void**)&save[i], bytes));
+      TRY(cudaMemcpyAsync(save[i], phi_dev[i], bytes, cudaMemcpyDeviceToDevice, b->stream));
     }
-    TRY(cudaEventRecord(e1, b->stream));
-    TRY(cudaEventSynchronize(e1));
-    float ms = 0.f;
-    TRY(cudaEventElapsedTime(&ms, e0, e1));
-    if (best_ms < 0.f || ms < best_ms) {
-      best_ms = ms;
-      best = b->blocks;
+    TRY(cudaEventCreate(&e0));
+    TRY(cudaEventCreate(&e1));
+    float ms = 0.f, best_ms = -1.f;
+    // grid size: 1 .. (resident blocks per SM) times the SM count
+    int best = b->blocks;
+    for (int blocks = sms; blocks <= most; blocks += sms) {
+      b->blocks = blocks;
+      TRYS(trial(b, src_dev, phi_dev, save.data(), tol, max_vcycles, e0, e1, ms));
+      if (best_ms < 0.f || ms < best_ms) best_ms = ms, best = blocks;
     }
-  }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  b->blocks = best;
-  if (blocks_out) *blocks_out = best;
+    b->blocks = best;
+    // tile size per level, one level at a time (coordinate descent from the current sizes)
+    for (int l = 0; l < b->maxL; ++l) {
+      long long biggest = 0;
+      for (auto* c : b->ctx)
+        if (l < c->L) biggest = std::max(biggest, ncell(c->lv[l].d));
+      int keep = b->desc.chunk[l];
+      for (int cand = MINCHUNK; cand <= MAXCHUNK; cand *= 2) {
+        if (cand == keep || (cand > biggest && cand / 2 >= biggest)) continue;
+        b->desc.chunk[l] = cand;
+        TRYS(build_tables(b));
+        TRYS(trial(b, src_dev, phi_dev, save.data(), tol, max_vcycles, e0, e1, ms));
+        if (ms < best_ms) best_ms = ms, keep = cand;
+      }
+      b->desc.chunk[l] = keep;
+      TRYS(build_tables(b));
+    }
+    // leave the caller's phi holding the solution from the initial guesses
+    TRYS(trial(b, src_dev, phi_dev, save.data(), tol, max_vcycles, e0, e1, ms));
+    return GBMG_OK;
+  };
+  st = run();
+  cudaStreamSynchronize(b->stream);
+  for (double* p : save)
+    if (p) cudaFree(p);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st != GBMG_OK) return st;
+  if (blocks_out) *blocks_out = b->blocks;
+  if (tiles_out)
+    for (int l = 0; l < b->maxL; ++l) tiles_out[l] = b->desc.chunk[l];
   return GBMG_OK;
 }

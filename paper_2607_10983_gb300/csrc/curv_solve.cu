@@ -32,6 +32,7 @@ template <typename T>
 gbmg_status curv_smooth(gbmg_ctx* c, int l, T*& e, T*& eo, const T* r, int nu, bool tr) {
   const Level& L = c->lv[l];
   for (int k = 0; k < nu; ++k) {
+    ProfScope ps(c, l == 0 ? GBMG_PROF_CURV0 : GBMG_PROF_OFF);
     TRY(launch_curv_jacobi<T>(c->stream, L.d, L.cc, r, e, eo, tr ? 1 : 0, (T)c->o.omega));
     std::swap(e, eo);
   }
