@@ -72,7 +72,8 @@ typedef struct {
   double omega;  /* Jacobi weight                                                  */
   int fused;     /* temporally blocked level kernels (GBMG_MIXED + Chebyshev):       */
                  /* 1: on levels of at least 2^23 cells, 2: on every level of at   */
-                 /* least 16^3 (results are identical), 0: one kernel per operation */
+                 /* least 16^3 (results are identical), 0: one kernel per operation; */
+                 /* an odd nx selects 0 (the fused kernels work on pairs of x cells) */
 } gbmg_opts;
 
 typedef struct {

@@ -2,13 +2,16 @@
 // the next defect-correction residual r' = F - m - A phi' (Sec. 3.2) in one pass.
 //
 // A CTA owns an output tile of TX x TY cells in (x, y) and a chunk of z planes; it
-// updates phi on the tile plus a one-cell halo, keeps the current plane in a padded,
-// double-buffered shared-memory plane (x/y neighbours) and the two older z planes in
-// registers, and forms the residual one plane behind.  One barrier per plane.
+// updates phi on the tile plus a one-cell halo and forms the residual one plane
+// behind.  Work unit: the pair of x-neighbouring cells, with the error-free
+// double-float sums done by packed FP32x2 instructions lane by lane (bit-identical to
+// the scalar double-float kernels).  A thread owns a column of R pairs; shared memory
+// holds the updated planes split by x parity and hi/lo part, in a ring of three; the
+// z window stays in registers.  One barrier per plane.
 #include <cstdio>
 
 #include "kernels.h"
-#include "stencil.cuh"
+#include "packed.cuh"
 
 namespace gbmg {
 
@@ -19,138 +22,157 @@ __device__ __forceinline__ int wrapmod(int i, int n) {
   return r < 0 ? r + n : r;
 }
 
-template <int TX, int TY, int H, int NT>
-struct Tile {
-  static constexpr int WX = TX + 2 * H;
-  static constexpr int WY = TY + 2 * H;
-  static constexpr int NPOS = WX * WY;
-  static constexpr int K = (NPOS + NT - 1) / NT;  // positions per thread
-  static constexpr int PAD = WX + 1;              // padding so p +- 1, p +- WX stay in bounds
-  // every thread slot (valid or not) owns a plane entry, so no slot needs a guard
-  static constexpr int PLANE = K * NT + 2 * PAD;
-};
-
-// Per-thread position bookkeeping: plane offset of each owned position in the
-// (wrapped) global mesh, and bit masks of valid / in-tile positions.
-template <int TX, int TY, int H, int NT>
-struct Positions {
-  using TL = Tile<TX, TY, H, NT>;
-  int goff[TL::K];
-  unsigned vmask = 0, tmask = 0;
-  __device__ __forceinline__ void init(Dims d, int x0, int y0) {
-#pragma unroll
-    for (int k = 0; k < TL::K; ++k) {
-      const int p = threadIdx.x + k * NT;
-      goff[k] = 0;
-      if (p < TL::NPOS) {
-        const int px = p % TL::WX, py = p / TL::WX;
-        const int ux = x0 - H + px, uy = y0 - H + py;
-        goff[k] = wrapmod(ux, d.nx) + wrapmod(uy, d.ny) * d.nx;
-        vmask |= 1u << k;
-        if (px >= H && px < H + TX && py >= H && py < H + TY && ux < d.nx && uy < d.ny) tmask |= 1u << k;
-      }
-    }
-  }
-};
-
 // ------------------------------------------------------------------ finest level, double-float
 
+// Tile of the double-float kernel: x-pairs with a one-pair halo in x (one cell is
+// needed), one row of halo in y, columns of R pairs per thread, even/odd cells and
+// hi/lo parts in four separate arrays per plane, three planes in a ring (z - 1, z,
+// z + 1 of the update).
+template <int TX_, int TY_, int R_, int NT_>
+struct DTile {
+  static constexpr int TX = TX_, TY = TY_, R = R_, NT = NT_;
+  static constexpr int WXP = TX / 2 + 2;                      // pairs per haloed row
+  static constexpr int WY = TY + 2;                           // haloed rows
+  static constexpr int NCOL = WXP * ((WY + R - 1) / R);
+  static constexpr int WS = conflict_free_stride(WXP, R);     // row stride of the arrays
+  static constexpr int ROWS = (NT + WXP - 1) / WXP * R;       // idle threads included
+  static constexpr int PAD = WS + 1;
+  static constexpr int ARR = ROWS * WS + 2 * PAD;             // floats of one array
+  static constexpr int PLANE = 4 * ARR;                       // even hi, even lo, odd hi, odd lo
+  static_assert(NCOL <= NT, "one column per thread");
+};
+
+__device__ __forceinline__ DF2 ld_df2(const float2* p) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  return DF2{make_float2(v.x, v.z), make_float2(v.y, v.w)};
+}
+__device__ __forceinline__ void st_df2(float2* p, const DF2& v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v.hi.x, v.lo.x, v.hi.y, v.lo.y);
+}
+
 // phi' = phi + e (double-float) on the tile plus a one-cell halo, then
-// r' = F - m - A phi' on the tile; block partial sums of r'^2 and of phi'.
-// Loads of the next plane are issued before the current plane is processed.
-template <int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT)
+// r' = F - m - A phi' on the tile, one plane behind; block partial sums of r'^2,
+// of phi' and (pf2 non-null) of (F - m)^2.  e NULL: phi' = phi (first residual of a
+// solve); phi_out NULL: phi' is not stored.  Loads of the next plane are issued
+// before the current plane is processed; the plane loop is unrolled by three so the
+// z window (registers) and the plane ring (shared memory) need no copies.
+template <class TL>
+__global__ void __launch_bounds__(TL::NT, 2)
 k_df_update_residual(Dims d, const float2* __restrict__ phi_in, const float* __restrict__ e,
                      const float2* __restrict__ F, const double* __restrict__ m_dev, float2* __restrict__ phi_out,
                      float* __restrict__ r_out, double* __restrict__ pr2, double* __restrict__ psum,
                      double* __restrict__ pf2, int zc) {
-  constexpr int H = 1;
-  using TL = Tile<TX, TY, H, NT>;
-  constexpr int WX = TL::WX, K = TL::K, PLANE = TL::PLANE, PAD = TL::PAD;
-  __shared__ float2 sp[2][PLANE];
+  constexpr int R = TL::R, WXP = TL::WXP, WS = TL::WS, ARR = TL::ARR, PLANE = TL::PLANE, PAD = TL::PAD;
+  extern __shared__ float smf[];
   __shared__ double shr[32];
   const int tid = threadIdx.x;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * zc;
+  const int x0 = blockIdx.x * TL::TX, y0 = blockIdx.y * TL::TY, z0 = blockIdx.z * zc;
   const int zend = min(z0 + zc, d.nz);
   const long long pst = (long long)d.nx * d.ny;
-  Positions<TX, TY, H, NT> P;
-  P.init(d, x0, y0);
-  const float2 m = f64_to_df(m_dev[0]);
-  float2 wp[K], wc[K];
-  float2 nphi[K], fq[K];
-  float ne[K];
+  // the thread's column of pairs
+  const int px = tid % WXP, pyb = tid / WXP;
+  const int p0 = pyb * R * WS + px;
+  const int ux = x0 - 2 + 2 * px;
+  int goff[R];
+  unsigned tmask = 0;
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    const int py = pyb * R + j, uy = y0 - 1 + py;
+    goff[j] = wrapmod(ux, d.nx) + wrapmod(uy, d.ny) * d.nx;
+    if (tid < TL::NCOL && px >= 1 && px <= TL::TX / 2 && py >= 1 && py <= TL::TY && ux < d.nx && uy < d.ny)
+      tmask |= 1u << j;
+  }
+  const float2 m1 = f64_to_df(m_dev[0]);
+  const DF2 m{bcast(m1.x), bcast(m1.y)};
+  const float2 Z = bcast(0.f);
+  DF2 W[3][R];        // the update at planes t (W[u]), t - 1, t - 2 of the ring
+  DF2 nphi[R], fq[R];
+  float2 ne[R];
   float r2 = 0.f, f2 = 0.f;
-  DfAcc ps{0.f, 0.f};
+  PAcc ps{Z, Z};
 #pragma unroll
-  for (int k = 0; k < K; ++k) wp[k] = wc[k] = fq[k] = make_float2(0.f, 0.f);
+  for (int j = 0; j < R; ++j) {
+    fq[j] = DF2{Z, Z};
+    ne[j] = Z;
 #pragma unroll
-  for (int k = 0; k < K; ++k) ne[k] = 0.f;
+    for (int u = 0; u < 3; ++u) W[u][j] = DF2{Z, Z};
+  }
   const int tb = z0 - 1, te = zend;
   auto load = [&](int t) {
     const long long base = (long long)wrapmod(t, d.nz) * pst;
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const bool v = P.vmask >> k & 1u;
-      nphi[k] = v ? phi_in[base + P.goff[k]] : make_float2(0.f, 0.f);
-      if (e) ne[k] = v ? __ldg(e + base + P.goff[k]) : 0.f;
+    for (int j = 0; j < R; ++j) {
+      nphi[j] = ld_df2(phi_in + base + goff[j]);
+      if (e) ne[j] = __ldg(reinterpret_cast<const float2*>(e + base + goff[j]));
     }
   };
   load(tb);
-  for (int t = tb; t <= te; ++t) {
-    const int cur = (t - tb) & 1, prv = cur ^ 1;
-    const long long base = (long long)wrapmod(t, d.nz) * pst;
-    float2 pn[K];
-    float2 fcur[K];
+  int t = tb;
+  while (t <= te) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      pn[k] = e ? df_add_f(nphi[k], ne[k]) : nphi[k];
-      fcur[k] = fq[k];
-    }
-    if (t < te) {
-      load(t + 1);
-      // F of the plane whose residual the next iteration computes (plane t)
-      if (t >= z0 && t < zend) {
+    for (int u = 0; u < 3; ++u, ++t) {
+      if (t > te) break;
+      float* const cur = smf + u * PLANE + PAD;            // plane t
+      const float* const ctr = smf + ((u + 2) % 3) * PLANE + PAD;  // plane t - 1
+      DF2 fcur[R];
 #pragma unroll
-        for (int k = 0; k < K; ++k) fq[k] = (P.tmask >> k & 1u) ? F[base + P.goff[k]] : make_float2(0.f, 0.f);
+      for (int j = 0; j < R; ++j) {
+        W[u][j] = e ? p_df_add_f(nphi[j], ne[j]) : nphi[j];
+        fcur[j] = fq[j];
       }
-    }
+      const long long base = (long long)wrapmod(t, d.nz) * pst;
+      if (t < te) {
+        load(t + 1);
+        // F of the plane whose residual the next iteration forms (plane t)
+        if (t >= z0 && t < zend) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      if (P.vmask >> k & 1u) {
-        sp[cur][PAD + tid + k * NT] = pn[k];
-        if ((P.tmask >> k & 1u) && t >= z0 && t < zend) {
-          if (phi_out) phi_out[base + P.goff[k]] = pn[k];
-          ps.add(pn[k].x);
-          ps.c += pn[k].y;
+          for (int j = 0; j < R; ++j) fq[j] = (tmask >> j & 1u) ? ld_df2(F + base + goff[j]) : DF2{Z, Z};
         }
       }
-    }
-    const int zp = t - 1;
-    if (zp >= z0 && zp < zend) {
-      const float2* src = sp[prv] + PAD;
-      const long long pbase = (long long)zp * pst;
+      const bool in_chunk = t >= z0 && t < zend;
 #pragma unroll
-      for (int k = 0; k < K; ++k) {
-        if (P.tmask >> k & 1u) {
-          const int p = tid + k * NT;
-          const long long gi = pbase + P.goff[k];
-          const float rv = df_resid(wc[k], src[p - 1], src[p + 1], src[p - WX], src[p + WX], wp[k], pn[k], fcur[k], m);
-          r_out[gi] = rv;
-          r2 += rv * rv;
-          const float fv = __fadd_rn(__fsub_rn(fcur[k].x, m.x), __fsub_rn(fcur[k].y, m.y));
-          f2 += fv * fv;
+      for (int j = 0; j < R; ++j) {
+        const int p = p0 + j * WS;
+        const DF2 v = W[u][j];
+        cur[p] = v.hi.x;
+        cur[p + ARR] = v.lo.x;
+        cur[p + 2 * ARR] = v.hi.y;
+        cur[p + 3 * ARR] = v.lo.y;
+        if ((tmask >> j & 1u) && in_chunk) {
+          if (phi_out) st_df2(phi_out + base + goff[j], v);
+          ps.add(v.hi);
+          ps.c = p_add(ps.c, v.lo);
         }
       }
-    }
+      const int zp = t - 1;
+      if (zp >= z0 && zp < zend) {
+        const long long pbase = (long long)zp * pst;
+        auto at = [&](int q) { return DF2{make_float2(ctr[q], ctr[q + 2 * ARR]), make_float2(ctr[q + ARR], ctr[q + 3 * ARR])}; };
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      wp[k] = wc[k];
-      wc[k] = pn[k];
+        for (int j = 0; j < R; ++j) {
+          if (!(tmask >> j & 1u)) continue;
+          const int p = p0 + j * WS;
+          const DF2 c = W[(u + 2) % 3][j];
+          const DF2 ym = j > 0 ? W[(u + 2) % 3][j - 1] : at(p - WS);
+          const DF2 yp = j < R - 1 ? W[(u + 2) % 3][j + 1] : at(p + WS);
+          const float2 rv = p_df_resid(c, ctr[p - 1 + 2 * ARR], ctr[p - 1 + 3 * ARR], ctr[p + 1], ctr[p + 1 + ARR], ym,
+                                       yp, W[(u + 1) % 3][j], W[u][j], fcur[j], m);
+          *reinterpret_cast<float2*>(r_out + pbase + goff[j]) = rv;
+          r2 = __fmaf_rn(rv.x, rv.x, r2);
+          r2 = __fmaf_rn(rv.y, rv.y, r2);
+          const float2 fv = p_add(p_sub(fcur[j].hi, m.hi), p_sub(fcur[j].lo, m.lo));
+          f2 = __fmaf_rn(fv.x, fv.x, f2);
+          f2 = __fmaf_rn(fv.y, fv.y, f2);
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
+  DfAcc acc{ps.s.x, ps.c.x};
+  acc.add(ps.s.y);
+  acc.c += ps.c.y;
   const double b2 = block_sum_f(r2, shr);
-  const double bs = block_sum_acc(ps, shr);
+  const double bs = block_sum_acc(acc, shr);
   const double bf = pf2 ? block_sum_f(f2, shr) : 0.0;
   if (tid == 0) {
     const int bid = block_linear_id();
@@ -160,32 +182,41 @@ k_df_update_residual(Dims d, const float2* __restrict__ phi_in, const float* __r
   }
 }
 
-constexpr int FTX = 64, FTY = 16, FNT = 256;   // double-float update tile
+using DFT = DTile<64, 16, 2, 320>;
+
 
 }  // namespace
 
 // ---- double-float update
 
-// z chunk of the double-float update: at least four waves of three CTAs per SM, so
-// that enough loads are in flight; the warm-up costs one plane per chunk.
+// z chunk of the double-float update: at least four waves of two CTAs per SM, so that
+// enough loads are in flight; the warm-up costs one plane per chunk.
 int df_zchunk(Dims d) {
-  const long long tiles = (long long)((d.nx + FTX - 1) / FTX) * ((d.ny + FTY - 1) / FTY);
+  const long long tiles = (long long)((d.nx + DFT::TX - 1) / DFT::TX) * ((d.ny + DFT::TY - 1) / DFT::TY);
   int zc = d.nz;
-  while (zc > 16 && tiles * ((d.nz + zc - 1) / zc) < 4 * 3 * 152) zc = (zc + 1) / 2;
+  while (zc > 16 && tiles * ((d.nz + zc - 1) / zc) < 4 * 2 * 152) zc = (zc + 1) / 2;
   return zc;
 }
 
 long long df_update_residual_partials(Dims d) {
   const int zc = df_zchunk(d);
-  return (long long)((d.nx + FTX - 1) / FTX) * ((d.ny + FTY - 1) / FTY) * ((d.nz + zc - 1) / zc);
+  return (long long)((d.nx + DFT::TX - 1) / DFT::TX) * ((d.ny + DFT::TY - 1) / DFT::TY) * ((d.nz + zc - 1) / zc);
 }
 
 cudaError_t launch_df_update_residual(cudaStream_t st, Dims d, const float2* phi_in, const float* e, const float2* F,
                                       const double* m_dev, float2* phi_out, float* r_out, double* pr2, double* psum,
                                       double* pf2) {
+  if (d.nx % 2) return cudaErrorInvalidValue;  // x-pairs
+  static bool attr = false;
+  const size_t sm = 3 * (size_t)DFT::PLANE * sizeof(float);
+  if (!attr) {
+    cudaError_t err = cudaFuncSetAttribute(k_df_update_residual<DFT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (err != cudaSuccess) return err;
+    attr = true;
+  }
   const int zc = df_zchunk(d);
-  const dim3 grid((d.nx + FTX - 1) / FTX, (d.ny + FTY - 1) / FTY, (d.nz + zc - 1) / zc);
-  k_df_update_residual<FTX, FTY, FNT><<<grid, FNT, 0, st>>>(d, phi_in, e, F, m_dev, phi_out, r_out, pr2, psum, pf2, zc);
+  const dim3 grid((d.nx + DFT::TX - 1) / DFT::TX, (d.ny + DFT::TY - 1) / DFT::TY, (d.nz + zc - 1) / zc);
+  k_df_update_residual<DFT><<<grid, DFT::NT, sm, st>>>(d, phi_in, e, F, m_dev, phi_out, r_out, pr2, psum, pf2, zc);
   note_launch();
   return cudaGetLastError();
 }

@@ -216,6 +216,7 @@ extern "C" gbmg_status mg_setup(gbmg_ctx** out, int nx, int ny, int nz, int leve
   if (o.fused && !(o.op == GBMG_OP_FLAT7 && o.prec == GBMG_MIXED && o.smoother == GBMG_SMOOTH_CHEBYSHEV &&
                    fused_degree_supported(o.degree)))
     o.fused = 0;
+  if (o.fused && nx % 2 != 0) o.fused = 0;  // the fused kernels work on x-pairs
   const bool curv = o.op == GBMG_OP_CURV19;
 
   std::vector<Dims> dims = level_dims(nx, ny, nz, levels);

@@ -26,7 +26,7 @@
 // tile-major list and CTA b runs the contiguous range [b T / G, (b+1) T / G), as one
 // z segment per tile it touches (each segment with its own warm-up planes).
 #include "kernels.h"
-#include "stencil.cuh"
+#include "packed.cuh"
 
 namespace gbmg {
 
@@ -42,68 +42,7 @@ __device__ __forceinline__ int mod3(int v) {
   return r < 0 ? r + 3 : r;
 }
 
-// ------------------------------------------------------------------ packed pairs
-
-__device__ __forceinline__ float2 p_add(float2 a, float2 b) {
-  float2 d;
-  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
-      "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-      : "=f"(d.x), "=f"(d.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-  return d;
-}
-__device__ __forceinline__ float2 p_mul(float2 a, float2 b) {
-  float2 d;
-  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
-      "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-      : "=f"(d.x), "=f"(d.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-  return d;
-}
-__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) {
-  float2 d;
-  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
-      "mov.b64 rc, {%6, %7};\n\tfma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-      : "=f"(d.x), "=f"(d.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
-  return d;
-}
-__device__ __forceinline__ float2 bcast(float v) { return make_float2(v, v); }
-
-// nbr_sum of the pair: the x neighbours of the even cell are (xm, c.y), those of
-// the odd cell (c.x, xp); then y, then z, in the order of the scalar nbr_sum.
-__device__ __forceinline__ float2 p_nbr_sum(float xm, float xp, float2 c, float2 ym, float2 yp, float2 zm,
-                                            float2 zp) {
-  float2 s = make_float2(t_add(xm, c.y), t_add(c.x, xp));
-  s = p_add(s, p_add(ym, yp));
-  return p_add(s, p_add(zm, zp));
-}
-// cheb_step on a pair (folded constants a, -b, c1 broadcast)
-__device__ __forceinline__ float2 p_cheb(float2 e, float2 r, float2 s, float2 c, float2& d, float2 a, float2 mb,
-                                         float2 c1) {
-  const float2 q = p_fma(mb, p_fma(bcast(-6.f), c, s), p_mul(a, r));
-  d = p_fma(c1, d, q);
-  return p_add(e, d);
-}
-// resid_from_sum on a pair (mih2 = -1/h^2 broadcast)
-__device__ __forceinline__ float2 p_resid(float2 r, float2 s, float2 c, float2 mih2) {
-  return p_fma(mih2, p_fma(bcast(-6.f), c, s), r);
-}
-__device__ __forceinline__ float2 p_fw3(float2 a, float2 b, float2 c) {
-  return p_fma(bcast(0.25f), p_add(a, c), p_mul(bcast(0.5f), b));
-}
-__device__ __forceinline__ float2 p_half_sum(float2 a, float2 b) { return p_mul(bcast(0.5f), p_add(a, b)); }
-
 // ------------------------------------------------------------------ tile geometry
-
-// Smallest row stride (in pairs) >= wxp for which a warp whose 32 consecutive
-// threads straddle two row blocks still reads 32 distinct banks: the jump between
-// the blocks, r * ws - (wxp - 1), must equal 1 modulo 32.  wxp itself if none exists.
-constexpr int conflict_free_stride(int wxp, int r) {
-  for (int ws = wxp; ws < wxp + 32; ++ws)
-    if ((r * ws - wxp) % 32 == 0) return ws;
-  return wxp;
-}
 
 template <int TX_, int TY_, int H_, int NT_, int R_>
 struct PTile {
