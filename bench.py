@@ -55,6 +55,8 @@ def parse():
     p.add_argument("--no-fused", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip e2e, baselines and CPU oracle legs")
     p.add_argument("--max-vcycles", type=int, default=40)
+    p.add_argument("--print-source-digests", action="store_true",
+                   help="print the source digest of each profiled kernel family and exit")
     return p.parse_args()
 
 
@@ -67,19 +69,37 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+KERNEL_SOURCES = {
+    "down0": ["legs.cu", "packed.cuh", "stencil.cuh", "common.cuh", "kernels.h"],
+    "up0": ["legs.cu", "packed.cuh", "stencil.cuh", "common.cuh", "kernels.h"],
+    "df0": ["fused_kernels.cu", "packed.cuh", "stencil.cuh", "common.cuh", "kernels.h"],
+}
+
+
+def kernel_source_digest(family):
+    """sha256 (first 16 hex digits) of the sources that define a kernel family."""
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES[family]:
+        with open(os.path.join(ROOT, "paper_2607_10983_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def ncu_traffic(family):
-    """DRAM bytes per cell of a kernel from a committed ncu summary, if the kernel source is unchanged."""
-    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    """DRAM bytes per cell of a kernel family from the committed ncu summary table
+    (profiles/ncu_traffic.md), or None when the kernel's sources changed since."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.md")
     try:
         with open(path) as fh:
-            d = json.load(fh)
-        src = os.path.join(ROOT, d["source"])
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        if digest != d["source_sha256_16"]:
-            return None
-        return d["kernels"].get(family)
-    except Exception:
+            for line in fh:
+                cols = [c.strip() for c in line.strip().strip("|").split("|")]
+                if len(cols) >= 5 and cols[0] == family:
+                    if cols[4] != kernel_source_digest(family):
+                        return None
+                    return float(cols[3])
+    except (OSError, ValueError, KeyError):
         return None
+    return None
 
 
 class Clocks:
@@ -609,6 +629,10 @@ def batched_leg(args):
 
 def main():
     args = parse()
+    if args.print_source_digests:
+        for f in KERNEL_SOURCES:
+            print(f, kernel_source_digest(f))
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
