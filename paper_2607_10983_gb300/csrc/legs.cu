@@ -479,16 +479,18 @@ k_up_fused(Dims d, const float* __restrict__ e_in, const float* __restrict__ ec,
 
 // ------------------------------------------------------------------ launch
 
-// Tiles per degree: 64 x 32 cells, columns of R = 4 pairs, 384 threads (block sizes
-// are multiples of 128 threads: registers are granted to groups of four warps).
-// The degree-4 down leg (halo 5) uses 64 x 24 so its columns still fit 384 threads.
+// Tiles per degree: 64 x 32 cells; block sizes are multiples of 128 threads
+// (registers are granted to groups of four warps).  Down leg: columns of R = 4 pairs,
+// 384 threads (the degree-4 leg, halo 5, uses 64 x 24 so its columns still fit).
+// Up leg: columns of R = 3 pairs, 512 threads (16 warps per SM; measured faster than
+// 4-pair columns for this leg, slower for the down leg, whose state per pair is larger).
 template <int V>
 struct DownTile {
   using T = PTile<64, (V >= 4 ? 24 : 32), V + 1, 384, 4>;
 };
 template <int V>
 struct UpTile {
-  using T = PTile<64, 32, V, 384, 4>;
+  using T = PTile<64, 32, V, 512, 3>;
 };
 
 template <int V>
