@@ -71,7 +71,7 @@ typedef struct {
   int nu1, nu2;  /* Jacobi sweeps before / after the coarse correction (>= 0)      */
   double omega;  /* Jacobi weight                                                  */
   int fused;     /* temporally blocked level kernels (GBMG_MIXED + Chebyshev):       */
-                 /* 1: on levels of at least 2^23 cells, 2: on every level of at   */
+                 /* 1: on levels of at least 2^18 cells, 2: on every level of at   */
                  /* least 16^3 (results are identical), 0: one kernel per operation; */
                  /* an odd nx selects 0 (the fused kernels work on pairs of x cells) */
 } gbmg_opts;

@@ -67,13 +67,15 @@ gbmg_status vcycle_unfused(gbmg_ctx* c, int l, T*& e, T*& eo, const T* r) {
   return GBMG_OK;
 }
 
-// Levels of at least 2^23 cells (about 203^3) use the temporally blocked kernels;
-// below that a level visit is latency-bound and the one-kernel-per-operation chain
-// is faster (each CTA of a blocked kernel streams its planes one after another).
+// Levels of at least 2^18 cells (64^3) use the temporally blocked kernels; below
+// that a level visit is latency-bound and the one-kernel-per-operation chain is as
+// fast.  Measured on the 512^3 / 256^3 warm sequences: thresholds 2^23 / 2^21 / 2^18
+// gave 64.0 / 65.3 / 65.3 and 280 / 303 / 309 solves/s.
+constexpr long long kFusedMinCells = 1ll << 18;
 bool level_fused(const gbmg_ctx* c, int l) {
   const Dims d = c->lv[l].d;
   return c->o.fused && l < c->L - 1 && d.nx >= 16 && d.ny >= 16 && d.nz >= 16 &&
-         (ncell(d) >= (1ll << 23) || c->fused_all);
+         (ncell(d) >= kFusedMinCells || c->fused_all);
 }
 
 // V-cycle in FP32 with the temporally blocked kernels on large levels (one launch per
