@@ -55,6 +55,8 @@ def parse():
     p.add_argument("--no-fused", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip e2e, baselines and CPU oracle legs")
     p.add_argument("--max-vcycles", type=int, default=40)
+    p.add_argument("--only", choices=["moving_mesh", "differentiable", "batched", "fixed_2_cycles"],
+                   help="run one extra workload alone and print its JSON object (no headline line)")
     p.add_argument("--print-source-digests", action="store_true",
                    help="print the source digest of each profiled kernel family and exit")
     return p.parse_args()
@@ -627,11 +629,36 @@ def batched_leg(args):
     return out
 
 
+def run_only(args):
+    import torch
+
+    from paper_2607_10983_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    if args.only == "moving_mesh":
+        out = moving_mesh_leg(args, dev)
+    elif args.only == "differentiable":
+        out = differentiable_leg(args, dev)
+    elif args.only == "batched":
+        out = batched_leg(args)
+    else:
+        import paper_2607_10983_gb300 as gb
+        F = [torch.from_numpy(a).to(dev) for a in sources(args.n, args.seq, 0)]
+        solver = gb.Solver(args.n, prec="mixed", degree=args.degree, fused=not args.no_fused)
+        out = fixed_cycles_leg(args, solver, F)
+        solver.close()
+    print(json.dumps({args.only: out}))
+
+
 def main():
     args = parse()
     if args.print_source_digests:
         for f in KERNEL_SOURCES:
             print(f, kernel_source_digest(f))
+        return
+    if args.only:
+        run_only(args)
         return
     if args.impl == "reference":
         run_reference(args)

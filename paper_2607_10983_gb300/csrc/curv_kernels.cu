@@ -289,14 +289,9 @@ __device__ __forceinline__ void df_acc_prod(DfAcc& acc, float w, float2 v) {
   acc.c += pe + w * v.y;
 }
 
-struct DfFieldAt {
-  const float2* __restrict__ p;
-  const Nbhd* nb;
-  __device__ __forceinline__ float2 operator()(int dx, int dy, int dz) const { return p[(*nb)(dx, dy, dz)]; }
-};
-
 // acc += h^2 (M u) (forward) with u double-float, every flux difference in double-float.
-__device__ __forceinline__ void df_apply_M(DfAcc& acc, const DfFieldAt& u, const CoefAt& Bc, float sign) {
+template <typename UF, typename BF>
+__device__ __forceinline__ void df_apply_M(DfAcc& acc, const UF& u, const BF& Bc, float sign) {
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
 #pragma unroll
@@ -326,7 +321,8 @@ __device__ __forceinline__ void df_apply_M(DfAcc& acc, const DfFieldAt& u, const
 }
 
 // acc += sign * h^2 (M^T y) with y double-float.
-__device__ __forceinline__ void df_apply_MT(DfAcc& acc, const DfFieldAt& y, const CoefAt& Bc, float sign) {
+template <typename UF, typename BF>
+__device__ __forceinline__ void df_apply_MT(DfAcc& acc, const UF& y, const BF& Bc, float sign) {
   auto q = [&](float w, int a, int b, int cx, int cy, int cz) {
     int px = cx, py = cy, pz = cz;
     shift(a, 1, px, py, pz);
@@ -353,47 +349,6 @@ __device__ __forceinline__ void df_apply_MT(DfAcc& acc, const DfFieldAt& y, cons
       q(w, a, b, m2x, m2y, m2z);
       q(-w, a, b, p2x, p2y, p2z);
     }
-  }
-}
-
-// r = (b - op(u) / h^2) / J rounded to float, with b = J (src - m) when scale_J (forward
-// source in L-form) or b = src (transposed solve, M-form right-hand side).  Partial sums
-// of r^2 and of (b / J)^2.
-__global__ void k_curv_df_residual(Dims d, CurvCoef cf, const float2* __restrict__ src, const double* __restrict__ m_dev,
-                                   int scale_J, const float2* __restrict__ u, int transpose, float* __restrict__ r,
-                                   double* __restrict__ pr2, double* __restrict__ pf2) {
-  __shared__ double sh[32];
-  const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y, z = blockIdx.z;
-  float rv = 0.f, fv = 0.f;
-  if (x < d.nx && y < d.ny) {
-    const Nbhd nb(d, x, y, z);
-    const long long i = nb(0, 0, 0);
-    const DfFieldAt U{u, &nb};
-    const CoefAt Bc{cf, &nb};
-    const float J = cf.J[i];
-    float2 b = src[i];
-    if (m_dev) {
-      const float2 m = f64_to_df(m_dev[0]);
-      b = df_add(b, make_float2(-m.x, -m.y));
-    }
-    // acc = h^2 b_M - h^2 op(u), b_M = J * b (forward) or b (transposed)
-    DfAcc acc{0.f, 0.f};
-    const float wb = scale_J ? J * cf.h2 : cf.h2;
-    // wb * b exactly: J * h^2 is rounded once; the operator's h^2 scaling is exact (power of 4)
-    df_acc_prod(acc, wb, b);
-    if (transpose) df_apply_MT(acc, U, Bc, -1.f);
-    else df_apply_M(acc, U, Bc, -1.f);
-    rv = (acc.s + acc.c) / (J * cf.h2);
-    r[i] = rv;
-    fv = scale_J ? (b.x + b.y) : (b.x + b.y) / J;
-  }
-  if (pr2) {
-    const double s = block_sum_f(rv * rv, sh);
-    if (is_thread0()) pr2[block_linear_id()] = s;
-  }
-  if (pf2) {
-    const double s = block_sum_f(fv * fv, sh);
-    if (is_thread0()) pf2[block_linear_id()] = s;
   }
 }
 
@@ -550,6 +505,219 @@ __global__ void k_jscale(long long n, const float2* __restrict__ lam, const floa
     if (out) out[i] = (double)J[i] * (l - s);
   }
 }
+
+// ------------------------------------------------------------------ tiled, z-streaming forms
+//
+// The FP32 sweep and residual and the double-float residual of the finest level run
+// as z-streaming tile kernels: a CTA owns a CTX x CTY tile of cells (one per thread)
+// and a chunk of z planes; the haloed planes (one cell of halo) of u and of the six
+// B components pass through a four-slot shared-memory ring, so every neighbour read
+// of the 19-point operator is a shared-memory load at a constant offset.  The
+// operator itself is the same template (apply_M_h2 / apply_MT_h2 / diag_M_h2) read
+// through shared-memory accessors.  Loads of the plane two ahead are issued before
+// the current plane is computed; one barrier per plane.
+constexpr int CTX = 32, CTY = 8, CNT = CTX * CTY;
+constexpr int CSW = CTX + 2, CSH = CTY + 2, CSN = CSW * CSH;  // haloed plane
+constexpr int CQ = (CSN + CNT - 1) / CNT;                      // haloed cells per thread
+
+template <typename V>
+struct RingU {
+  const V* pl[3];  // planes t - 1, t, t + 1
+  int c;           // haloed index of the thread's cell
+  __device__ __forceinline__ V operator()(int dx, int dy, int dz) const { return pl[dz + 1][c + dy * CSW + dx]; }
+};
+struct RingB {
+  const float* pl[3];
+  int c;
+  __device__ __forceinline__ float operator()(int comp, int dx, int dy, int dz) const {
+    return pl[dz + 1][comp * CSN + c + dy * CSW + dx];
+  }
+};
+
+// One ring slot: the haloed plane of u (V = float or float2) followed by B (6 x CSN floats).
+template <typename V>
+constexpr size_t ring_slot_bytes() {
+  return ((CSN * sizeof(V) + 15) / 16 * 16) + 6 * CSN * sizeof(float);
+}
+
+template <typename V>
+struct Ring {
+  char* base;
+  __device__ __forceinline__ V* u(int slot) const { return reinterpret_cast<V*>(base + slot * ring_slot_bytes<V>()); }
+  __device__ __forceinline__ float* b(int slot) const {
+    return reinterpret_cast<float*>(base + slot * ring_slot_bytes<V>() + (CSN * sizeof(V) + 15) / 16 * 16);
+  }
+};
+
+// Prefetch registers of one haloed plane: each thread loads CQ haloed cells.
+template <typename V>
+struct PlaneRegs {
+  V u[CQ];
+  float b[CQ][6];
+};
+
+template <typename V>
+__device__ __forceinline__ void load_plane(Dims d, const V* __restrict__ u, const CurvCoef& cf, int x0, int y0, int z,
+                                           PlaneRegs<V>& R) {
+  const long long zo = (long long)(((z % d.nz) + d.nz) % d.nz) * d.nx * d.ny;
+#pragma unroll
+  for (int k = 0; k < CQ; ++k) {
+    const int q = threadIdx.x + k * CNT;
+    if (q < CSN) {
+      const int gx = (((x0 - 1 + q % CSW) % d.nx) + d.nx) % d.nx, gy = (((y0 - 1 + q / CSW) % d.ny) + d.ny) % d.ny;
+      const long long gi = zo + (long long)gy * d.nx + gx;
+      R.u[k] = u[gi];
+#pragma unroll
+      for (int m = 0; m < 6; ++m) R.b[k][m] = __ldg(cf.B[m] + gi);
+    }
+  }
+}
+
+template <typename V>
+__device__ __forceinline__ void store_plane(const Ring<V>& ring, int slot, const PlaneRegs<V>& R) {
+  V* su = ring.u(slot);
+  float* sb = ring.b(slot);
+#pragma unroll
+  for (int k = 0; k < CQ; ++k) {
+    const int q = threadIdx.x + k * CNT;
+    if (q < CSN) {
+      su[q] = R.u[k];
+#pragma unroll
+      for (int m = 0; m < 6; ++m) sb[m * CSN + q] = R.b[k][m];
+    }
+  }
+}
+
+// z chunk: at least four waves of four CTAs per SM.
+int curv_zchunk(Dims d) {
+  const long long tiles = (long long)((d.nx + CTX - 1) / CTX) * ((d.ny + CTY - 1) / CTY);
+  int zc = d.nz;
+  while (zc > 8 && tiles * ((d.nz + zc - 1) / zc) < 4 * 4 * 152) zc = (zc + 1) / 2;
+  return zc;
+}
+dim3 curv_tiled_grid(Dims d) {
+  const int zc = curv_zchunk(d);
+  return dim3((d.nx + CTX - 1) / CTX, (d.ny + CTY - 1) / CTY, (d.nz + zc - 1) / zc);
+}
+
+enum CurvMode { CM_JACOBI = 0, CM_RESID = 1 };
+
+// FP32 forms.  CM_JACOBI: out = e + omega (J r h^2 - op(e) h^2) / diag h^2 (Appendix B);
+// CM_RESID: out = r - op(u) / (h^2 J) with block partial sums of out^2 (partials nullable).
+template <int MODE, int TR>
+__global__ void __launch_bounds__(CNT) k_curv_tiled(Dims d, CurvCoef cf, const float* __restrict__ r,
+                                                      const float* __restrict__ u, float* __restrict__ out,
+                                                      float omega, float inv_h2, double* __restrict__ partials, int zc) {
+  extern __shared__ __align__(16) char smc[];
+  __shared__ double shr[32];
+  const Ring<float> ring{smc};
+  const int tx = threadIdx.x % CTX, ty = threadIdx.x / CTX;
+  const int x0 = blockIdx.x * CTX, y0 = blockIdx.y * CTY, z0 = blockIdx.z * zc;
+  const int zend = min(z0 + zc, d.nz);
+  const int x = x0 + tx, y = y0 + ty;
+  const bool own = x < d.nx && y < d.ny;
+  const long long pst = (long long)d.nx * d.ny;
+  const int c = (ty + 1) * CSW + tx + 1;
+  float rr = 0.f;
+  PlaneRegs<float> R;
+  auto slot = [&](int p) { return (p - (z0 - 1)) & 3; };
+  load_plane(d, u, cf, x0, y0, z0 - 1, R);
+  store_plane(ring, slot(z0 - 1), R);
+  load_plane(d, u, cf, x0, y0, z0, R);
+  store_plane(ring, slot(z0), R);
+  load_plane(d, u, cf, x0, y0, z0 + 1, R);
+  for (int t = z0; t < zend; ++t) {
+    store_plane(ring, slot(t + 1), R);
+    __syncthreads();
+    if (t + 1 < zend) load_plane(d, u, cf, x0, y0, t + 2, R);
+    if (own) {
+      const RingU<float> U{{ring.u(slot(t - 1)), ring.u(slot(t)), ring.u(slot(t + 1))}, c};
+      const RingB Bc{{ring.b(slot(t - 1)), ring.b(slot(t)), ring.b(slot(t + 1))}, c};
+      const long long i = (long long)t * pst + (long long)y * d.nx + x;
+      const float Mh2 = TR ? apply_MT_h2<float>(U, Bc) : apply_M_h2<float>(U, Bc);
+      if (MODE == CM_JACOBI) {
+        const float Dh2 = diag_M_h2<float>(Bc);
+        out[i] = U(0, 0, 0) + omega * ((cf.J[i] * r[i] * cf.h2 - Mh2) / Dh2);
+      } else {
+        const float res = r[i] - Mh2 * inv_h2 / cf.J[i];
+        out[i] = res;
+        rr += res * res;
+      }
+    }
+  }
+  if (MODE == CM_RESID && partials) {
+    const double s = block_sum_f(rr, shr);
+    if (is_thread0()) partials[block_linear_id()] = s;
+  }
+}
+
+struct DfRingAt {
+  const float2* pl[3];
+  int c;
+  __device__ __forceinline__ float2 operator()(int dx, int dy, int dz) const { return pl[dz + 1][c + dy * CSW + dx]; }
+};
+
+// r = (b - op(u) / h^2) / J rounded to float, with b = J (src - m) when scale_J (forward
+// source in L-form) or b = src (transposed solve, M-form right-hand side).  Partial sums
+// of r^2 and of (b / J)^2.
+__global__ void __launch_bounds__(CNT) k_curv_df_residual_tiled(Dims d, CurvCoef cf, const float2* __restrict__ src,
+                                                                 const double* __restrict__ m_dev, int scale_J,
+                                                                 const float2* __restrict__ u, int transpose,
+                                                                 float* __restrict__ r, double* __restrict__ pr2,
+                                                                 double* __restrict__ pf2, int zc) {
+  extern __shared__ __align__(16) char smc[];
+  __shared__ double shr[32];
+  const Ring<float2> ring{smc};
+  const int tx = threadIdx.x % CTX, ty = threadIdx.x / CTX;
+  const int x0 = blockIdx.x * CTX, y0 = blockIdx.y * CTY, z0 = blockIdx.z * zc;
+  const int zend = min(z0 + zc, d.nz);
+  const int x = x0 + tx, y = y0 + ty;
+  const bool own = x < d.nx && y < d.ny;
+  const long long pst = (long long)d.nx * d.ny;
+  const int c = (ty + 1) * CSW + tx + 1;
+  float2 m = make_float2(0.f, 0.f);
+  if (m_dev) m = f64_to_df(m_dev[0]);
+  float r2 = 0.f, f2 = 0.f;
+  PlaneRegs<float2> R;
+  auto slot = [&](int p) { return (p - (z0 - 1)) & 3; };
+  load_plane(d, u, cf, x0, y0, z0 - 1, R);
+  store_plane(ring, slot(z0 - 1), R);
+  load_plane(d, u, cf, x0, y0, z0, R);
+  store_plane(ring, slot(z0), R);
+  load_plane(d, u, cf, x0, y0, z0 + 1, R);
+  for (int t = z0; t < zend; ++t) {
+    store_plane(ring, slot(t + 1), R);
+    __syncthreads();
+    if (t + 1 < zend) load_plane(d, u, cf, x0, y0, t + 2, R);
+    if (own) {
+      const long long i = (long long)t * pst + (long long)y * d.nx + x;
+      const float J = cf.J[i];
+      float2 b = src[i];
+      if (m_dev) b = df_add(b, make_float2(-m.x, -m.y));
+      DfAcc acc{0.f, 0.f};
+      const float wb = scale_J ? J * cf.h2 : cf.h2;
+      df_acc_prod(acc, wb, b);
+      const DfRingAt U{{ring.u(slot(t - 1)), ring.u(slot(t)), ring.u(slot(t + 1))}, c};
+      const RingB Bc{{ring.b(slot(t - 1)), ring.b(slot(t)), ring.b(slot(t + 1))}, c};
+      if (transpose) df_apply_MT(acc, U, Bc, -1.f);
+      else df_apply_M(acc, U, Bc, -1.f);
+      const float rv = (acc.s + acc.c) / (J * cf.h2);
+      r[i] = rv;
+      r2 += rv * rv;
+      const float fv = scale_J ? (b.x + b.y) : (b.x + b.y) / J;
+      f2 += fv * fv;
+    }
+  }
+  if (pr2) {
+    const double s = block_sum_f(r2, shr);
+    if (is_thread0()) pr2[block_linear_id()] = s;
+  }
+  if (pf2) {
+    const double s = block_sum_f(f2, shr);
+    if (is_thread0()) pf2[block_linear_id()] = s;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_psibar(cudaStream_t st, Dims d, const double* psi, const double* phi, const double* lam,
@@ -584,10 +752,24 @@ cudaError_t launch_curv_apply(cudaStream_t st, Dims d, CurvCoef cf, const T* u, 
   return cudaGetLastError();
 }
 
+long long curv_partial_count(Dims d) {
+  const dim3 g = curv_tiled_grid(d);
+  return (long long)g.x * g.y * g.z;
+}
+
 template <typename T>
 cudaError_t launch_curv_residual(cudaStream_t st, Dims d, CurvCoef cf, const T* r, const T* u, T* out, int transpose,
                                  double* partials) {
-  k_curv_residual<T><<<cell_grid(d), dim3(BX, BY), 0, st>>>(d, cf, r, u, out, (T)(1.0 / cf.h2), transpose, partials);
+  if constexpr (sizeof(T) == 4) {
+    const size_t sm = 4 * ring_slot_bytes<float>();
+    const float ih2 = (float)(1.0 / cf.h2);
+    if (transpose)
+      k_curv_tiled<CM_RESID, 1><<<curv_tiled_grid(d), CNT, sm, st>>>(d, cf, r, u, out, 0.f, ih2, partials, curv_zchunk(d));
+    else
+      k_curv_tiled<CM_RESID, 0><<<curv_tiled_grid(d), CNT, sm, st>>>(d, cf, r, u, out, 0.f, ih2, partials, curv_zchunk(d));
+  } else {
+    k_curv_residual<T><<<cell_grid(d), dim3(BX, BY), 0, st>>>(d, cf, r, u, out, (T)(1.0 / cf.h2), transpose, partials);
+  }
   note_launch();
   return cudaGetLastError();
 }
@@ -595,7 +777,15 @@ cudaError_t launch_curv_residual(cudaStream_t st, Dims d, CurvCoef cf, const T* 
 template <typename T>
 cudaError_t launch_curv_jacobi(cudaStream_t st, Dims d, CurvCoef cf, const T* r, const T* e_in, T* e_out, int transpose,
                                T omega) {
-  k_curv_jacobi<T><<<cell_grid(d), dim3(BX, BY), 0, st>>>(d, cf, r, e_in, e_out, transpose, omega);
+  if constexpr (sizeof(T) == 4) {
+    const size_t sm = 4 * ring_slot_bytes<float>();
+    if (transpose)
+      k_curv_tiled<CM_JACOBI, 1><<<curv_tiled_grid(d), CNT, sm, st>>>(d, cf, r, e_in, e_out, omega, 0.f, nullptr, curv_zchunk(d));
+    else
+      k_curv_tiled<CM_JACOBI, 0><<<curv_tiled_grid(d), CNT, sm, st>>>(d, cf, r, e_in, e_out, omega, 0.f, nullptr, curv_zchunk(d));
+  } else {
+    k_curv_jacobi<T><<<cell_grid(d), dim3(BX, BY), 0, st>>>(d, cf, r, e_in, e_out, transpose, omega);
+  }
   note_launch();
   return cudaGetLastError();
 }
@@ -609,7 +799,8 @@ cudaError_t launch_curv_dense(cudaStream_t st, Dims d, CurvCoef cf, int transpos
 
 cudaError_t launch_curv_df_residual(cudaStream_t st, Dims d, CurvCoef cf, const float2* src, const double* m_dev,
                                     int scale_J, const float2* u, int transpose, float* r, double* pr2, double* pf2) {
-  k_curv_df_residual<<<cell_grid(d), dim3(BX, BY), 0, st>>>(d, cf, src, m_dev, scale_J, u, transpose, r, pr2, pf2);
+  k_curv_df_residual_tiled<<<curv_tiled_grid(d), CNT, 4 * ring_slot_bytes<float2>(), st>>>(
+      d, cf, src, m_dev, scale_J, u, transpose, r, pr2, pf2, curv_zchunk(d));
   note_launch();
   return cudaGetLastError();
 }

@@ -72,7 +72,7 @@ gbmg_status curv_solve_impl(gbmg_ctx* c, const double* src, const double* u_in, 
   double* part1 = c->partials + c->npart;
   double* part2 = c->partials + 2 * c->npart;
   double* sc = c->scal;
-  const long long pr = df_partial_count(n), pc = partial_count(L0.d);
+  const long long pr = df_partial_count(n), pc = curv_partial_count(L0.d);
   TRY(launch_f64_to_df(c->stream, n, src, c->F_df, part));
   if (!tr) {
     TRY(launch_wsum(c->stream, n, src, L0.cc.J, part, part1));

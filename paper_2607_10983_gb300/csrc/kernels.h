@@ -101,6 +101,8 @@ cudaError_t launch_curv_jacobi(cudaStream_t st, Dims d, CurvCoef cf, const T* r,
 // dense n x n matrix of op / J on a (small) level, FP64 row-major
 cudaError_t launch_curv_dense(cudaStream_t st, Dims d, CurvCoef cf, int transpose, double* out);
 // double-float outer residual: r = b - op(u)/J with b = J (src - m) (scale_J) or src
+// block partial sums written by launch_curv_df_residual and launch_curv_residual<float>
+long long curv_partial_count(Dims d);
 cudaError_t launch_curv_df_residual(cudaStream_t st, Dims d, CurvCoef cf, const float2* src, const double* m_dev,
                                     int scale_J, const float2* u, int transpose, float* r, double* pr2, double* pf2);
 // partial sums of x * J and of J (df_partial_count(n) blocks each)
