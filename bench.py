@@ -72,9 +72,9 @@ def measured_peaks():
 
 
 KERNEL_SOURCES = {
-    "down0": ["legs.cu", "packed.cuh", "stencil.cuh", "common.cuh", "kernels.h"],
-    "up0": ["legs.cu", "packed.cuh", "stencil.cuh", "common.cuh", "kernels.h"],
-    "df0": ["fused_kernels.cu", "packed.cuh", "stencil.cuh", "common.cuh", "kernels.h"],
+    "down0": ["legs.cu", "packed.cuh", "stencil.cuh", "common.cuh"],
+    "up0": ["legs.cu", "packed.cuh", "stencil.cuh", "common.cuh"],
+    "df0": ["fused_kernels.cu", "packed.cuh", "stencil.cuh", "common.cuh"],
 }
 
 
@@ -89,8 +89,8 @@ def kernel_source_digest(family):
 
 def ncu_traffic(family):
     """DRAM bytes per cell of a kernel family from the committed ncu summary table
-    (profiles/ncu_traffic.md), or None when the kernel's sources changed since."""
-    path = os.path.join(ROOT, "profiles", "ncu_traffic.md")
+    (profiles/ncu_traffic.txt), or None when the kernel's sources changed since."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     try:
         with open(path) as fh:
             for line in fh:

@@ -20,7 +20,7 @@ TEST INFRASTRUCTURE.  Plain float64 NumPy/SciPy written from the paper:
 * Sec. 4.8 adjoint, Eq. (curv_operator), (adj_rhs), (adj_op): A = W^-1 M with
   W = diag(sqrt g); F_bar = A^-T phi_bar; s_bar = -[d_s(A phi)]^T F_bar.
 
-Readings (listed in DESIGN.md):
+Readings taken where the paper is silent or ambiguous:
 * Face coefficient B_{i+1/2} = (B_i + B_{i+1})/2 (arithmetic mean).
 * The V-cycle works on L = M/J (the paper's A_psi): the residual f - L u is
   restricted, the coarse problem is L_c e = R r.

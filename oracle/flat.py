@@ -17,7 +17,7 @@ TEST INFRASTRUCTURE.  Plain float64 NumPy/SciPy, written from the paper:
   axis followed by decimation.
 * Sec. 3.2: warm start as defect correction, phi = phi0 + e with A e = F - A phi0.
 
-Readings taken where the paper is silent or ambiguous (each listed in the design doc):
+Readings taken where the paper is silent or ambiguous:
 * Chebyshev degree v means v applications of the operator per smoothing pass
   (the standard Chebyshev semi-iteration on D^-1 A), not degree v+1 in the error.
 * Restriction and prolongation are vertex-centred: coarse node I sits on fine
