@@ -55,7 +55,7 @@ def parse():
     p.add_argument("--no-fused", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip e2e, baselines and CPU oracle legs")
     p.add_argument("--max-vcycles", type=int, default=40)
-    p.add_argument("--only", choices=["moving_mesh", "differentiable", "batched", "fixed_2_cycles"],
+    p.add_argument("--only", choices=["moving_mesh", "differentiable", "batched", "fixed_2_cycles", "predictors"],
                    help="run one extra workload alone and print its JSON object (no headline line)")
     p.add_argument("--print-source-digests", action="store_true",
                    help="print the source digest of each profiled kernel family and exit")
@@ -351,6 +351,7 @@ def run_ours(args):
         line["e2e"] = e2e_leg(args, solver, host_src)
         line["baselines"] = baseline_legs(args, F, dev)
         line["fixed_2_cycles"] = fixed_cycles_leg(args, solver, F)
+        line["predictors"] = predictors_leg(args, solver, F)
         del F
         del phi
         solver.close()
@@ -467,6 +468,42 @@ def fixed_cycles_leg(args, solver, F):
     dt = time.perf_counter() - t0
     return {"solves_per_s": len(F) / dt, "rel_res_per_source": rel,
             "note": "t = 0 to the tolerance, t >= 1 at most 2 V-cycles (status NOT_CONVERGED allowed)"}
+
+
+def predictors_leg(args, solver, F):
+    """The sequence with the warm-start predictors of Sec. 3.2: recycling (the headline
+    path), linear and quadratic extrapolation over the previous solutions (mg_predict,
+    one extra FP64 pass per solve, counted in the time).  Early steps use the highest
+    order their history allows.  The synthetic sources drift exactly linearly in t, so
+    extrapolation is near exact here; real PM sources are not."""
+    import torch
+    n, seq = args.n, len(F)
+    ring = [torch.zeros((n, n, n), dtype=torch.float64, device=F[0].device) for _ in range(4)]
+    out = {}
+    for name, order in (("recycle", 0), ("linear", 1), ("quadratic", 2)):
+        for b in ring:
+            b.zero_()
+        hist = []          # indices into ring, most recent first
+        cycles = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for t in range(seq):
+            if not hist or order == 0:
+                cur = hist[0] if hist else 0          # cold start, or recycling in place
+            else:
+                cur = next(i for i in range(4) if i not in hist[:3])
+                k = min(order, len(hist) - 1)
+                solver.predict([ring[i] for i in hist[:k + 1]], order=k, out=ring[cur])
+            _, st = solver.solve(F[t], ring[cur], tol=args.tol, max_vcycles=args.max_vcycles)
+            cycles.append(st.cycles)
+            hist = [cur] + [i for i in hist if i != cur]
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out[name] = {"solves_per_s": seq / dt, "cycles_per_solve": sum(cycles) / seq, "cycles": cycles}
+    del ring
+    out["note"] = ("sources drift exactly linearly in t (delta_t = delta_0 + 0.05 t eta), so extrapolation "
+                   "is near exact on this workload; the headline value uses recycling")
+    return out
 
 
 def _timed(fn):
@@ -646,7 +683,8 @@ def run_only(args):
         import paper_2607_10983_gb300 as gb
         F = [torch.from_numpy(a).to(dev) for a in sources(args.n, args.seq, 0)]
         solver = gb.Solver(args.n, prec="mixed", degree=args.degree, fused=not args.no_fused)
-        out = fixed_cycles_leg(args, solver, F)
+        leg = fixed_cycles_leg if args.only == "fixed_2_cycles" else predictors_leg
+        out = leg(args, solver, F)
         solver.close()
     print(json.dumps({args.only: out}))
 

@@ -146,6 +146,20 @@ gbmg_status mg_solve_adjoint(gbmg_ctx* ctx, const double* phi_bar_dev, double* s
 gbmg_status mg_solve_host(gbmg_ctx* ctx, const double* source_host, double* phi_inout_host,
                           double tol, int max_vcycles, gbmg_stats* stats);
 
+/* Warm-start predictor (Sec. 3.2 "Predictors"): the initial guess of the next solve from
+ * earlier solutions of this context's mesh, FP64, nx*ny*nz values each.
+ *   history_dev[0] = phi_{n-1} (most recent), history_dev[1] = phi_{n-2}, ...
+ *   order 0: out = growth * phi_{n-1}   (recycling for growth = 1; the growth-scaled
+ *            predictor, Eq. growth, with growth = D(a_n) / D(a_{n-1}))
+ *   order 1: out = 2 phi_{n-1} - phi_{n-2}                (linear extrapolation)
+ *   order 2: out = 3 phi_{n-1} - 3 phi_{n-2} + phi_{n-3}  (quadratic extrapolation)
+ * Every product and sum is one correctly rounded FP64 operation, left to right as
+ * written.  out_dev may be history_dev[0] (in place).  Queued on the context's stream.
+ * Errors: GBMG_ERR_INVALID_ARG for order outside 0..2, n_history < order + 1 or NULL
+ * pointers. */
+gbmg_status mg_predict(gbmg_ctx* ctx, int order, double growth, const double* const* history_dev, int n_history,
+                       double* out_dev);
+
 /* Statistics of the last completed mg_solve on this context (waits for the stream). */
 gbmg_status mg_last_stats(gbmg_ctx* ctx, gbmg_stats* stats);
 

@@ -272,3 +272,23 @@ def defect_correction_solve(F: np.ndarray, phi0: np.ndarray, cycles: int, **kw):
         r = residual(F, phi)
         phi = phi + vcycle(0, np.zeros_like(r), r, nlev, **kw)
     return phi - phi.mean()
+
+
+def predict(history, order: int, growth: float = 1.0) -> np.ndarray:
+    """Initial guess of the next solve from earlier solutions (Sec. 3.2, "Predictors").
+
+    history[0] is the most recent solution phi_{n-1}, history[1] is phi_{n-2}, ...
+      order 0: growth * phi_{n-1}  (recycling for growth = 1; the growth-scaled
+               predictor, Eq. growth, with growth = D(a_n) / D(a_{n-1}))
+      order 1: 2 phi_{n-1} - phi_{n-2}                 (linear extrapolation)
+      order 2: 3 phi_{n-1} - 3 phi_{n-2} + phi_{n-3}   (quadratic extrapolation)
+    Each product and sum is one IEEE operation, left to right as written.
+    """
+    h = [np.asarray(x, dtype=np.float64) for x in history]
+    if order == 0:
+        return growth * h[0]
+    if order == 1:
+        return 2.0 * h[0] - h[1]
+    if order == 2:
+        return 3.0 * h[0] - 3.0 * h[1] + h[2]
+    raise ValueError("order must be 0, 1 or 2")

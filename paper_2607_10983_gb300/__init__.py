@@ -103,6 +103,7 @@ _SIGS = {
     "mg_rel_residual_noalloc": (_S, [_I, _I, _I, _P, _P, _P, _P]),
     "mg_grad": (_S, [_P, _I, _I, _P, _P]),
     "mg_grad_dot": (_S, [_P, _I, _P, _P, _P]),
+    "mg_predict": (_S, [_P, _I, _D, ctypes.POINTER(_P), _I, _P]),
     "mg_batch_create": (_S, [ctypes.POINTER(_P), ctypes.POINTER(_P), _I, _P]),
     "mg_batch_destroy": (None, [_P]),
     "mg_batch_set_blocks": (_S, [_P, _I]),
@@ -280,6 +281,16 @@ class Solver:
     def curv_vcycle(self, r: torch.Tensor, transpose: bool = False):
         out = torch.empty_like(r)
         _check(lib().mg_curv_vcycle(self._c(), int(transpose), _ptr(r, torch.float32, self.shape), _ptr(out)))
+        return out
+
+    def predict(self, history, order: int = 1, growth: float = 1.0, out: torch.Tensor | None = None) -> torch.Tensor:
+        """Warm-start predictor (mg_predict): history[0] is the most recent solution.
+        order 0: growth * phi_{n-1}; 1: 2 phi_{n-1} - phi_{n-2}; 2: 3 phi_{n-1} - 3 phi_{n-2} + phi_{n-3}."""
+        if out is None:
+            out = torch.empty_like(history[0])
+        arr = (_P * len(history))(*[_ptr(h, torch.float64, self.shape) for h in history])
+        _check(lib().mg_predict(self._c(), int(order), float(growth), arr, len(history),
+                                _ptr(out, torch.float64, self.shape)))
         return out
 
     def solve_host(self, F, phi, tol: float = 1e-6, max_vcycles: int = 50):

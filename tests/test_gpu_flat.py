@@ -247,3 +247,43 @@ def test_fused_solve_iterates_match_unfused(gb, shape):
     diff = (pa - pb).abs().max().item()
     assert diff <= 1e-14 * pb.abs().max().item()
     np.testing.assert_allclose(sa.history, sb.history, rtol=1e-5)
+
+
+@pytest.mark.parametrize("order,growth", [(0, 1.0), (0, 1.3), (1, 1.0), (2, 1.0)])
+def test_predict_matches_oracle_bit_for_bit(gb, order, growth):
+    shape = (24, 16, 32)
+    hist = [np.random.default_rng(70 + k).standard_normal(shape) for k in range(3)]
+    s = gb.Solver(shape)
+    got = s.predict([to_dev(h) for h in hist], order=order, growth=growth).cpu().numpy()
+    assert np.array_equal(got, flat.predict(hist, order, growth))
+    # in place on the most recent solution
+    h0 = to_dev(hist[0])
+    s.predict([h0, to_dev(hist[1]), to_dev(hist[2])], order=order, growth=growth, out=h0)
+    assert np.array_equal(h0.cpu().numpy(), flat.predict(hist, order, growth))
+    with pytest.raises(gb.GbmgError):
+        s.predict([to_dev(hist[0])], order=2)
+
+
+def test_predictors_save_cycles_in_a_warm_sequence(gb):
+    """Eq. kwarm with the predictors on the GPU: sources drifting linearly in the step
+    index; extrapolated starts need fewer cycles than recycling and reach the same
+    solution (FFT oracle)."""
+    n = 32
+    d0, eta = grf(n, 2), grf(n, 3)
+    F = [d0 + 0.05 * t * eta for t in range(5)]
+    s = gb.Solver(n)
+    sols = []
+    for t in range(4):
+        phi = sols[-1].clone() if sols else torch.zeros((n, n, n), dtype=torch.float64, device="cuda")
+        s.solve(to_dev(F[t]), phi, tol=1e-10, max_vcycles=40)
+        sols.append(phi)
+    _, rec = s.solve(to_dev(F[4]), sols[3].clone(), tol=1e-8, max_vcycles=40)
+    lin_phi = s.predict([sols[3], sols[2]], order=1)
+    _, lin = s.solve(to_dev(F[4]), lin_phi, tol=1e-8, max_vcycles=40)
+    quad_phi = s.predict([sols[3], sols[2], sols[1]], order=2)
+    _, quad = s.solve(to_dev(F[4]), quad_phi, tol=1e-8, max_vcycles=40)
+    assert lin.rel_res0 < 1e-3 * rec.rel_res0 and quad.rel_res0 < 1e-3 * rec.rel_res0
+    assert lin.cycles < rec.cycles and quad.cycles < rec.cycles
+    ref = flat.fft_solve(F[4])
+    for p in (lin_phi, quad_phi):
+        assert np.linalg.norm(p.cpu().numpy() - ref) / np.linalg.norm(ref) < 1e-8

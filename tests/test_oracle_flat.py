@@ -232,3 +232,43 @@ def test_warm_start_cycle_saving():
     predicted = k_cold - math.log(1 / eps) / math.log(1 / rho)
     assert k_warm < k_cold
     assert abs(k_warm - predicted) <= 1.5, (k_cold, k_warm, predicted)
+
+
+def test_predictors_exact_on_their_sequences():
+    """Sec. 3.2 predictors: growth scaling is exact on a pure-growth sequence, linear
+    (quadratic) extrapolation on sequences linear (quadratic) in the step index, and
+    linear extrapolation of a quadratic sequence misses by exactly twice its t^2 term."""
+    rng = np.random.default_rng(11)
+    a, b, c = (rng.standard_normal((4, 5, 6)) for _ in range(3))
+    g = 1.25
+    grow = [a]
+    for _ in range(3):
+        grow.append(g * grow[-1])
+    assert np.array_equal(flat.predict([grow[2]], 0, g), grow[3])
+    assert np.array_equal(flat.predict([grow[2]], 0), grow[2])
+    lin = [a + t * b for t in range(4)]
+    np.testing.assert_allclose(flat.predict([lin[2], lin[1]], 1), lin[3], rtol=0, atol=1e-14)
+    quad = [a + t * b + t * t * c for t in range(5)]
+    np.testing.assert_allclose(flat.predict([quad[3], quad[2], quad[1]], 2), quad[4], rtol=0, atol=1e-13)
+    np.testing.assert_allclose(quad[4] - flat.predict([quad[3], quad[2]], 1), 2.0 * c, rtol=0, atol=1e-13)
+    with pytest.raises(ValueError):
+        flat.predict([a], 3)
+
+
+def test_extrapolation_saves_cycles_on_a_smooth_sequence():
+    """Eq. kwarm with the predictors: on sources drifting smoothly (here linearly) in
+    the step index, linear extrapolation starts orders of magnitude closer than
+    recycling and needs fewer cycles to the same tolerance."""
+    from synth import grf
+    n = 16
+    d0, eta = grf(n, 2), grf(n, 3)
+    F = [d0 + 0.05 * t * eta for t in range(4)]
+    sols = []
+    for t in range(3):
+        phi, _ = flat.mg_solve(F[t], phi0=sols[-1] if sols else None, tol=1e-12)
+        sols.append(phi)
+    _, rec = flat.mg_solve(F[3], phi0=sols[2], tol=1e-8)
+    _, lin = flat.mg_solve(F[3], phi0=flat.predict([sols[2], sols[1]], 1), tol=1e-8)
+    _, quad = flat.mg_solve(F[3], phi0=flat.predict([sols[2], sols[1], sols[0]], 2), tol=1e-8)
+    assert lin[0] < 1e-3 * rec[0] and quad[0] < 1e-3 * rec[0]
+    assert len(lin) < len(rec) and len(quad) < len(rec)
