@@ -160,6 +160,23 @@ gbmg_status mg_solve_host(gbmg_ctx* ctx, const double* source_host, double* phi_
 gbmg_status mg_predict(gbmg_ctx* ctx, int order, double growth, const double* const* history_dev, int n_history,
                        double* out_dev);
 
+/* One mesh-motion step (Sec. 4.4) on a GBMG_OP_CURV19 context:
+ *   psidot solves L_psi[psidot] = kappa (m_init - sqrt(g) rho)   (Eq. calcdefp)
+ *     with the curvilinear solver of mg_solve (same operator, same projection and gauge),
+ *     the source first smoothed by smooth_passes passes of the separable [1/4, 1/2, 1/4]
+ *     filter (the paper smooths the source without naming the filter);
+ *   psi <- psi + dtau psidot - mean(psi + dtau psidot)             (Eq. defadvance).
+ * rho_dev: mass density per unit computational volume on the finest level (FP64);
+ * psi_inout_dev: the deformation potential, updated in place (FP64);
+ * psidot_inout_dev: initial guess of psidot (warm start; zeros for a cold start) and the
+ * solution out (FP64).  The geometry is set from the incoming psi; after the call the
+ * context needs mg_set_geometry (or coeffs in mg_solve) before its next solve.  Waits for
+ * the stream.  Returns the solve's convergence status; psi is advanced with the last
+ * iterate of psidot in every case except argument and CUDA errors. */
+gbmg_status mg_mesh_motion(gbmg_ctx* ctx, const double* rho_dev, double kappa, double m_init, int smooth_passes,
+                           double dtau, double* psi_inout_dev, double* psidot_inout_dev, double tol, int max_vcycles,
+                           gbmg_stats* stats);
+
 /* Statistics of the last completed mg_solve on this context (waits for the stream). */
 gbmg_status mg_last_stats(gbmg_ctx* ctx, gbmg_stats* stats);
 

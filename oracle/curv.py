@@ -373,3 +373,29 @@ def solve_vjp(delta: np.ndarray, psi: np.ndarray, phi: np.ndarray, phi_bar: np.n
     Abar = Abar_from_J(A, Jbar) - Abar_from_B(A, Bbar_from_operator(lam, phi, lev0.h))
     psi_bar = hessian_T(Abar, lev0.h)
     return delta_bar, psi_bar
+
+
+# ---------------------------------------------------------------- mesh motion
+
+
+def smooth_binomial(u: np.ndarray, passes: int) -> np.ndarray:
+    """passes of the separable [1/4, 1/2, 1/4] filter, periodic (the one-axis weights of the
+    full-weighting restriction, Appendix B, without decimation; the paper smooths the
+    mesh-motion source without naming the filter)."""
+    u = np.asarray(u, dtype=np.float64)
+    for _ in range(passes):
+        for ax in range(3):
+            u = 0.25 * (np.roll(u, 1, axis=ax) + np.roll(u, -1, axis=ax)) + 0.5 * u
+    return u
+
+
+def mesh_motion_step(psi: np.ndarray, rho: np.ndarray, kappa: float, m_init: float, dtau: float,
+                     passes: int = 2, tol: float = 1e-10):
+    """One mesh-motion step (Sec. 4.4): L_psi[psidot] = kappa (m_init - sqrt(g) rho), Eq. calcdefp,
+    with the smoothed source, solved by the curvilinear solver (weighted projection, zero-mean
+    gauge); then psi <- Z[psi + dtau psidot], Eq. defadvance.  Returns (psi_new, psidot)."""
+    J = geometry(np.asarray(psi, dtype=np.float64), 1.0)[0]
+    src = smooth_binomial(kappa * (m_init - J * rho), passes)
+    psidot, _ = solve(src, psi, tol=tol)
+    new = psi + dtau * psidot
+    return new - new.mean(), psidot

@@ -104,6 +104,7 @@ _SIGS = {
     "mg_grad": (_S, [_P, _I, _I, _P, _P]),
     "mg_grad_dot": (_S, [_P, _I, _P, _P, _P]),
     "mg_predict": (_S, [_P, _I, _D, ctypes.POINTER(_P), _I, _P]),
+    "mg_mesh_motion": (_S, [_P, _P, _D, _D, _I, _D, _P, _P, _D, _I, ctypes.POINTER(_Stats)]),
     "mg_batch_create": (_S, [ctypes.POINTER(_P), ctypes.POINTER(_P), _I, _P]),
     "mg_batch_destroy": (None, [_P]),
     "mg_batch_set_blocks": (_S, [_P, _I]),
@@ -292,6 +293,19 @@ class Solver:
         _check(lib().mg_predict(self._c(), int(order), float(growth), arr, len(history),
                                 _ptr(out, torch.float64, self.shape)))
         return out
+
+    def mesh_motion(self, rho: torch.Tensor, psi: torch.Tensor, kappa: float, m_init: float, dtau: float,
+                    psidot: torch.Tensor | None = None, smooth_passes: int = 2, tol: float = 1e-6,
+                    max_vcycles: int = 100):
+        """One mesh-motion step (mg_mesh_motion): psi (float64) advanced in place; returns (psi, psidot, Stats)."""
+        if psidot is None:
+            psidot = torch.zeros_like(psi)
+        st = _Stats()
+        s = lib().mg_mesh_motion(self._c(), _ptr(rho, torch.float64, self.shape), float(kappa), float(m_init),
+                                 int(smooth_passes), float(dtau), _ptr(psi, torch.float64, self.shape),
+                                 _ptr(psidot, torch.float64, self.shape), float(tol), int(max_vcycles), ctypes.byref(st))
+        _check(s, allow_convergence=True)
+        return psi, psidot, Stats.from_c(st)
 
     def solve_host(self, F, phi, tol: float = 1e-6, max_vcycles: int = 50):
         """Same solve on host float64 arrays (numpy or CPU tensors); phi is overwritten."""

@@ -207,3 +207,33 @@ def test_curvilinear_errors(gb):
         gb.Solver(16, op="curv", smoother="chebyshev")
     with pytest.raises(gb.GbmgError):
         gb.Solver(16, op="curv", prec="fp64")
+
+
+@pytest.mark.parametrize("shape,passes", [((16, 16, 16), 2), ((16, 24, 32), 1)])
+def test_mesh_motion_matches_oracle(gb, shape, passes):
+    """One mesh-motion step (Sec. 4.4, Eq. calcdefp and Eq. defadvance) against the oracle:
+    psidot and the advanced psi, then a second step warm-started from the first psidot."""
+    psi = psi_field(shape, 21, rowsum=0.3)
+    rho = 1.0 + 0.3 * grf(shape, 22)
+    kappa, m_init, dtau = 0.8, 1.0, 0.25
+    ref_psi, ref_dot = curv.mesh_motion_step(psi, rho, kappa, m_init, dtau, passes=passes, tol=1e-12)
+    s = gb.Solver(shape, op="curv")
+    p = to_dev(psi)
+    p, dot, st = s.mesh_motion(to_dev(rho), p, kappa, m_init, dtau, smooth_passes=passes, tol=1e-10,
+                               max_vcycles=200)
+    assert st.status == 0 and st.rel_res <= 1e-10
+    # the remaining difference is the FP32 rounding of J in the source and of the coefficients
+    assert rel_l2(dot.cpu().numpy(), ref_dot) < 1e-6
+    assert rel_l2(p.cpu().numpy(), ref_psi) < 1e-6
+    assert abs(float(p.mean())) < 1e-12 * float(p.abs().max())
+    ref2_psi, ref2_dot = curv.mesh_motion_step(ref_psi, rho, kappa, m_init, dtau, passes=passes, tol=1e-12)
+    p, dot2, st2 = s.mesh_motion(to_dev(rho), p, kappa, m_init, dtau, psidot=dot.clone(), smooth_passes=passes,
+                                 tol=1e-10, max_vcycles=200)
+    assert st2.status == 0 and st2.rel_res0 < st.rel_res0   # warm start from the previous psidot
+    assert rel_l2(dot2.cpu().numpy(), ref2_dot) < 2e-6
+    assert rel_l2(p.cpu().numpy(), ref2_psi) < 2e-6
+    # the context needs its geometry again before the next solve
+    with pytest.raises(gb.GbmgError):
+        s.solve(to_dev(rho))
+    with pytest.raises(gb.GbmgError):
+        gb.Solver(shape).mesh_motion(to_dev(rho), to_dev(psi), kappa, m_init, dtau)

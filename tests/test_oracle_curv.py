@@ -176,3 +176,41 @@ def test_vjp_against_central_differences():
         eps = 1e-3
         fd = (loss(delta, psi + eps * wdir) - loss(delta, psi - eps * wdir)) / (2 * eps)
         assert abs(fd - float((psibar * wdir).sum())) < 1e-5 * max(1.0, abs(fd))
+
+
+def test_binomial_smoothing_plane_wave_factor():
+    """[1/4, 1/2, 1/4] per axis has the symbol cos^2(k/2); p passes over three axes multiply
+    a plane wave by prod_a cos^2(k_a / 2)^p."""
+    n = (8, 12, 16)
+    kk = [2 * math.pi * m / s for m, s in zip((1, 2, 3), n)]   # (kz, ky, kx)
+    z, y, x = np.meshgrid(*[np.arange(s) for s in n], indexing="ij")
+    u = np.cos(kk[0] * z + kk[1] * y + kk[2] * x)
+    for p in (1, 2):
+        factor = np.prod([math.cos(k / 2) ** 2 for k in kk]) ** p
+        np.testing.assert_allclose(curv.smooth_binomial(u, p), factor * u, rtol=0, atol=1e-13)
+
+
+def test_mesh_motion_flat_mesh_is_spectral_solve():
+    """psi = 0 (sqrt g = 1): the deformation-rate potential is the flat Poisson solution of
+    the smoothed kappa (m_init - rho), and psi_new = dtau psidot (zero mean)."""
+    n = 16
+    rho = 1.0 + 0.3 * grf(n, 31)
+    psi0 = np.zeros((n, n, n))
+    kappa, m_init, dtau = 0.7, 1.0, 0.2
+    new, psidot = curv.mesh_motion_step(psi0, rho, kappa, m_init, dtau, passes=2, tol=1e-12)
+    ref = flat.fft_solve(curv.smooth_binomial(kappa * (m_init - rho), 2))
+    ref -= ref.mean()
+    np.testing.assert_allclose(psidot, ref, rtol=0, atol=1e-9 * np.abs(ref).max())
+    np.testing.assert_allclose(new, dtau * ref, rtol=0, atol=1e-9 * np.abs(ref).max())
+
+
+def test_mesh_motion_equal_mass_per_cell_is_stationary():
+    """m = sqrt(g) rho equal to m_init in every cell gives a zero source: psidot = 0 and psi
+    only loses its mean (Eq. defadvance gauge)."""
+    n = 16
+    psi = smoothed_grf(n, 32, 2.0, 0.3) + 0.5
+    J = curv.geometry(psi, 1.0)[0]
+    rho = 1.3 / J
+    new, psidot = curv.mesh_motion_step(psi, rho, 2.0, 1.3, 0.5, passes=1)
+    assert np.abs(psidot).max() < 1e-12
+    np.testing.assert_allclose(new, psi - psi.mean(), rtol=0, atol=1e-12)
