@@ -55,7 +55,8 @@ def parse():
     p.add_argument("--no-fused", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip e2e, baselines and CPU oracle legs")
     p.add_argument("--max-vcycles", type=int, default=40)
-    p.add_argument("--only", choices=["moving_mesh", "differentiable", "batched", "fixed_2_cycles", "predictors"],
+    p.add_argument("--only", choices=["moving_mesh", "differentiable", "batched", "fixed_2_cycles", "predictors",
+                                      "pm_force"],
                    help="run one extra workload alone and print its JSON object (no headline line)")
     p.add_argument("--print-source-digests", action="store_true",
                    help="print the source digest of each profiled kernel family and exit")
@@ -358,6 +359,7 @@ def run_ours(args):
         torch.cuda.empty_cache()
         line["differentiable_256"] = differentiable_leg(args, dev)
         line["moving_mesh_256"] = moving_mesh_leg(args, dev)
+        line["pm_force_256"] = pm_force_leg(args, dev)
         torch.cuda.empty_cache()
         line["batched_48"] = batched_leg(args)
         line["cpu_baseline"] = oracle_sample(n, seq, args.tol)
@@ -503,6 +505,61 @@ def predictors_leg(args, solver, F):
     del ring
     out["note"] = ("sources drift exactly linearly in t (delta_t = delta_0 + 0.05 t eta), so extrapolation "
                    "is near exact on this workload; the headline value uses recycling")
+    return out
+
+
+def pm_force_leg(args, dev):
+    """Static PM force evaluation at 256^3: 256^3 particles (displaced lattice) on a 256^3
+    mesh; CIC paint, solve, fourth-order gradient, read (the unit of the paper's
+    force-evaluation cost tables).  Variants: cold solve to 1e-6, and warm starts from the
+    previous step's potential (particles displaced 2% less) with at most 1 or 2 V-cycles
+    (the paper's operating points).  Per-stage device times."""
+    import torch
+
+    import paper_2607_10983_gb300 as gb
+    from synth import lattice_particles
+    n = 256
+    p_prev = torch.from_numpy(lattice_particles(n, n, 9, rms_displacement=1.96)).to(dev)
+    p = torch.from_numpy(lattice_particles(n, n, 9, rms_displacement=2.0)).to(dev)
+    s = gb.Solver(n)
+    rho = s.cic_paint(p_prev, 1.0)
+    phi_prev, _ = s.solve(rho, tol=args.tol, max_vcycles=args.max_vcycles)
+    phi = torch.empty_like(phi_prev)
+    force = torch.empty((p.shape[0], 3), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+
+    def step(warm, tol, maxv):
+        if warm:
+            phi.copy_(phi_prev)
+        else:
+            phi.zero_()
+        ev[0].record(stream)
+        s.cic_paint(p, 1.0, out=rho)
+        ev[1].record(stream)
+        _, st = s.solve(rho, phi, tol=tol, max_vcycles=maxv)
+        ev[2].record(stream)
+        ev[3].record(stream)
+        s.force(phi, p, out=force)
+        ev[4].record(stream)
+        torch.cuda.synchronize()
+        return st, [ev[i].elapsed_time(ev[i + 1]) for i in range(4)]
+
+    out = {}
+    for name, warm, tol, maxv in (("cold_to_1e-6", False, args.tol, args.max_vcycles), ("warm_1_cycle", True, 0.0, 1),
+                                  ("warm_2_cycles", True, 0.0, 2)):
+        step(warm, tol, maxv)                    # warm-up
+        reps, tot, stages = 3, 0.0, [0.0] * 4
+        for _ in range(reps):
+            st, t = step(warm, tol, maxv)
+            tot += sum(t)
+            stages = [a + b for a, b in zip(stages, t)]
+        out[name] = {"ms": tot / reps, "cycles": st.cycles, "rel_res": st.rel_res,
+                     "paint_solve_force_ms": [stages[0] / reps, stages[1] / reps, (stages[2] + stages[3]) / reps]}
+    s.close()
+    out["workload"] = ("256^3 particles (lattice + Zel'dovich-like displacement, rms 2 cells, seed 9) on a 256^3 "
+                       "mesh; force = -grad4 phi read at the particles; context: the paper quotes 17.9 ms (FFT) "
+                       "and 16.5 ms (warm MG, 1 cycle) per full PM step at 256^3 on one A100")
     return out
 
 
@@ -679,6 +736,8 @@ def run_only(args):
         out = differentiable_leg(args, dev)
     elif args.only == "batched":
         out = batched_leg(args)
+    elif args.only == "pm_force":
+        out = pm_force_leg(args, dev)
     else:
         import paper_2607_10983_gb300 as gb
         F = [torch.from_numpy(a).to(dev) for a in sources(args.n, args.seq, 0)]

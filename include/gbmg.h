@@ -177,6 +177,34 @@ gbmg_status mg_mesh_motion(gbmg_ctx* ctx, const double* rho_dev, double kappa, d
                            double dtau, double* psi_inout_dev, double* psidot_inout_dev, double tol, int max_vcycles,
                            gbmg_stats* stats);
 
+/* ---------------------------------------------------------------------------------
+ * Particle-mesh steps around the solve (Sec. 2.1: particles are deposited by
+ * cloud-in-cell interpolation to form the source; a static force evaluation is paint,
+ * solve, fourth-order gradient (mg_grad), read).  On the finest level of ctx.
+ * pos_dev: n_particles x 3 FP32, columns x, y, z in cell units (node (i, j, k) at position
+ * (i, j, k)); any position is wrapped onto the periodic mesh.  Per axis node floor(x)
+ * gets weight 1 - f and node floor(x) + 1 weight f, f = x - floor(x), formed in FP64.
+ * --------------------------------------------------------------------------------- */
+/* rho_dev (FP64, nx*ny*nz) = sum over particles of mass_p x CIC weight; mass_dev (FP32,
+ * n_particles) or, when NULL, the scalar `mass` for every particle.  rho_dev is
+ * overwritten; the sum uses FP64 atomics, so its rounding depends on the order in which
+ * particles land.  Queued on the context's stream. */
+gbmg_status mg_cic_paint(gbmg_ctx* ctx, const float* pos_dev, const float* mass_dev, double mass,
+                         long long n_particles, double* rho_dev);
+/* out_dev[p * ncomp + c] = sum of the CIC weights times field_dev[c * nx*ny*nz + node]
+ * (FP64, ncomp = 1..3 components, e.g. the output of mg_grad); corners summed in the order
+ * dz, dy, dx, each product and sum correctly rounded.  The transpose of mg_cic_paint. */
+gbmg_status mg_cic_read(gbmg_ctx* ctx, const double* field_dev, int ncomp, const float* pos_dev,
+                        long long n_particles, double* out_dev);
+
+/* Single-precision force at the particles (the paper's PM force evaluation runs in FP32):
+ * phi (FP64) rounded to FP32, force grid -grad4 phi (the fourth-order gradient of mg_grad,
+ * h = 1) in FP32, then CIC read in FP32 with the weights of mg_cic_paint.
+ * force_out_dev: n_particles x 3 FP32 (x, y, z).  Allocates 16 bytes per cell of scratch on
+ * first use (kept until mg_destroy).  Queued on the context's stream. */
+gbmg_status mg_force(gbmg_ctx* ctx, const double* phi_dev, const float* pos_dev, long long n_particles,
+                     float* force_out_dev);
+
 /* Statistics of the last completed mg_solve on this context (waits for the stream). */
 gbmg_status mg_last_stats(gbmg_ctx* ctx, gbmg_stats* stats);
 

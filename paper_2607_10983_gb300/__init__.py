@@ -104,6 +104,9 @@ _SIGS = {
     "mg_grad": (_S, [_P, _I, _I, _P, _P]),
     "mg_grad_dot": (_S, [_P, _I, _P, _P, _P]),
     "mg_predict": (_S, [_P, _I, _D, ctypes.POINTER(_P), _I, _P]),
+    "mg_cic_paint": (_S, [_P, _P, _P, _D, ctypes.c_longlong, _P]),
+    "mg_cic_read": (_S, [_P, _P, _I, _P, ctypes.c_longlong, _P]),
+    "mg_force": (_S, [_P, _P, _P, ctypes.c_longlong, _P]),
     "mg_mesh_motion": (_S, [_P, _P, _D, _D, _I, _D, _P, _P, _D, _I, ctypes.POINTER(_Stats)]),
     "mg_batch_create": (_S, [ctypes.POINTER(_P), ctypes.POINTER(_P), _I, _P]),
     "mg_batch_destroy": (None, [_P]),
@@ -306,6 +309,37 @@ class Solver:
                                  _ptr(psidot, torch.float64, self.shape), float(tol), int(max_vcycles), ctypes.byref(st))
         _check(s, allow_convergence=True)
         return psi, psidot, Stats.from_c(st)
+
+    def cic_paint(self, pos: torch.Tensor, mass=1.0, out: torch.Tensor | None = None) -> torch.Tensor:
+        """Cloud-in-cell density (float64, mesh shape) of particles pos (n, 3) float32 in cell units;
+        mass: scalar or float32 tensor (n,)."""
+        if pos.dtype != torch.float32 or pos.dim() != 2 or pos.shape[1] != 3 or not pos.is_contiguous():
+            raise ValueError("pos must be a contiguous float32 (n, 3) tensor")
+        if out is None:
+            out = torch.empty(self.shape, dtype=torch.float64, device=pos.device)
+        mptr, m0 = (None, float(mass)) if not torch.is_tensor(mass) else (_ptr(mass, torch.float32, (pos.shape[0],)), 0.0)
+        _check(lib().mg_cic_paint(self._c(), _ptr(pos, torch.float32), mptr, m0, int(pos.shape[0]),
+                                  _ptr(out, torch.float64, self.shape)))
+        return out
+
+    def cic_read(self, field: torch.Tensor, pos: torch.Tensor) -> torch.Tensor:
+        """Field (ncomp, *mesh) or mesh-shaped, float64, interpolated at pos (n, 3) float32: (n, ncomp)."""
+        if pos.dtype != torch.float32 or pos.dim() != 2 or pos.shape[1] != 3 or not pos.is_contiguous():
+            raise ValueError("pos must be a contiguous float32 (n, 3) tensor")
+        nc = 1 if field.dim() == 3 else field.shape[0]
+        out = torch.empty((pos.shape[0], nc), dtype=torch.float64, device=pos.device)
+        shp = self.shape if nc == 1 and field.dim() == 3 else (nc,) + self.shape
+        _check(lib().mg_cic_read(self._c(), _ptr(field, torch.float64, shp), nc, _ptr(pos, torch.float32),
+                                 int(pos.shape[0]), _ptr(out)))
+        return out
+
+    def force(self, phi: torch.Tensor, pos: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """FP32 force -grad4 phi at the particles (mg_force): (n, 3) float32."""
+        if out is None:
+            out = torch.empty((pos.shape[0], 3), dtype=torch.float32, device=pos.device)
+        _check(lib().mg_force(self._c(), _ptr(phi, torch.float64, self.shape), _ptr(pos, torch.float32),
+                              int(pos.shape[0]), _ptr(out, torch.float32, (pos.shape[0], 3))))
+        return out
 
     def solve_host(self, F, phi, tol: float = 1e-6, max_vcycles: int = 50):
         """Same solve on host float64 arrays (numpy or CPU tensors); phi is overwritten."""

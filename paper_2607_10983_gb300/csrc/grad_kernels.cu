@@ -16,10 +16,12 @@ namespace {
 constexpr int BX = 32, BY = 8;
 inline dim3 cell_grid(Dims d) { return dim3((d.nx + BX - 1) / BX, (d.ny + BY - 1) / BY, d.nz); }
 
+// |s| <= 2 <= n: one conditional wrap instead of a modulo
+__device__ __forceinline__ int wrap2(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 __device__ __forceinline__ long long shifted(Dims d, int x, int y, int z, int axis, int s) {
-  if (axis == 0) x = ((x + s) % d.nx + d.nx) % d.nx;
-  else if (axis == 1) y = ((y + s) % d.ny + d.ny) % d.ny;
-  else z = ((z + s) % d.nz + d.nz) % d.nz;
+  if (axis == 0) x = wrap2(x + s, d.nx);
+  else if (axis == 1) y = wrap2(y + s, d.ny);
+  else z = wrap2(z + s, d.nz);
   return lin(d, x, y, z);
 }
 

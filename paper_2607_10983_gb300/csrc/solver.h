@@ -66,6 +66,7 @@ struct gbmg_ctx {
   double* adj_S = nullptr;      // adjoint scratch (6 finest fields), allocated on first use
   double* adj_lam = nullptr;    // adjoint scratch (1 finest field)
   double* motion = nullptr;     // mesh-motion scratch (2 finest fields), allocated on first use
+  float* force_scratch = nullptr;  // FP32 potential and force grid (4 finest fields), first use of mg_force
   float2* F_df = nullptr;       // mixed precision: source as double-float
   float2* phi_df = nullptr;     // mixed precision: potential as double-float
   float2* phi_df2 = nullptr;    // mixed precision: second potential buffer (fused update)

@@ -15,7 +15,7 @@ from __future__ import annotations
 import numpy as np
 import scipy.fft as sfft
 
-__all__ = ["white_noise", "grf", "smoothed_grf", "warm_sequence", "vector_noise", "workers"]
+__all__ = ["white_noise", "grf", "smoothed_grf", "warm_sequence", "vector_noise", "lattice_particles", "workers"]
 
 
 def workers() -> int:
@@ -113,3 +113,29 @@ def warm_sequence(shape, seed0: int, seed_eta: int, steps: int, rate: float = 0.
     eta = grf(shape, seed_eta)
     for t in range(steps):
         yield d0 + (rate * t) * eta
+
+
+def lattice_particles(n_side: int, n_mesh: int, seed: int, rms_displacement: float = 1.0) -> np.ndarray:
+    """Particles (n_side^3, 3) float32, columns x, y, z in mesh cell units on an n_mesh^3
+    mesh: a cubic lattice (spacing n_mesh / n_side, offset half a spacing) displaced along
+    the gradient of a seeded potential (a P(k) ~ k^-2 field divided by k^2, i.e. a
+    Zel'dovich-like displacement), scaled to the requested rms displacement in cells and
+    wrapped into [0, n_mesh).  Input generation only."""
+    shape = (n_side,) * 3
+    d = white_noise(shape, seed)
+    dk = sfft.rfftn(d, workers=workers())
+    nz_, ny_, nx_ = shape
+    kz = 2 * np.pi * np.fft.fftfreq(nz_)[:, None, None]
+    ky = 2 * np.pi * np.fft.fftfreq(ny_)[None, :, None]
+    kx = 2 * np.pi * np.fft.rfftfreq(nx_)[None, None, :]
+    k2 = kx ** 2 + ky ** 2 + kz ** 2
+    k2[0, 0, 0] = 1.0
+    pk = dk * k2 ** (-0.5) / k2          # delta_k ~ k^-1 white noise, potential delta_k / k^2
+    pk[0, 0, 0] = 0.0
+    disp = np.stack([sfft.irfftn(1j * kk * pk, s=shape, workers=workers()) for kk in (kx, ky, kz)], -1)
+    disp *= rms_displacement / np.sqrt((disp ** 2).sum(-1).mean())
+    spacing = n_mesh / n_side
+    g = (np.arange(n_side) + 0.5) * spacing
+    q = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1)[..., ::-1]   # (z, y, x) grid -> columns x, y, z
+    pos = (q.reshape(-1, 3) + disp.reshape(-1, 3) * spacing) % n_mesh
+    return pos.astype(np.float32)
