@@ -353,6 +353,7 @@ def run_ours(args):
         line["baselines"] = baseline_legs(args, F, dev)
         line["fixed_2_cycles"] = fixed_cycles_leg(args, solver, F)
         line["predictors"] = predictors_leg(args, solver, F)
+        line["krylov_2"] = krylov_leg(args, F)
         del F
         del phi
         solver.close()
@@ -561,6 +562,29 @@ def pm_force_leg(args, dev):
                        "mesh; force = -grad4 phi read at the particles; context: the paper quotes 17.9 ms (FFT) "
                        "and 16.5 ms (warm MG, 1 cycle) per full PM step at 256^3 on one A100")
     return out
+
+
+def krylov_leg(args, F):
+    """The sequence with V-cycle-preconditioned CG corrections (Sec. 3.2; 2 CG steps, i.e.
+    2 V-cycles, per defect-correction step), warm-started by recycling."""
+    import torch
+
+    import paper_2607_10983_gb300 as gb
+    n = args.n
+    s = gb.Solver(n, prec="mixed", degree=args.degree, krylov=2)
+    phi = torch.zeros_like(F[0])
+    s.solve(F[0], phi.clone(), tol=1e-2, max_vcycles=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    steps = []
+    for f in F:
+        _, st = s.solve(f, phi, tol=args.tol, max_vcycles=args.max_vcycles)
+        steps.append(st.cycles)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    s.close()
+    return {"solves_per_s": len(F) / dt, "outer_steps_per_solve": sum(steps) / len(F),
+            "vcycles_per_solve": 2 * sum(steps) / len(F)}
 
 
 def _timed(fn):

@@ -74,6 +74,10 @@ typedef struct {
                  /* 1: on levels of at least 2^18 cells, 2: on every level of at   */
                  /* least 16^3 (results are identical), 0: one kernel per operation; */
                  /* an odd nx selects 0 (the fused kernels work on pairs of x cells) */
+  int krylov;    /* 0: each defect-correction step applies one V-cycle; k > 0 (<= 16,    */
+                 /* flat + GBMG_MIXED + Chebyshev): k steps of conjugate gradients      */
+                 /* preconditioned by the V-cycle (Sec. 3.2) on the FP32 error equation */
+                 /* of each step; stats count defect-correction steps                  */
 } gbmg_opts;
 
 typedef struct {

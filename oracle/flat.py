@@ -292,3 +292,52 @@ def predict(history, order: int, growth: float = 1.0) -> np.ndarray:
     if order == 2:
         return 3.0 * h[0] - 3.0 * h[1] + h[2]
     raise ValueError("order must be 0, 1 or 2")
+
+
+def pcg(r: np.ndarray, steps: int, precond, apply) -> tuple[np.ndarray, list[float]]:
+    """`steps` iterations of preconditioned conjugate gradients for apply(e) = r from e = 0
+    (Sec. 3.2: multigrid as the preconditioner of a conjugate-gradient iteration).
+    Standard PCG: z = M r, p = z; alpha = (r, z) / (p, A p); e += alpha p; r -= alpha A p;
+    beta = (r', z') / (r, z); p = z' + beta p.  A and M may both be negative definite (the
+    periodic Laplacian and its V-cycle on zero-mean fields): the iterates are those of CG
+    on -A with the preconditioner -M.  Returns (e, iterates) with the iterate after each step."""
+    e = np.zeros_like(r)
+    rr = np.array(r, dtype=np.float64, copy=True)
+    z = precond(rr)
+    p = z.copy()
+    rz = float(np.vdot(rr, z))
+    its = []
+    for j in range(steps):
+        q = apply(p)
+        alpha = rz / float(np.vdot(p, q))
+        e = e + alpha * p
+        its.append(e)
+        rr = rr - alpha * q
+        if j == steps - 1:
+            break
+        z = precond(rr)
+        rz_new = float(np.vdot(rr, z))
+        beta = rz_new / rz
+        rz = rz_new
+        p = z + beta * p
+    return e, its
+
+
+def mg_pcg_solve(F: np.ndarray, phi0: np.ndarray | None = None, inner_steps: int = 2, tol: float = 1e-10,
+                 max_outer: int = 50, levels: int = 0, degree: int = 3, alpha: float = 8.0):
+    """Defect correction whose correction is `inner_steps` steps of PCG on A e = r with one
+    V-cycle from zero (Chebyshev smoother) as the preconditioner.  Returns (phi, history)
+    with the relative residual before the first and after every outer step."""
+    F = project_mean(np.asarray(F, dtype=np.float64))
+    nlev = len(level_shapes(F.shape, levels))
+    phi = np.zeros_like(F) if phi0 is None else np.array(phi0, dtype=np.float64, copy=True)
+    nF = float(np.linalg.norm(F))
+    hist = [float(np.linalg.norm(residual(F, phi))) / nF]
+    M = lambda v: vcycle(0, np.zeros_like(v), v, nlev, "cheb", degree, alpha)
+    for _ in range(max_outer):
+        if hist[-1] <= tol:
+            break
+        e, _ = pcg(residual(F, phi), inner_steps, M, apply_A)
+        phi = phi + e
+        hist.append(float(np.linalg.norm(residual(F, phi))) / nF)
+    return phi - phi.mean(), hist

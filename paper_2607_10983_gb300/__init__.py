@@ -39,7 +39,8 @@ class GbmgError(RuntimeError):
 class _Opts(ctypes.Structure):
     _fields_ = [("op", ctypes.c_int), ("prec", ctypes.c_int), ("smoother", ctypes.c_int),
                 ("degree", ctypes.c_int), ("alpha", ctypes.c_double), ("nu1", ctypes.c_int),
-                ("nu2", ctypes.c_int), ("omega", ctypes.c_double), ("fused", ctypes.c_int)]
+                ("nu2", ctypes.c_int), ("omega", ctypes.c_double), ("fused", ctypes.c_int),
+                ("krylov", ctypes.c_int)]
 
 
 class _Stats(ctypes.Structure):
@@ -188,7 +189,7 @@ class Solver:
 
     def __init__(self, shape, levels: int = 0, degree: int = 3, prec: str = "mixed",
                  smoother: str | None = None, fused: bool = True, alpha: float = 8.0,
-                 nu1: int = 2, nu2: int = 2, omega: float = 2.0 / 3.0, op: str = "flat"):
+                 nu1: int = 2, nu2: int = 2, omega: float = 2.0 / 3.0, op: str = "flat", krylov: int = 0):
         L = lib()
         if smoother is None:
             smoother = "jacobi" if op == "curv" else "chebyshev"
@@ -200,6 +201,7 @@ class Solver:
         o.prec = {"fp64": FP64, "mixed": MIXED}[prec]
         o.smoother = {"chebyshev": CHEBYSHEV, "jacobi": JACOBI}[smoother]
         o.degree, o.alpha, o.nu1, o.nu2, o.omega, o.fused = degree, alpha, nu1, nu2, omega, int(fused)
+        o.krylov = int(krylov)
         self.prec = prec
         self.work_dtype = torch.float64 if prec == "fp64" else torch.float32
         ctx = _P()

@@ -173,6 +173,7 @@ extern "C" void gbmg_default_opts(gbmg_opts* o) {
   o->nu2 = 2;
   o->omega = 2.0 / 3.0;
   o->fused = 1;
+  o->krylov = 0;
 }
 
 extern "C" const char* mg_status_string(gbmg_status s) {
@@ -217,6 +218,9 @@ extern "C" gbmg_status mg_setup(gbmg_ctx** out, int nx, int ny, int nz, int leve
                    fused_degree_supported(o.degree)))
     o.fused = 0;
   if (o.fused && nx % 2 != 0) o.fused = 0;  // the fused kernels work on x-pairs
+  if (o.krylov < 0 || o.krylov > 16) return fail(GBMG_ERR_INVALID_ARG, "mg_setup: krylov must be in [0, 16]");
+  if (o.krylov && !(o.op == GBMG_OP_FLAT7 && o.prec == GBMG_MIXED && o.smoother == GBMG_SMOOTH_CHEBYSHEV))
+    return fail(GBMG_ERR_INVALID_ARG, "mg_setup: krylov needs the flat operator, mixed precision and Chebyshev");
   const bool curv = o.op == GBMG_OP_CURV19;
 
   std::vector<Dims> dims = level_dims(nx, ny, nz, levels);

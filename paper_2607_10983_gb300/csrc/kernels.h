@@ -60,6 +60,15 @@ cudaError_t launch_df_update(cudaStream_t st, long long n, float2* phi, const fl
                              double* partials_sum);
 long long df_partial_count(long long n);
 
+// ---- conjugate-gradient vectors (FP32, device scalars): partials of a . b
+// (df_partial_count(n) blocks); e = (first ? 0 : e) + (num/den) p, r -= (num/den) q;
+// p = z + (num/den) p
+cudaError_t launch_dot_f32(cudaStream_t st, long long n, const float* a, const float* b, double* partials);
+cudaError_t launch_pcg_update(cudaStream_t st, long long n, float* e, float* r, const float* p, const float* q,
+                              const double* num, const double* den, int first);
+cudaError_t launch_pcg_dir(cudaStream_t st, long long n, float* p, const float* z, const double* num,
+                           const double* den);
+
 // ---- temporally blocked FP32 level kernels (Chebyshev smoother) ----
 bool fused_degree_supported(int degree);
 // e = Chebyshev pre-smoothing of A e = r from e = 0; rc = R (r - A e) on the next level.

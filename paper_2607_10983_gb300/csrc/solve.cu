@@ -108,6 +108,59 @@ gbmg_status vcycle_fused(gbmg_ctx* c, int l, float*& e, const float* r) {
   return GBMG_OK;
 }
 
+// Device scalar slots of the conjugate-gradient correction.
+enum PcgScal { S_RZ = 16, S_RZ_NEW = 17, S_PQ = 18 };
+
+// k = c->o.krylov steps of conjugate gradients for the finest FP32 error equation
+// A e = r, preconditioned by one V-cycle from zero (Sec. 3.2).  A and the V-cycle are
+// both negative definite on zero-mean fields, so these are the iterates of CG on -A
+// with the preconditioner -M.  r is overwritten by the inner residual; e receives the
+// pointer to the correction.
+gbmg_status pcg_correction(gbmg_ctx* c, float* r, float*& e_out) {
+  const Level& L0 = c->lv[0];
+  const long long n = ncell(L0.d);
+  if (!c->pcg) {
+    TRY(cudaMalloc((void**)&c->pcg, (size_t)n * 3 * sizeof(float)));
+    c->owned.push_back(c->pcg);
+  }
+  float* E = c->pcg;
+  float* P = c->pcg + n;
+  float* Q = c->pcg + 2 * n;
+  double* part = c->partials;
+  double* sc = c->scal;
+  const long long pr = df_partial_count(n);
+  // z = M r: one V-cycle from zero (fused legs where the level is large enough)
+  auto precond = [&](float*& z) -> gbmg_status {
+    if (c->o.fused) return vcycle_fused(c, 0, z, r);
+    float* e = (float*)L0.e;
+    float* eo = (float*)L0.e2;
+    TRY(cudaMemsetAsync(e, 0, (size_t)n * sizeof(float), c->stream));
+    TRYS(vcycle_unfused<float>(c, 0, e, eo, r));
+    z = e;
+    return GBMG_OK;
+  };
+  float* z = nullptr;
+  TRYS(precond(z));
+  TRY(cudaMemcpyAsync(P, z, (size_t)n * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+  TRY(launch_dot_f32(c->stream, n, r, z, part));
+  TRY(launch_finalize(c->stream, part, pr, sc + S_RZ, 1.0));
+  const int k = c->o.krylov;
+  for (int j = 0; j < k; ++j) {
+    TRY(launch_apply<float>(c->stream, L0.d, P, Q, 1.0f));
+    TRY(launch_dot_f32(c->stream, n, P, Q, part));
+    TRY(launch_finalize(c->stream, part, pr, sc + S_PQ, 1.0));
+    TRY(launch_pcg_update(c->stream, n, E, r, P, Q, sc + S_RZ, sc + S_PQ, j == 0 ? 1 : 0));
+    if (j == k - 1) break;
+    TRYS(precond(z));
+    TRY(launch_dot_f32(c->stream, n, r, z, part));
+    TRY(launch_finalize(c->stream, part, pr, sc + S_RZ_NEW, 1.0));
+    TRY(launch_pcg_dir(c->stream, n, P, z, sc + S_RZ_NEW, sc + S_RZ));
+    TRY(cudaMemcpyAsync(sc + S_RZ, sc + S_RZ_NEW, sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  }
+  e_out = E;
+  return GBMG_OK;
+}
+
 gbmg_status solve_fp64(gbmg_ctx* c, const double* F, double* phi, double tol, int maxv, gbmg_stats& st) {
   const Level& L0 = c->lv[0];
   const long long n = ncell(L0.d);
@@ -180,7 +233,8 @@ gbmg_status solve_mixed(gbmg_ctx* c, const double* F, double* phi, double tol, i
   while (!mon.done()) {
     if (c->o.fused) {
       float* e = nullptr;
-      TRYS(vcycle_fused(c, 0, e, r0));
+      if (c->o.krylov) TRYS(pcg_correction(c, r0, e));
+      else TRYS(vcycle_fused(c, 0, e, r0));
       {
         ProfScope ps(c, GBMG_PROF_DF0);
         TRY(launch_df_update_residual(c->stream, L0.d, phi_cur, e, c->F_df, sc + S_MEAN_F, phi_nxt, r_alt, part,
@@ -192,8 +246,12 @@ gbmg_status solve_mixed(gbmg_ctx* c, const double* F, double* phi, double tol, i
     } else {
       float* e = (float*)L0.e;
       float* eo = (float*)L0.e2;
-      TRY(cudaMemsetAsync(e, 0, (size_t)n * sizeof(float), c->stream));
-      TRYS(vcycle_unfused<float>(c, 0, e, eo, r0));
+      if (c->o.krylov) {
+        TRYS(pcg_correction(c, r0, e));
+      } else {
+        TRY(cudaMemsetAsync(e, 0, (size_t)n * sizeof(float), c->stream));
+        TRYS(vcycle_unfused<float>(c, 0, e, eo, r0));
+      }
       TRY(launch_df_update(c->stream, n, phi_cur, e, nullptr));
       {
         ProfScope ps(c, GBMG_PROF_DF0);

@@ -30,6 +30,7 @@ extern thread_local std::string g_last_error;
 std::vector<Dims> level_dims(int nx, int ny, int nz, int levels);
 // curvilinear / adjoint drivers (curv_solve.cu)
 gbmg_status curv_solve(gbmg_ctx* c, const double* F, double* phi, double tol, int maxv, gbmg_stats& st);
+
 bool dense_pinv(int n, const std::vector<double>& Lm, const std::vector<double>& w, std::vector<double>& G);
 std::vector<double> dense_flat(Dims d, double h);
 void chebyshev_schedule(int degree, double alpha, std::vector<double>& c1, std::vector<double>& c2);
@@ -67,6 +68,7 @@ struct gbmg_ctx {
   double* adj_lam = nullptr;    // adjoint scratch (1 finest field)
   double* motion = nullptr;     // mesh-motion scratch (2 finest fields), allocated on first use
   float* force_scratch = nullptr;  // FP32 potential and force grid (4 finest fields), first use of mg_force
+  float* pcg = nullptr;         // conjugate-gradient vectors e, p, q (3 finest FP32 fields), first use
   float2* F_df = nullptr;       // mixed precision: source as double-float
   float2* phi_df = nullptr;     // mixed precision: potential as double-float
   float2* phi_df2 = nullptr;    // mixed precision: second potential buffer (fused update)

@@ -287,3 +287,31 @@ def test_predictors_save_cycles_in_a_warm_sequence(gb):
     ref = flat.fft_solve(F[4])
     for p in (lin_phi, quad_phi):
         assert np.linalg.norm(p.cpu().numpy() - ref) / np.linalg.norm(ref) < 1e-8
+
+
+@pytest.mark.parametrize("fused", [0, 2])
+def test_krylov_solve_matches_oracle(gb, fused):
+    """Defect correction with V-cycle-preconditioned CG steps (Sec. 3.2): same solution as
+    the FFT oracle, residual history close to the oracle's mg_pcg_solve, and fewer
+    outer steps than plain V-cycles."""
+    shape = (32, 32, 32)
+    F = grf(shape, 51)
+    s = gb.Solver(shape, krylov=2, fused=fused)
+    phi, st = s.solve(to_dev(F), tol=1e-10, max_vcycles=40)
+    assert st.status == 0 and st.rel_res <= 1e-10
+    ref = flat.fft_solve(F)
+    assert np.linalg.norm(phi.cpu().numpy() - ref) / np.linalg.norm(ref) < 1e-9
+    _, hist = flat.mg_pcg_solve(F, inner_steps=2, tol=1e-10)
+    m = min(len(st.history), len(hist) - 1, 4)
+    np.testing.assert_allclose(st.history[:m], hist[1:m + 1], rtol=2e-2)
+    _, plain = gb.Solver(shape, fused=fused).solve(to_dev(F), tol=1e-10, max_vcycles=40)
+    assert 2 * st.cycles <= plain.cycles + 1
+
+
+def test_krylov_option_validation(gb):
+    with pytest.raises(gb.GbmgError):
+        gb.Solver(32, krylov=17)
+    with pytest.raises(gb.GbmgError):
+        gb.Solver(32, krylov=2, prec="fp64")
+    with pytest.raises(gb.GbmgError):
+        gb.Solver(16, op="curv", krylov=1)

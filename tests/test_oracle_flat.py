@@ -272,3 +272,50 @@ def test_extrapolation_saves_cycles_on_a_smooth_sequence():
     _, quad = flat.mg_solve(F[3], phi0=flat.predict([sols[2], sols[1], sols[0]], 2), tol=1e-8)
     assert lin[0] < 1e-3 * rec[0] and quad[0] < 1e-3 * rec[0]
     assert len(lin) < len(rec) and len(quad) < len(rec)
+
+
+def test_pcg_exact_preconditioner_converges_in_one_step():
+    """With the exact inverse on the zero-mean subspace as preconditioner, alpha = 1 and one
+    PCG step is the solution."""
+    r = flat.project_mean(grf(8, 41))
+    e, _ = flat.pcg(r, 1, lambda v: flat.fft_solve(v), flat.apply_A)
+    np.testing.assert_allclose(e, flat.fft_solve(r), rtol=0, atol=1e-12 * np.abs(e).max())
+
+
+def test_pcg_terminates_within_the_distinct_eigenvalues():
+    """Unpreconditioned CG on the 4^3 periodic Laplacian: the symbol 2(cos kx + cos ky + cos kz) - 6
+    with cos in {1, 0, -1} takes 6 distinct nonzero values, so CG (exact arithmetic) ends
+    within 6 steps on a zero-mean right-hand side."""
+    r = flat.project_mean(np.random.default_rng(42).standard_normal((4, 4, 4)))
+    lam = np.unique(np.round(flat.eigenvalues((4, 4, 4), rfft=False), 12))
+    assert len(lam[lam != 0]) == 6
+    e, its = flat.pcg(r, 6, lambda v: v, flat.apply_A)
+    assert np.linalg.norm(flat.apply_A(e) - r) < 1e-12 * np.linalg.norm(r)
+    e5, _ = flat.pcg(r, 5, lambda v: v, flat.apply_A)
+    assert np.linalg.norm(flat.apply_A(e5) - r) > 1e-8 * np.linalg.norm(r)
+
+
+def test_pcg_energy_decreases_and_first_step_is_scaled_vcycle():
+    """MG-preconditioned CG: the error energy (e - e*, -A (e - e*)) decreases at every step,
+    and the first step is the V-cycle correction scaled by alpha = (r, z) / (z, A z)."""
+    n = 16
+    r = flat.project_mean(grf(n, 43))
+    nlev = len(flat.level_shapes((n, n, n)))
+    M = lambda v: flat.vcycle(0, np.zeros_like(v), v, nlev)
+    exact = flat.fft_solve(r)
+    _, its = flat.pcg(r, 4, M, flat.apply_A)
+    energy = [float(np.vdot(x - exact, -flat.apply_A(x - exact))) for x in its]
+    assert all(b < a for a, b in zip(energy, energy[1:]))
+    z = M(r)
+    alpha = float(np.vdot(r, z)) / float(np.vdot(z, flat.apply_A(z)))
+    np.testing.assert_allclose(its[0], alpha * z, rtol=0, atol=1e-13 * np.abs(z).max())
+
+
+def test_mg_pcg_solve_converges_faster_than_vcycles():
+    n = 32
+    F = grf(n, 44)
+    phi, hist = flat.mg_pcg_solve(F, inner_steps=2, tol=1e-10)
+    np.testing.assert_allclose(phi, flat.fft_solve(F), rtol=0, atol=1e-9 * np.abs(phi).max())
+    _, plain = flat.mg_solve(F, tol=1e-10)
+    # two preconditioned steps per outer step beat two plain cycles per outer step
+    assert 2 * (len(hist) - 1) <= len(plain) - 1
