@@ -60,7 +60,9 @@ struct BDesc {
   int chunk[BMAXL];  // tile (chunk) size in cells per level
   double tol;
   float c1[16];
-  double c2[16];
+  float ca[BMAXL][8];  // folded Chebyshev constants a = c2 D^-1 and b = a / h^2 per level and step
+  float cb[BMAXL][8];
+  float ih2[BMAXL];    // 1 / h_l^2
   BProb* p;
   // chunk tables per level: problem index and first cell
   int* cprob[BMAXL];
@@ -84,11 +86,15 @@ __device__ __forceinline__ unsigned long long globaltimer() {
   return t;
 }
 
+// (x, y, z) of cell i of one problem: 32-bit division (every problem holds fewer than
+// 2^31 cells, checked at mg_batch_create), two divisions per cell.
 __device__ __forceinline__ void cell_xyz(Dims d, long long i, int& x, int& y, int& z) {
-  x = (int)(i % d.nx);
-  const long long q = i / d.nx;
-  y = (int)(q % d.ny);
-  z = (int)(q / d.ny);
+  const unsigned u = (unsigned)i, nx = (unsigned)d.nx, ny = (unsigned)d.ny;
+  const unsigned q = u / nx;
+  x = (int)(u - q * nx);
+  const unsigned zz = q / ny;
+  y = (int)(q - zz * ny);
+  z = (int)zz;
 }
 
 template <typename V>
@@ -250,12 +256,9 @@ __global__ void __launch_bounds__(BT) k_batched_solve(BDesc B) {
       for (int k = 0; k < V; ++k) {
         const bool from_zero = k == 0;
         const float c1 = B.c1[k];
-        const double c2 = B.c2[k];
+        const float a = B.ca[l][k], b = B.cb[l][k];
         phase(B, l, smoothed, [&](const BProb& P, int lv, long long i) {
           const Dims d = P.d[lv];
-          const double h = (double)(1 << lv);
-          const double ad = c2 * (-(h * h) / 6.0);
-          const float a = (float)ad, b = (float)(ad * (1.0 / (h * h)));
           const float* e = cur_a ? P.ea[lv] : P.eb[lv];
           float* eo = cur_a ? P.eb[lv] : P.ea[lv];
           float c = 0.f, s = 0.f;
@@ -273,9 +276,9 @@ __global__ void __launch_bounds__(BT) k_batched_solve(BDesc B) {
         grid.sync();
       }
       // residual, then full weighting to the next level
+      const float ih2 = B.ih2[l];
       phase(B, l, smoothed, [&](const BProb& P, int lv, long long i) {
         const Dims d = P.d[lv];
-        const float ih2 = (float)(1.0 / ((double)(1 << lv) * (double)(1 << lv)));
         const float* e = cur_a ? P.ea[lv] : P.eb[lv];
         int x, y, z;
         cell_xyz(d, i, x, y, z);
@@ -345,12 +348,9 @@ __global__ void __launch_bounds__(BT) k_batched_solve(BDesc B) {
       grid.sync();
       for (int k = 0; k < V; ++k) {
         const float c1 = B.c1[k];
-        const double c2 = B.c2[k];
+        const float a = B.ca[l][k], b = B.cb[l][k];
         phase(B, l, smoothed, [&](const BProb& P, int lv, long long i) {
           const Dims d = P.d[lv];
-          const double h = (double)(1 << lv);
-          const double ad = c2 * (-(h * h) / 6.0);
-          const float a = (float)ad, b = (float)(ad * (1.0 / (h * h)));
           const float* e = cur_a ? P.ea[lv] : P.eb[lv];
           float* eo = cur_a ? P.eb[lv] : P.ea[lv];
           int x, y, z;
@@ -498,6 +498,8 @@ extern "C" gbmg_status mg_batch_create(gbmg_batch** out, gbmg_ctx* const* ctxs, 
       return fail(GBMG_ERR_INVALID_ARG,
                   "mg_batch_create: contexts must be flat, mixed precision, Chebyshev, fused = 0");
     if (c->L > BMAXL || c->L < 2) return fail(GBMG_ERR_INVALID_ARG, "mg_batch_create: each problem needs 2 to 16 levels");
+    if (ncell(c->lv[0].d) >= (1ll << 31)) return fail(GBMG_ERR_INVALID_ARG, "mg_batch_create: a problem has 2^31 cells or more");
+    if (c->o.degree > 8) return fail(GBMG_ERR_INVALID_ARG, "mg_batch_create: Chebyshev degree above 8");
     if (c->o.degree != ctxs[0]->o.degree || c->o.alpha != ctxs[0]->o.alpha)
       return fail(GBMG_ERR_INVALID_ARG, "mg_batch_create: all contexts need the same smoother");
     if (c->device != ctxs[0]->device) return fail(GBMG_ERR_INVALID_ARG, "mg_batch_create: contexts on different devices");
@@ -565,9 +567,16 @@ extern "C" gbmg_status mg_batch_create(gbmg_batch** out, gbmg_ctx* const* ctxs, 
   D.count = count;
   D.maxL = maxL;
   D.degree = ctxs[0]->o.degree;
-  for (int k = 0; k < D.degree && k < 16; ++k) {
-    D.c1[k] = (float)ctxs[0]->cc1[k];
-    D.c2[k] = ctxs[0]->cc2[k];
+  for (int k = 0; k < D.degree && k < 16; ++k) D.c1[k] = (float)ctxs[0]->cc1[k];
+  for (int l = 0; l < maxL; ++l) {
+    const double h = (double)(1 << l);
+    D.ih2[l] = (float)(1.0 / (h * h));
+    for (int k = 0; k < D.degree && k < 8; ++k) {
+      double a, b;
+      cheb_constants(ctxs[0]->cc2[k], h, a, b);
+      D.ca[l][k] = (float)a;
+      D.cb[l][k] = (float)b;
+    }
   }
   D.p = (BProb*)(m + oP);
   for (int l = 0; l < maxL; ++l) {
