@@ -4,14 +4,18 @@
 //
 // Each problem keeps the hierarchy of its own context.  The kernel runs the whole
 // mixed-precision solve of every problem: prologue (double-float conversion, mean,
-// first residual), then V-cycles of the one-kernel-per-operation arithmetic (same
-// per-cell code, so each problem's iterates equal those of mg_solve with fused = 0),
-// each operation a grid-wide phase separated by grid.sync().  Work inside a phase is
-// split into chunks (tiles of whole x rows, a per-level size) that belong to one
-// problem, so per-problem sums
-// are deterministic (chunk partials summed in order).  A problem that has converged
-// (or failed) skips its chunks; the loop ends when none is active or max_vcycles is
-// reached.  Per-problem completion times come from %globaltimer.
+// first residual), V-cycles, epilogue (gauge, FP64 output); every step is a
+// grid-wide phase separated by grid.sync().  Levels of at least 16^3 run the fused
+// legs (one pass per level visit and leg, the device code of the per-level fused
+// kernels) and the finest level the fused double-float update and residual; the
+// work of a fused phase is the list of (problem, tile, plane) of every problem,
+// split evenly over the CTAs.  Smaller levels run the one-kernel-per-operation
+// arithmetic over chunks (tiles of whole x rows, a per-level size) of one problem.
+// All of it rounds exactly like mg_solve, so each problem's iterates equal the
+// single solves' up to the summation order of the norms and means, which are summed
+// per problem over fixed chunks in a fixed order (deterministic).  A problem that has
+// converged (or failed) skips its work; the loop ends when none is active or
+// max_vcycles is reached.  Per-problem completion times come from %globaltimer.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -19,7 +23,9 @@
 #include <cstring>
 #include <vector>
 
+#include "dfk.cuh"
 #include "kernels.h"
+#include "legs.cuh"
 #include "solver.h"
 #include "stencil.cuh"
 
@@ -32,7 +38,19 @@ constexpr int BMAXL = 16;
 constexpr int CHUNK = 4096;      // default tile (chunk) size in cells
 constexpr int MINCHUNK = 1024;   // smallest tile the tables are sized for
 constexpr int MAXCHUNK = 65536;
-constexpr int BT = 256;
+constexpr int BT = 384;          // block size (the fused legs' thread-column layout)
+constexpr int DFZC = 16;         // z planes per item of the fused double-float phase
+
+// tiles of the fused device code at BT threads
+template <int V>
+struct BDown {
+  using T = legs::PTile<64, (V >= 4 ? 24 : 32), V + 1, BT, 4>;
+};
+template <int V>
+struct BUp {
+  using T = legs::PTile<64, 32, (V > 0 ? V : 1), BT, 4>;
+};
+using BDf = dfk::DTile<64, 16, 2, BT>;
 
 // per-problem scalars
 enum { P_MEAN = 0, P_F2 = 1, P_R2 = 2, P_REL = 3, P_PREV1 = 4, P_PREV2 = 5, P_MPHI = 6, P_N = 8 };
@@ -49,10 +67,13 @@ struct BProb {
   float* t[BMAXL];
   const float* G;
   float2* F;
-  float2* phi;
+  float2* phi;   // double-float phi, and the second buffer of the fused update (phi2)
+  float2* phi2;
   const double* src;
   double* out;
-  int c0, nch;  // first level-0 chunk and count
+  int c0, nch;      // first level-0 chunk and count
+  unsigned fmask;   // bit l: level l runs the fused legs
+  int dffused;      // the finest level runs the fused double-float update (even nx)
 };
 
 struct BDesc {
@@ -63,6 +84,14 @@ struct BDesc {
   float ca[BMAXL][8];  // folded Chebyshev constants a = c2 D^-1 and b = a / h^2 per level and step
   float cb[BMAXL][8];
   float ih2[BMAXL];    // 1 / h_l^2
+  const legs::Coef* coef;       // folded Chebyshev constants per level (device)
+  const long long* doff[BMAXL];  // per level: prefix over problems of fused down-leg planes
+  const long long* uoff[BMAXL];  // per level: the same for the up leg
+  long long dtot[BMAXL], utot[BMAXL];
+  const int* dfoff;              // prefix over problems of fused double-float items
+  int dftot;
+  double* dfpart;                // per double-float item: partial sum of r^2
+  int* phicur;                   // per problem: 0 = phi, 1 = phi2 holds the current iterate
   BProb* p;
   // chunk tables per level: problem index and first cell
   int* cprob[BMAXL];
@@ -148,10 +177,97 @@ __device__ __forceinline__ double chunk_total(const BDesc& B, const BProb& P, co
   return s;
 }
 
-__global__ void __launch_bounds__(BT) k_batched_solve(BDesc B) {
+// level l of problem P runs the fused legs
+__device__ __forceinline__ bool lv_fused(const BProb& P, int l) { return (P.fmask >> l) & 1u; }
+// buffer holding the final correction of level l after its up leg
+__device__ __forceinline__ float* final_e(const BProb& P, int l) {
+  return (l < P.L - 1 && lv_fused(P, l)) ? P.eb[l] : P.ea[l];
+}
+
+// Fused phases: the (problem, tile, plane) list of level l, split evenly over the
+// CTAs; each contiguous run within one tile is one z segment of the leg.
+template <int V>
+__device__ __forceinline__ void fused_down(const BDesc& B, int l, float* smf) {
+  using TL = typename BDown<V>::T;
+  const long long T = B.dtot[l];
+  if (T == 0) return;
+  long long a = (long long)blockIdx.x * T / gridDim.x;
+  const long long b = (long long)(blockIdx.x + 1) * T / gridDim.x;
+  int p = 0;
+  while (a < b) {
+    while (B.doff[l][p + 1] <= a) ++p;
+    const BProb& P = B.p[p];
+    const Dims d = P.d[l];
+    const long long loc = a - B.doff[l][p];
+    const long long tile = loc / d.nz;
+    const int z0 = (int)(loc % d.nz);
+    const int zend = (int)(z0 + (b - a) < d.nz ? z0 + (b - a) : d.nz);
+    const int tiles_x = (d.nx + TL::TX - 1) / TL::TX;
+    if (B.status[p] == ST_ACTIVE)
+      legs::down_segment<V, TL>(d, P.r[l], P.ea[l], P.r[l + 1], (int)(tile % tiles_x) * TL::TX,
+                                (int)(tile / tiles_x) * TL::TY, z0, zend, B.ih2[l], B.coef[l], smf);
+    a += zend - z0;
+    __syncthreads();
+  }
+}
+
+template <int V>
+__device__ __forceinline__ void fused_up(const BDesc& B, int l, float* smf) {
+  using TL = typename BUp<V>::T;
+  const long long T = B.utot[l];
+  if (T == 0) return;
+  long long a = (long long)blockIdx.x * T / gridDim.x;
+  const long long b = (long long)(blockIdx.x + 1) * T / gridDim.x;
+  int p = 0;
+  while (a < b) {
+    while (B.uoff[l][p + 1] <= a) ++p;
+    const BProb& P = B.p[p];
+    const Dims d = P.d[l];
+    const long long loc = a - B.uoff[l][p];
+    const long long tile = loc / d.nz;
+    const int z0 = (int)(loc % d.nz);
+    const int zend = (int)(z0 + (b - a) < d.nz ? z0 + (b - a) : d.nz);
+    const int tiles_x = (d.nx + TL::TX - 1) / TL::TX;
+    if (B.status[p] == ST_ACTIVE)
+      legs::up_segment<V, TL>(d, P.ea[l], final_e(P, l + 1), P.r[l], P.eb[l], (int)(tile % tiles_x) * TL::TX,
+                              (int)(tile / tiles_x) * TL::TY, z0, zend, B.ih2[l], B.coef[l], smf);
+    a += zend - z0;
+    __syncthreads();
+  }
+}
+
+// Fused double-float update + residual of the finest level: items of one tile and
+// DFZC planes, each with its own partial sum of r^2 (summed per problem in order).
+__device__ __forceinline__ void fused_df(const BDesc& B, float* smf, double* sh) {
+  for (int it = blockIdx.x; it < B.dftot; it += gridDim.x) {
+    int p = 0;
+    while (B.dfoff[p + 1] <= it) ++p;
+    if (B.status[p] != ST_ACTIVE) continue;
+    const BProb& P = B.p[p];
+    const Dims d = P.d[0];
+    const int loc = it - B.dfoff[p];
+    const int tiles_x = (d.nx + BDf::TX - 1) / BDf::TX, nzc = (d.nz + DFZC - 1) / DFZC;
+    const int tile = loc / nzc, zc = loc % nzc;
+    const int cur = B.phicur[p];
+    const float2 m1 = f64_to_df(B.sc[p * P_N + P_MEAN]);
+    float r2 = 0.f, f2 = 0.f;
+    PAcc ps{bcast(0.f), bcast(0.f)};
+    dfk::df_segment<BDf>(d, cur ? P.phi2 : P.phi, final_e(P, 0), P.F, DF2{bcast(m1.x), bcast(m1.y)},
+                         cur ? P.phi : P.phi2, P.r[0], (tile % tiles_x) * BDf::TX, (tile / tiles_x) * BDf::TY,
+                         zc * DFZC, min(zc * DFZC + DFZC, d.nz), smf, r2, ps, f2);
+    const double s = block_sum_f(r2, sh);
+    if (threadIdx.x == 0) B.dfpart[it] = s;
+  }
+}
+
+// V = 1..4: the Chebyshev degree, fused legs on levels of at least 16^3; V = 0: any
+// degree (B.degree), one kernel per operation everywhere.
+template <int V>
+__global__ void __launch_bounds__(BT, 1) k_batched_solve(BDesc B) {
   cg::grid_group grid = cg::this_grid();
+  extern __shared__ __align__(16) float smf[];
   __shared__ double sh[32];
-  const int V = B.degree;
+  const int Vd = V > 0 ? V : B.degree;
   const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
   if (lead) *B.tstart = globaltimer();
   // ---- prologue: double-float copies and the mean of F
@@ -162,18 +278,21 @@ __global__ void __launch_bounds__(BT) k_batched_solve(BDesc B) {
     acc.add(f.x);
     acc.c += f.y;
   });
+  for (int pi = blockIdx.x * blockDim.x + threadIdx.x; pi < B.count; pi += gridDim.x * blockDim.x) B.phicur[pi] = 0;
   grid.sync();
   for (int pi = blockIdx.x * blockDim.x + threadIdx.x; pi < B.count; pi += gridDim.x * blockDim.x) {
     const BProb& P = B.p[pi];
     B.sc[pi * P_N + P_MEAN] = chunk_total(B, P, B.part0) / (double)ncell(P.d[0]);
   }
   grid.sync();
-  // residual of the initial guess and ||F - mean||^2
-  auto df_residual_phase = [&](bool with_f2) {
+  // residual of the current iterate (per operation, problems selected by `sel`) and,
+  // on the first call, ||F - mean||^2
+  auto df_residual_phase = [&](bool with_f2, bool fused_too) {
     for (int c = blockIdx.x; c < B.nchunk[0]; c += gridDim.x) {
       const int pi = B.cprob[0][c];
       if (B.status[pi] != ST_ACTIVE) continue;
       const BProb& P = B.p[pi];
+      if (!fused_too && V > 0 && P.dffused) continue;
       const Dims d = P.d[0];
       const float2 m = f64_to_df(B.sc[pi * P_N + P_MEAN]);
       const long long s0 = B.cstart[0][c];
@@ -211,7 +330,14 @@ __global__ void __launch_bounds__(BT) k_batched_solve(BDesc B) {
       const BProb& P = B.p[pi];
       double* s = B.sc + pi * P_N;
       if (first) s[P_F2] = chunk_total(B, P, B.part1);
-      const double r2 = chunk_total(B, P, B.part0);
+      double r2;
+      if (!first && V > 0 && P.dffused) {
+        r2 = 0.0;
+        for (int k = B.dfoff[pi]; k < B.dfoff[pi + 1]; ++k) r2 += B.dfpart[k];
+        B.phicur[pi] ^= 1;  // the fused update wrote the other buffer
+      } else {
+        r2 = chunk_total(B, P, B.part0);
+      }
       const double rel = s[P_F2] > 0.0 ? sqrt(r2 / s[P_F2]) : sqrt(r2);
       int cyc = B.cycles[pi];
       if (first) {
@@ -236,7 +362,7 @@ __global__ void __launch_bounds__(BT) k_batched_solve(BDesc B) {
       }
     }
   };
-  df_residual_phase(true);
+  df_residual_phase(true, true);
   grid.sync();
   finalize(true);
   grid.sync();
@@ -251,9 +377,11 @@ __global__ void __launch_bounds__(BT) k_batched_solve(BDesc B) {
     if (*((volatile int*)B.any_active) == 0) break;
     // down: levels 0 .. maxL-2, then the coarsest solves
     for (int l = 0; l + 1 < B.maxL; ++l) {
-      auto smoothed = [&](const BProb& P, int lv) { return lv < P.L - 1; };
+      // per-operation levels (smaller than 16^3, or every level for V = 0)
+      auto smoothed = [&](const BProb& P, int lv) { return lv < P.L - 1 && !(V > 0 && lv_fused(P, lv)); };
+      if constexpr (V > 0) fused_down<V>(B, l, smf);
       bool cur_a = true;  // current e in ea
-      for (int k = 0; k < V; ++k) {
+      for (int k = 0; k < Vd; ++k) {
         const bool from_zero = k == 0;
         const float c1 = B.c1[k];
         const float a = B.ca[l][k], b = B.cb[l][k];
@@ -285,36 +413,34 @@ __global__ void __launch_bounds__(BT) k_batched_solve(BDesc B) {
         P.t[lv][i] = resid_from_sum(P.r[lv][i], nsum_at(e, d, x, y, z, i), e[i], ih2);
       });
       grid.sync();
-      if (l + 1 < B.maxL) {
-        phase(B, l + 1, [&](const BProb& P, int lv) { return lv - 1 < P.L - 1; },
-              [&](const BProb& P, int lv, long long I) {
-                const Dims df = P.d[lv - 1], dc = P.d[lv];
-                int X, Y, Z;
-                cell_xyz(dc, I, X, Y, Z);
-                const float* f = P.t[lv - 1];
-                int xs[3], ys[3], zs[3];
+      phase(B, l + 1, [&](const BProb& P, int lv) { return smoothed(P, lv - 1); },
+            [&](const BProb& P, int lv, long long I) {
+              const Dims df = P.d[lv - 1], dc = P.d[lv];
+              int X, Y, Z;
+              cell_xyz(dc, I, X, Y, Z);
+              const float* f = P.t[lv - 1];
+              int xs[3], ys[3], zs[3];
 #pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                  xs[k] = wrapi(2 * X + k - 1, df.nx);
-                  ys[k] = wrapi(2 * Y + k - 1, df.ny);
-                  zs[k] = wrapi(2 * Z + k - 1, df.nz);
-                }
-                float yv[3];
+              for (int k = 0; k < 3; ++k) {
+                xs[k] = wrapi(2 * X + k - 1, df.nx);
+                ys[k] = wrapi(2 * Y + k - 1, df.ny);
+                zs[k] = wrapi(2 * Z + k - 1, df.nz);
+              }
+              float yv[3];
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                  float zv[3];
+              for (int a = 0; a < 3; ++a) {
+                float zv[3];
 #pragma unroll
-                  for (int b = 0; b < 3; ++b)
-                    zv[b] = fw3(f[lin(df, xs[a], ys[b], zs[0])], f[lin(df, xs[a], ys[b], zs[1])],
-                                f[lin(df, xs[a], ys[b], zs[2])]);
-                  yv[a] = fw3(zv[0], zv[1], zv[2]);
-                }
-                P.r[lv][I] = fw3(yv[0], yv[1], yv[2]);
-              });
-      }
+                for (int b = 0; b < 3; ++b)
+                  zv[b] = fw3(f[lin(df, xs[a], ys[b], zs[0])], f[lin(df, xs[a], ys[b], zs[1])],
+                              f[lin(df, xs[a], ys[b], zs[2])]);
+                yv[a] = fw3(zv[0], zv[1], zv[2]);
+              }
+              P.r[lv][I] = fw3(yv[0], yv[1], yv[2]);
+            });
       grid.sync();
       // coarsest solves of the problems whose hierarchy ends at level l + 1
-      if (l + 1 < B.maxL) {
+      {
         const int warps = blockDim.x / 32, lane = threadIdx.x & 31;
         for (int pi = blockIdx.x; pi < B.count; pi += gridDim.x) {
           const BProb& P = B.p[pi];
@@ -332,21 +458,23 @@ __global__ void __launch_bounds__(BT) k_batched_solve(BDesc B) {
       }
       grid.sync();
     }
-    // up: levels maxL-2 .. 0.  Pre-smoothing from zero leaves e in eb when V is odd
-    // and in ea when V is even; V more steps then always end in ea, which is where
-    // the coarser level's correction is read from and where the coarsest solve writes.
+    // up: levels maxL-2 .. 0.  Per operation: pre-smoothing from zero leaves e in eb
+    // when V is odd and in ea when V is even; V more steps then always end in ea,
+    // which is where the coarser level's correction is read from and where the
+    // coarsest solve writes.  Fused levels end in eb (final_e).
     for (int l = B.maxL - 2; l >= 0; --l) {
-      auto smoothed = [&](const BProb& P, int lv) { return lv < P.L - 1; };
-      bool cur_a = (V % 2) == 0;
+      auto smoothed = [&](const BProb& P, int lv) { return lv < P.L - 1 && !(V > 0 && lv_fused(P, lv)); };
+      if constexpr (V > 0) fused_up<V>(B, l, smf);
+      bool cur_a = (Vd % 2) == 0;
       phase(B, l, smoothed, [&](const BProb& P, int lv, long long i) {
         const Dims d = P.d[lv];
         int x, y, z;
         cell_xyz(d, i, x, y, z);
         float* e = cur_a ? P.ea[lv] : P.eb[lv];
-        e[i] = t_add(e[i], prolong_value(P.ea[lv + 1], P.d[lv + 1], x, y, z));
+        e[i] = t_add(e[i], prolong_value(final_e(P, lv + 1), P.d[lv + 1], x, y, z));
       });
       grid.sync();
-      for (int k = 0; k < V; ++k) {
+      for (int k = 0; k < Vd; ++k) {
         const float c1 = B.c1[k];
         const float a = B.ca[l][k], b = B.cb[l][k];
         phase(B, l, smoothed, [&](const BProb& P, int lv, long long i) {
@@ -365,10 +493,11 @@ __global__ void __launch_bounds__(BT) k_batched_solve(BDesc B) {
       }
     }
     // phi += e, next residual, convergence
-    phase(B, 0, [&](const BProb&, int) { return true; },
-          [&](const BProb& P, int, long long i) { P.phi[i] = df_add_f(P.phi[i], P.ea[0][i]); });
+    if constexpr (V > 0) fused_df(B, smf, sh);
+    phase(B, 0, [&](const BProb& P, int) { return !(V > 0 && P.dffused); },
+          [&](const BProb& P, int, long long i) { P.phi[i] = df_add_f(P.phi[i], final_e(P, 0)[i]); });
     grid.sync();
-    df_residual_phase(false);
+    df_residual_phase(false, false);
     grid.sync();
     finalize(false);
     grid.sync();
@@ -383,7 +512,7 @@ __global__ void __launch_bounds__(BT) k_batched_solve(BDesc B) {
   grid.sync();
   // ---- epilogue: gauge and FP64 output for every problem
   phase0_sum(B, B.part0, sh, true, [&](const BProb& P, long long i, DfAcc& acc) {
-    const float2 v = P.phi[i];
+    const float2 v = (B.phicur[&P - B.p] ? P.phi2 : P.phi)[i];
     acc.add(v.x);
     acc.c += v.y;
   });
@@ -396,13 +525,14 @@ __global__ void __launch_bounds__(BT) k_batched_solve(BDesc B) {
   for (int c = blockIdx.x; c < B.nchunk[0]; c += gridDim.x) {
     const int pi = B.cprob[0][c];
     const BProb& P = B.p[pi];
+    const float2* ph = B.phicur[pi] ? P.phi2 : P.phi;
     float2 ms = f64_to_df(B.sc[pi * P_N + P_MPHI]);
     ms.x = -ms.x;
     ms.y = -ms.y;
     const long long s0 = B.cstart[0][c];
     const long long n = ncell(P.d[0]);
     const long long s1 = s0 + B.chunk[0] < n ? s0 + B.chunk[0] : n;
-    for (long long i = s0 + threadIdx.x; i < s1; i += blockDim.x) P.out[i] = df_to_f64(df_add(P.phi[i], ms));
+    for (long long i = s0 + threadIdx.x; i < s1; i += blockDim.x) P.out[i] = df_to_f64(df_add(ph[i], ms));
   }
 }
 
@@ -434,8 +564,14 @@ struct gbmg_batch {
   unsigned version = 0, g_version = ~0u;
   double g_tol = -1.0;
   int g_maxv = -1, g_blocks = -1;
+  // kernel for the batch's degree and its dynamic shared memory; device memory of the
+  // second phi buffers and the fused-phase tables
+  const void* kern = nullptr;
+  size_t smem = 0;
+  char* mem2 = nullptr;
   ~gbmg_batch() {
     if (gexec) cudaGraphExecDestroy(gexec);
+    if (mem2) cudaFree(mem2);
     if (gstream) cudaStreamDestroy(gstream);
     for (auto ev : gev)
       if (ev) cudaEventDestroy(ev);
@@ -477,9 +613,33 @@ gbmg_status build_tables(gbmg_batch* b) {
   return GBMG_OK;
 }
 
+// dynamic shared memory of the fused phases at degree V
+template <int V>
+size_t batch_smem() {
+  size_t s = 0;
+  if constexpr (V > 0) {
+    using TD = typename BDown<V>::T;
+    using TU = typename BUp<V>::T;
+    s = std::max(s, (size_t)(V + 1) * 2 * TD::PLANE * sizeof(float));
+    s = std::max(s, ((size_t)V * 2 * TU::PLANE + 3 * legs::PCoarse<TU>::CN) * sizeof(float));
+    s = std::max(s, (size_t)3 * BDf::PLANE * sizeof(float));
+  }
+  return s;
+}
+
+void pick_kernel(int degree, const void*& k, size_t& smem) {
+  switch (degree) {
+    case 1: k = (const void*)k_batched_solve<1>; smem = batch_smem<1>(); return;
+    case 2: k = (const void*)k_batched_solve<2>; smem = batch_smem<2>(); return;
+    case 3: k = (const void*)k_batched_solve<3>; smem = batch_smem<3>(); return;
+    case 4: k = (const void*)k_batched_solve<4>; smem = batch_smem<4>(); return;
+    default: k = (const void*)k_batched_solve<0>; smem = 0; return;
+  }
+}
+
 gbmg_status max_blocks(const gbmg_batch* b, int& blocks) {
   int per_sm = 0, sms = 0;
-  TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched_solve, BT, 0));
+  TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b->kern, BT, b->smem));
   TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
   if (per_sm < 1) return fail(GBMG_ERR_CUDA, "batch: kernel does not fit on an SM");
   blocks = per_sm * sms;
@@ -612,6 +772,99 @@ extern "C" gbmg_status mg_batch_create(gbmg_batch** out, gbmg_ctx* const* ctxs, 
     P.F = c->F_df;
     P.phi = c->phi_df;
   }
+  // fused phases: levels of at least 16^3 (not the coarsest) for degrees 1..4, the
+  // finest level's double-float update for even nx; plane lists per level, items of
+  // the double-float phase, second phi buffers, per-level Chebyshev constants
+  const int V = (D.degree >= 1 && D.degree <= 4) ? D.degree : 0;
+  pick_kernel(D.degree, b->kern, b->smem);
+  const int DTY = V >= 4 ? 24 : 32;
+  std::vector<long long> doff((size_t)maxL * (count + 1), 0), uoff((size_t)maxL * (count + 1), 0);
+  std::vector<int> dfoff(count + 1, 0);
+  long long phi2_cells = 0;
+  for (int i = 0; i < count; ++i) {
+    const gbmg_ctx* c = b->ctx[i];
+    BProb& P = b->hprob[i];
+    for (int l = 0; V > 0 && l + 1 < c->L; ++l) {
+      const Dims d = c->lv[l].d;
+      if (d.nx >= 16 && d.ny >= 16 && d.nz >= 16) P.fmask |= 1u << l;
+    }
+    P.dffused = V > 0 && c->lv[0].d.nx % 2 == 0;
+    if (P.dffused) phi2_cells += ncell(c->lv[0].d);
+  }
+  for (int l = 0; l < maxL; ++l)
+    for (int i = 0; i < count; ++i) {
+      const gbmg_ctx* c = b->ctx[i];
+      long long dn = 0, un = 0;
+      if (b->hprob[i].fmask >> l & 1u) {
+        const Dims d = c->lv[l].d;
+        dn = (long long)ceil_div(d.nx, 64) * ceil_div(d.ny, DTY) * d.nz;
+        un = (long long)ceil_div(d.nx, 64) * ceil_div(d.ny, 32) * d.nz;
+      }
+      doff[(size_t)l * (count + 1) + i + 1] = doff[(size_t)l * (count + 1) + i] + dn;
+      uoff[(size_t)l * (count + 1) + i + 1] = uoff[(size_t)l * (count + 1) + i] + un;
+    }
+  for (int i = 0; i < count; ++i) {
+    const Dims d = b->ctx[i]->lv[0].d;
+    const int items = b->hprob[i].dffused ? (int)(ceil_div(d.nx, BDf::TX) * ceil_div(d.ny, BDf::TY) * ceil_div(d.nz, DFZC)) : 0;
+    dfoff[i + 1] = dfoff[i] + items;
+  }
+  std::vector<legs::Coef> coef(maxL);
+  for (int l = 0; l < maxL; ++l) {
+    std::memset(&coef[l], 0, sizeof(legs::Coef));
+    for (int k = 0; k < D.degree && k < 16; ++k) {
+      double a, bb;
+      cheb_constants(ctxs[0]->cc2[k], (double)(1 << l), a, bb);
+      coef[l].c1[k] = (float)ctxs[0]->cc1[k];
+      coef[l].a[k] = (float)a;
+      coef[l].b[k] = (float)bb;
+    }
+  }
+  {
+    size_t off2 = 0;
+    auto take2 = [&](size_t bytes) {
+      const size_t o = off2;
+      off2 += (bytes + 255) & ~(size_t)255;
+      return o;
+    };
+    const size_t oPhi2 = take2(sizeof(float2) * (size_t)std::max(phi2_cells, 1ll));
+    const size_t oDoff = take2(sizeof(long long) * doff.size()), oUoff = take2(sizeof(long long) * uoff.size());
+    const size_t oDf = take2(sizeof(int) * dfoff.size());
+    const size_t oDfp = take2(sizeof(double) * (size_t)std::max(dfoff[count], 1));
+    const size_t oCur = take2(sizeof(int) * count), oCoef = take2(sizeof(legs::Coef) * maxL);
+    e = cudaMalloc((void**)&b->mem2, off2);
+    if (e == cudaSuccess) e = cudaMemcpy(b->mem2 + oDoff, doff.data(), sizeof(long long) * doff.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->mem2 + oUoff, uoff.data(), sizeof(long long) * uoff.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->mem2 + oDf, dfoff.data(), sizeof(int) * dfoff.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->mem2 + oCoef, coef.data(), sizeof(legs::Coef) * maxL, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      delete b;
+      return cuda_fail(e, "mg_batch_create: fused-phase tables");
+    }
+    long long acc = 0;
+    for (int i = 0; i < count; ++i)
+      if (b->hprob[i].dffused) {
+        b->hprob[i].phi2 = reinterpret_cast<float2*>(b->mem2 + oPhi2) + acc;
+        acc += ncell(b->ctx[i]->lv[0].d);
+      }
+    for (int l = 0; l < maxL; ++l) {
+      D.doff[l] = reinterpret_cast<const long long*>(b->mem2 + oDoff) + (size_t)l * (count + 1);
+      D.uoff[l] = reinterpret_cast<const long long*>(b->mem2 + oUoff) + (size_t)l * (count + 1);
+      D.dtot[l] = doff[(size_t)l * (count + 1) + count];
+      D.utot[l] = uoff[(size_t)l * (count + 1) + count];
+    }
+    D.dfoff = reinterpret_cast<const int*>(b->mem2 + oDf);
+    D.dftot = dfoff[count];
+    D.dfpart = reinterpret_cast<double*>(b->mem2 + oDfp);
+    D.phicur = reinterpret_cast<int*>(b->mem2 + oCur);
+    D.coef = reinterpret_cast<const legs::Coef*>(b->mem2 + oCoef);
+  }
+  if (b->smem > 0) {
+    e = cudaFuncSetAttribute(b->kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+    if (e != cudaSuccess) {
+      delete b;
+      return cuda_fail(e, "mg_batch_create: shared-memory attribute");
+    }
+  }
   gbmg_status st = build_tables(b);
   // persistent grid: every block resident at once (cooperative launch)
   if (st == GBMG_OK) st = max_blocks(b, b->blocks);
@@ -644,7 +897,7 @@ extern "C" gbmg_status mg_batch_use_graph(gbmg_batch* b, int on) {
 extern "C" gbmg_status mg_batch_set_tiles(gbmg_batch* b, const int* tile_cells, int nlevels) {
   if (!b || !tile_cells || nlevels < 1) return fail(GBMG_ERR_INVALID_ARG, "mg_batch_set_tiles: bad argument");
   for (int l = 0; l < nlevels && l < b->maxL; ++l)
-    if (tile_cells[l] < MINCHUNK || tile_cells[l] > MAXCHUNK || tile_cells[l] % BT != 0)
+    if (tile_cells[l] < MINCHUNK || tile_cells[l] > MAXCHUNK || tile_cells[l] % 256 != 0)
       return fail(GBMG_ERR_INVALID_ARG, "mg_batch_set_tiles: tile sizes must be multiples of 256 in [1024, 65536]");
   DeviceGuard g(b->device);
   for (int l = 0; l < nlevels && l < b->maxL; ++l) b->desc.chunk[l] = tile_cells[l];
@@ -679,7 +932,7 @@ extern "C" gbmg_status mg_batch_solve(gbmg_batch* b, const double* const* src_de
     TRY(cudaMemsetAsync(D.status, 0, sizeof(int) * b->count, st));
     TRY(cudaMemsetAsync(D.cycles, 0, sizeof(int) * b->count, st));
     void* args[] = {&D};
-    TRY(cudaLaunchCooperativeKernel((void*)k_batched_solve, dim3(b->blocks), dim3(BT), args, 0, st));
+    TRY(cudaLaunchCooperativeKernel(b->kern, dim3(b->blocks), dim3(BT), args, b->smem, st));
     TRY(cudaMemcpyAsync(b->hstatus, D.status, b->res_bytes, cudaMemcpyDeviceToHost, st));
     TRY(cudaMemcpyAsync(b->hsc, D.sc, sizeof(double) * P_N * b->count, cudaMemcpyDeviceToHost, st));
     return GBMG_OK;
