@@ -42,13 +42,17 @@ constexpr int BT = 384;          // block size (the fused legs' thread-column la
 constexpr int DFZC = 16;         // z planes per item of the fused double-float phase
 
 // tiles of the fused device code at BT threads
+// (columns of 4 pairs for the down leg, of 3 pairs for the up leg: at the register
+// limit of BT threads per SM, 4-pair columns spill in the up leg)
+constexpr int down_ty(int v) { return v >= 4 ? 24 : 32; }
+constexpr int up_ty(int v) { return v >= 4 ? 20 : 24; }
 template <int V>
 struct BDown {
-  using T = legs::PTile<64, (V >= 4 ? 24 : 32), V + 1, BT, 4>;
+  using T = legs::PTile<64, down_ty(V), V + 1, BT, 4>;
 };
 template <int V>
 struct BUp {
-  using T = legs::PTile<64, 32, (V > 0 ? V : 1), BT, 4>;
+  using T = legs::PTile<64, up_ty(V), (V > 0 ? V : 1), BT, 3>;
 };
 using BDf = dfk::DTile<64, 16, 2, BT>;
 
@@ -91,6 +95,9 @@ struct BDesc {
   const int* dfoff;              // prefix over problems of fused double-float items
   int dftot;
   double* dfpart;                // per double-float item: partial sum of r^2
+  double* dfpart2;               // per double-float item: partial sum of (F - m)^2 (first residual)
+  unsigned perop;                // bit l: some problem runs level l per operation (not the coarsest)
+  unsigned coarse;               // bit l: some problem's coarsest level is l
   int* phicur;                   // per problem: 0 = phi, 1 = phi2 holds the current iterate
   BProb* p;
   // chunk tables per level: problem index and first cell
@@ -238,7 +245,7 @@ __device__ __forceinline__ void fused_up(const BDesc& B, int l, float* smf) {
 
 // Fused double-float update + residual of the finest level: items of one tile and
 // DFZC planes, each with its own partial sum of r^2 (summed per problem in order).
-__device__ __forceinline__ void fused_df(const BDesc& B, float* smf, double* sh) {
+__device__ __forceinline__ void fused_df(const BDesc& B, float* smf, double* sh, bool first) {
   for (int it = blockIdx.x; it < B.dftot; it += gridDim.x) {
     int p = 0;
     while (B.dfoff[p + 1] <= it) ++p;
@@ -252,11 +259,17 @@ __device__ __forceinline__ void fused_df(const BDesc& B, float* smf, double* sh)
     const float2 m1 = f64_to_df(B.sc[p * P_N + P_MEAN]);
     float r2 = 0.f, f2 = 0.f;
     PAcc ps{bcast(0.f), bcast(0.f)};
-    dfk::df_segment<BDf>(d, cur ? P.phi2 : P.phi, final_e(P, 0), P.F, DF2{bcast(m1.x), bcast(m1.y)},
-                         cur ? P.phi : P.phi2, P.r[0], (tile % tiles_x) * BDf::TX, (tile / tiles_x) * BDf::TY,
-                         zc * DFZC, min(zc * DFZC + DFZC, d.nz), smf, r2, ps, f2);
+    // first: the residual of the initial iterate (no update, phi not written)
+    dfk::df_segment<BDf>(d, cur ? P.phi2 : P.phi, first ? nullptr : final_e(P, 0), P.F,
+                         DF2{bcast(m1.x), bcast(m1.y)}, first ? nullptr : (cur ? P.phi : P.phi2), P.r[0],
+                         (tile % tiles_x) * BDf::TX, (tile / tiles_x) * BDf::TY, zc * DFZC,
+                         min(zc * DFZC + DFZC, d.nz), smf, r2, ps, f2);
     const double s = block_sum_f(r2, sh);
     if (threadIdx.x == 0) B.dfpart[it] = s;
+    if (first) {
+      const double sf = block_sum_f(f2, sh);
+      if (threadIdx.x == 0) B.dfpart2[it] = sf;
+    }
   }
 }
 
@@ -329,12 +342,21 @@ __global__ void __launch_bounds__(BT, 1) k_batched_solve(BDesc B) {
       if (B.status[pi] != ST_ACTIVE) continue;
       const BProb& P = B.p[pi];
       double* s = B.sc + pi * P_N;
-      if (first) s[P_F2] = chunk_total(B, P, B.part1);
+      const bool fz = V > 0 && P.dffused;
+      if (first) {
+        if (fz) {
+          double f2 = 0.0;
+          for (int k = B.dfoff[pi]; k < B.dfoff[pi + 1]; ++k) f2 += B.dfpart2[k];
+          s[P_F2] = f2;
+        } else {
+          s[P_F2] = chunk_total(B, P, B.part1);
+        }
+      }
       double r2;
-      if (!first && V > 0 && P.dffused) {
+      if (fz) {
         r2 = 0.0;
         for (int k = B.dfoff[pi]; k < B.dfoff[pi + 1]; ++k) r2 += B.dfpart[k];
-        B.phicur[pi] ^= 1;  // the fused update wrote the other buffer
+        if (!first) B.phicur[pi] ^= 1;  // the fused update wrote the other buffer
       } else {
         r2 = chunk_total(B, P, B.part0);
       }
@@ -362,7 +384,8 @@ __global__ void __launch_bounds__(BT, 1) k_batched_solve(BDesc B) {
       }
     }
   };
-  df_residual_phase(true, true);
+  if constexpr (V > 0) fused_df(B, smf, sh, true);
+  df_residual_phase(true, V == 0);
   grid.sync();
   finalize(true);
   grid.sync();
@@ -380,8 +403,9 @@ __global__ void __launch_bounds__(BT, 1) k_batched_solve(BDesc B) {
       // per-operation levels (smaller than 16^3, or every level for V = 0)
       auto smoothed = [&](const BProb& P, int lv) { return lv < P.L - 1 && !(V > 0 && lv_fused(P, lv)); };
       if constexpr (V > 0) fused_down<V>(B, l, smf);
+      const bool perop = V == 0 || (B.perop >> l & 1u);
       bool cur_a = true;  // current e in ea
-      for (int k = 0; k < Vd; ++k) {
+      for (int k = 0; perop && k < Vd; ++k) {
         const bool from_zero = k == 0;
         const float c1 = B.c1[k];
         const float a = B.ca[l][k], b = B.cb[l][k];
@@ -405,6 +429,7 @@ __global__ void __launch_bounds__(BT, 1) k_batched_solve(BDesc B) {
       }
       // residual, then full weighting to the next level
       const float ih2 = B.ih2[l];
+      if (perop) {
       phase(B, l, smoothed, [&](const BProb& P, int lv, long long i) {
         const Dims d = P.d[lv];
         const float* e = cur_a ? P.ea[lv] : P.eb[lv];
@@ -438,9 +463,10 @@ __global__ void __launch_bounds__(BT, 1) k_batched_solve(BDesc B) {
               }
               P.r[lv][I] = fw3(yv[0], yv[1], yv[2]);
             });
+      }
       grid.sync();
       // coarsest solves of the problems whose hierarchy ends at level l + 1
-      {
+      if (B.coarse >> (l + 1) & 1u) {
         const int warps = blockDim.x / 32, lane = threadIdx.x & 31;
         for (int pi = blockIdx.x; pi < B.count; pi += gridDim.x) {
           const BProb& P = B.p[pi];
@@ -455,8 +481,8 @@ __global__ void __launch_bounds__(BT, 1) k_batched_solve(BDesc B) {
             if (lane == 0) e[row] = acc;
           }
         }
+        grid.sync();
       }
-      grid.sync();
     }
     // up: levels maxL-2 .. 0.  Per operation: pre-smoothing from zero leaves e in eb
     // when V is odd and in ea when V is even; V more steps then always end in ea,
@@ -465,16 +491,18 @@ __global__ void __launch_bounds__(BT, 1) k_batched_solve(BDesc B) {
     for (int l = B.maxL - 2; l >= 0; --l) {
       auto smoothed = [&](const BProb& P, int lv) { return lv < P.L - 1 && !(V > 0 && lv_fused(P, lv)); };
       if constexpr (V > 0) fused_up<V>(B, l, smf);
+      const bool perop = V == 0 || (B.perop >> l & 1u);
       bool cur_a = (Vd % 2) == 0;
-      phase(B, l, smoothed, [&](const BProb& P, int lv, long long i) {
-        const Dims d = P.d[lv];
-        int x, y, z;
-        cell_xyz(d, i, x, y, z);
-        float* e = cur_a ? P.ea[lv] : P.eb[lv];
-        e[i] = t_add(e[i], prolong_value(final_e(P, lv + 1), P.d[lv + 1], x, y, z));
-      });
+      if (perop)
+        phase(B, l, smoothed, [&](const BProb& P, int lv, long long i) {
+          const Dims d = P.d[lv];
+          int x, y, z;
+          cell_xyz(d, i, x, y, z);
+          float* e = cur_a ? P.ea[lv] : P.eb[lv];
+          e[i] = t_add(e[i], prolong_value(final_e(P, lv + 1), P.d[lv + 1], x, y, z));
+        });
       grid.sync();
-      for (int k = 0; k < Vd; ++k) {
+      for (int k = 0; perop && k < Vd; ++k) {
         const float c1 = B.c1[k];
         const float a = B.ca[l][k], b = B.cb[l][k];
         phase(B, l, smoothed, [&](const BProb& P, int lv, long long i) {
@@ -493,7 +521,7 @@ __global__ void __launch_bounds__(BT, 1) k_batched_solve(BDesc B) {
       }
     }
     // phi += e, next residual, convergence
-    if constexpr (V > 0) fused_df(B, smf, sh);
+    if constexpr (V > 0) fused_df(B, smf, sh, false);
     phase(B, 0, [&](const BProb& P, int) { return !(V > 0 && P.dffused); },
           [&](const BProb& P, int, long long i) { P.phi[i] = df_add_f(P.phi[i], final_e(P, 0)[i]); });
     grid.sync();
@@ -777,7 +805,6 @@ extern "C" gbmg_status mg_batch_create(gbmg_batch** out, gbmg_ctx* const* ctxs, 
   // the double-float phase, second phi buffers, per-level Chebyshev constants
   const int V = (D.degree >= 1 && D.degree <= 4) ? D.degree : 0;
   pick_kernel(D.degree, b->kern, b->smem);
-  const int DTY = V >= 4 ? 24 : 32;
   std::vector<long long> doff((size_t)maxL * (count + 1), 0), uoff((size_t)maxL * (count + 1), 0);
   std::vector<int> dfoff(count + 1, 0);
   long long phi2_cells = 0;
@@ -790,6 +817,9 @@ extern "C" gbmg_status mg_batch_create(gbmg_batch** out, gbmg_ctx* const* ctxs, 
     }
     P.dffused = V > 0 && c->lv[0].d.nx % 2 == 0;
     if (P.dffused) phi2_cells += ncell(c->lv[0].d);
+    for (int l = 0; l + 1 < c->L; ++l)
+      if (!(P.fmask >> l & 1u)) D.perop |= 1u << l;
+    D.coarse |= 1u << (c->L - 1);
   }
   for (int l = 0; l < maxL; ++l)
     for (int i = 0; i < count; ++i) {
@@ -797,8 +827,8 @@ extern "C" gbmg_status mg_batch_create(gbmg_batch** out, gbmg_ctx* const* ctxs, 
       long long dn = 0, un = 0;
       if (b->hprob[i].fmask >> l & 1u) {
         const Dims d = c->lv[l].d;
-        dn = (long long)ceil_div(d.nx, 64) * ceil_div(d.ny, DTY) * d.nz;
-        un = (long long)ceil_div(d.nx, 64) * ceil_div(d.ny, 32) * d.nz;
+        dn = (long long)ceil_div(d.nx, 64) * ceil_div(d.ny, down_ty(V)) * d.nz;
+        un = (long long)ceil_div(d.nx, 64) * ceil_div(d.ny, up_ty(V)) * d.nz;
       }
       doff[(size_t)l * (count + 1) + i + 1] = doff[(size_t)l * (count + 1) + i] + dn;
       uoff[(size_t)l * (count + 1) + i + 1] = uoff[(size_t)l * (count + 1) + i] + un;
@@ -830,6 +860,7 @@ extern "C" gbmg_status mg_batch_create(gbmg_batch** out, gbmg_ctx* const* ctxs, 
     const size_t oDoff = take2(sizeof(long long) * doff.size()), oUoff = take2(sizeof(long long) * uoff.size());
     const size_t oDf = take2(sizeof(int) * dfoff.size());
     const size_t oDfp = take2(sizeof(double) * (size_t)std::max(dfoff[count], 1));
+    const size_t oDfp2 = take2(sizeof(double) * (size_t)std::max(dfoff[count], 1));
     const size_t oCur = take2(sizeof(int) * count), oCoef = take2(sizeof(legs::Coef) * maxL);
     e = cudaMalloc((void**)&b->mem2, off2);
     if (e == cudaSuccess) e = cudaMemcpy(b->mem2 + oDoff, doff.data(), sizeof(long long) * doff.size(), cudaMemcpyHostToDevice);
@@ -855,6 +886,7 @@ extern "C" gbmg_status mg_batch_create(gbmg_batch** out, gbmg_ctx* const* ctxs, 
     D.dfoff = reinterpret_cast<const int*>(b->mem2 + oDf);
     D.dftot = dfoff[count];
     D.dfpart = reinterpret_cast<double*>(b->mem2 + oDfp);
+    D.dfpart2 = reinterpret_cast<double*>(b->mem2 + oDfp2);
     D.phicur = reinterpret_cast<int*>(b->mem2 + oCur);
     D.coef = reinterpret_cast<const legs::Coef*>(b->mem2 + oCoef);
   }
