@@ -42,13 +42,14 @@ constexpr int BT = 384;          // block size (the fused legs' thread-column la
 constexpr int DFZC = 16;         // z planes per item of the fused double-float phase
 
 // tiles of the fused device code at BT threads
-// (columns of 4 pairs for the down leg, of 3 pairs for the up leg: at the register
-// limit of BT threads per SM, 4-pair columns spill in the up leg)
-constexpr int down_ty(int v) { return v >= 4 ? 24 : 32; }
+// (columns of 3 pairs for both legs: this kernel holds the state of every phase under
+// one register limit of BT threads per SM, and 4-pair columns spill there, which the
+// separate leg kernels do not)
+constexpr int down_ty(int v) { return v >= 4 ? 20 : 22; }
 constexpr int up_ty(int v) { return v >= 4 ? 20 : 24; }
 template <int V>
 struct BDown {
-  using T = legs::PTile<64, down_ty(V), V + 1, BT, 4>;
+  using T = legs::PTile<64, down_ty(V), V + 1, BT, 3>;
 };
 template <int V>
 struct BUp {
