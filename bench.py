@@ -58,6 +58,7 @@ def parse():
     p.add_argument("--only", choices=["moving_mesh", "differentiable", "batched", "fixed_2_cycles", "predictors",
                                       "pm_force"],
                    help="run one extra workload alone and print its JSON object (no headline line)")
+    p.add_argument("--no-autotune", action="store_true", help="batched leg: default grid and tiles")
     p.add_argument("--print-source-digests", action="store_true",
                    help="print the source digest of each profiled kernel family and exit")
     return p.parse_args()
@@ -703,7 +704,10 @@ def batched_leg(args):
     F = [torch.from_numpy(grf(s, 1000 + i)).cuda() for i, s in enumerate(shapes)]
     phis = [torch.zeros_like(f) for f in F]
     batch = gb.Batch(shapes, degree=args.degree)
-    blocks, tiles = batch.autotune(F, phis, tol=args.tol, max_vcycles=args.max_vcycles)
+    if args.no_autotune:   # default grid (one CTA per SM) and tiles: fixed launches for profiling
+        blocks, tiles = "default", batch.tiles()
+    else:
+        blocks, tiles = batch.autotune(F, phis, tol=args.tol, max_vcycles=args.max_vcycles)
     batch.use_graph(True)
     for p in phis:
         p.zero_()
