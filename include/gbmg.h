@@ -144,11 +144,31 @@ gbmg_status mg_solve_adjoint(gbmg_ctx* ctx, const double* phi_bar_dev, double* s
                              double* psi_bar_dev, const double* phi_dev, const double* source_dev,
                              double tol, int max_vcycles, gbmg_stats* stats);
 
-/* Same solve with host buffers: copies F and the initial phi to the device, solves,
- * copies phi back and waits.  Staging buffers are allocated on the first call and
- * kept until mg_destroy. */
+/* Same solve with host buffers (nx*ny*nz doubles each, phi overwritten), waits for the
+ * stream.  Mixed precision with page-locked buffers (cudaHostAlloc, cudaHostRegister):
+ * the conversion kernels read F and the initial phi from host memory and write the
+ * result there, over the host link, with no staging copy.  Otherwise F and phi are
+ * copied to device staging buffers (allocated on the first such call, kept until
+ * mg_destroy), solved there and phi copied back.  Results are identical either way. */
 gbmg_status mg_solve_host(gbmg_ctx* ctx, const double* source_host, double* phi_inout_host,
                           double tol, int max_vcycles, gbmg_stats* stats);
+
+/* A warm-started sequence of solves with host buffers (the time-stepping use of Sec. 3.2:
+ * each solve starts from the previous solution, "recycling"):
+ *   solve t = 0 .. count-1 of A phi_t = F_t - mean(F_t), initial guess phi_{t-1}
+ *   (phi0_host for t = 0, or zero when phi0_host is NULL); phi_host[t] receives phi_t.
+ * sources_host[t], phi_host[t], phi0_host: nx*ny*nz doubles each, page-locked for the
+ * copies to run asynchronously (pageable memory works, with synchronous copies).  The
+ * copy of F_{t+1} to the device and of phi_{t-1} back run on two copy streams of the
+ * context while solve t runs on its stream; the iterate stays on the device between
+ * solves.  Each solve equals mg_solve on the same data (results identical).
+ * stats: NULL or count entries.  Returns GBMG_OK when every solve converged, else the
+ * first non-converged status (the sequence still runs to the end); argument, state and
+ * CUDA errors stop it.  Allocates two sources and two potentials on the device on the
+ * first call (kept until mg_destroy).  Waits for all of it before returning. */
+gbmg_status mg_solve_host_sequence(gbmg_ctx* ctx, int count, const double* const* sources_host,
+                                   double* const* phi_host, const double* phi0_host, double tol,
+                                   int max_vcycles, gbmg_stats* stats);
 
 /* Warm-start predictor (Sec. 3.2 "Predictors"): the initial guess of the next solve from
  * earlier solutions of this context's mesh, FP64, nx*ny*nz values each.

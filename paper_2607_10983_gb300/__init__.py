@@ -77,6 +77,8 @@ _SIGS = {
     "mg_set_stream": (_S, [_P, _P]),
     "mg_solve": (_S, [_P, _P, _P, _P, _D, _I, ctypes.POINTER(_Stats)]),
     "mg_solve_host": (_S, [_P, _P, _P, _D, _I, ctypes.POINTER(_Stats)]),
+    "mg_solve_host_sequence": (_S, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_P), _P, _D, _I,
+                                    ctypes.POINTER(_Stats)]),
     "mg_last_stats": (_S, [_P, ctypes.POINTER(_Stats)]),
     "mg_num_levels": (_I, [_P]),
     "mg_level_dims": (_S, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
@@ -356,6 +358,31 @@ class Solver:
                                 ctypes.byref(st))
         _check(s, allow_convergence=True)
         return phi, Stats.from_c(st)
+
+    def solve_host_sequence(self, sources, phis, phi0=None, tol: float = 1e-6, max_vcycles: int = 50):
+        """Warm-started sequence on host float64 arrays: phis[t] receives the solution for
+        sources[t], each solve starting from the previous one (phi0, or zero, for the first).
+        Copies overlap the neighbouring solves; page-locked buffers (pinned tensors) make
+        them asynchronous.  Returns the per-solve Stats."""
+        import numpy as np
+
+        def host(a):
+            a = a.numpy() if isinstance(a, torch.Tensor) else a
+            if a.dtype != np.float64 or not a.flags.c_contiguous or tuple(a.shape) != self.shape:
+                raise ValueError("expected C-contiguous float64 arrays of the solver's shape")
+            return a
+        if len(sources) != len(phis):
+            raise ValueError("sources and phis differ in length")
+        src = [host(a) for a in sources]
+        out = [host(a) for a in phis]
+        count = len(src)
+        sp = (_P * max(count, 1))(*[a.ctypes.data for a in src])
+        op = (_P * max(count, 1))(*[a.ctypes.data for a in out])
+        p0 = host(phi0).ctypes.data if phi0 is not None else None
+        st = (_Stats * max(count, 1))()
+        s = lib().mg_solve_host_sequence(self._c(), count, sp, op, p0, float(tol), int(max_vcycles), st)
+        _check(s, allow_convergence=True)
+        return [Stats.from_c(st[t]) for t in range(count)]
 
     # -- measurement
     def profile_begin(self, families):

@@ -179,6 +179,13 @@ __global__ void k_shift(long long n, const T* __restrict__ x, const double* __re
     out[i] = t_sub(x[i], s);
 }
 
+// A few device scalars into page-locked host memory through its device address (no copy
+// engine: the scalars do not queue behind large copies of other streams).
+__global__ void k_scalars_to_host(const double* __restrict__ src, double* __restrict__ dst, int n) {
+  if ((int)threadIdx.x < n) dst[threadIdx.x] = src[threadIdx.x];
+  __threadfence_system();
+}
+
 __global__ void k_finalize(const double* __restrict__ p, long long count, double* __restrict__ out, double scale) {
   __shared__ double sh[32];
   double s = 0.0;
@@ -333,6 +340,13 @@ cudaError_t launch_shift(cudaStream_t st, long long n, const T* x, const double*
 
 cudaError_t launch_finalize(cudaStream_t st, const double* p, long long count, double* out, double scale) {
   k_finalize<<<1, 1024, 0, st>>>(p, count, out, scale);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scalars_to_host(cudaStream_t st, const double* src, double* dst_mapped, int n) {
+  if (n < 0 || n > 32) return cudaErrorInvalidValue;
+  k_scalars_to_host<<<1, 32, 0, st>>>(src, dst_mapped, n);
   note_launch();
   return cudaGetLastError();
 }

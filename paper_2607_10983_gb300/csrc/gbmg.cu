@@ -155,6 +155,13 @@ using namespace gbmg;
 gbmg_ctx::~gbmg_ctx() {
   for (auto& v : prof_ev)
     for (cudaEvent_t e : v) cudaEventDestroy(e);
+  for (cudaStream_t s : {seq_h2d, seq_d2h})
+    if (s) {
+      cudaStreamSynchronize(s);
+      cudaStreamDestroy(s);
+    }
+  for (cudaEvent_t e : seq_ev)
+    if (e) cudaEventDestroy(e);
   if (arena) cudaFree(arena);
   if (host_scal) cudaFreeHost(host_scal);
   for (void* p : owned) cudaFree(p);
@@ -290,6 +297,7 @@ extern "C" gbmg_status mg_setup(gbmg_ctx** out, int nx, int ny, int nz, int leve
     return cuda_fail(e, "mg_setup: workspace allocation");
   }
   e = cudaMallocHost((void**)&c->host_scal, 64 * sizeof(double));
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&c->host_scal_dev, c->host_scal, 0);
   if (e != cudaSuccess) {
     delete c;
     return cuda_fail(e, "mg_setup: pinned allocation");

@@ -46,6 +46,8 @@ cudaError_t launch_shift(cudaStream_t st, long long n, const T* x, const double*
 
 // out[0] = scale * (sum of `count` partials), summed in a fixed order (one block).
 cudaError_t launch_finalize(cudaStream_t st, const double* partials, long long count, double* out, double scale);
+// n <= 32 doubles from device memory into page-locked host memory (its device address)
+cudaError_t launch_scalars_to_host(cudaStream_t st, const double* src, double* dst_mapped, int n);
 
 // ---- double-float path (finest level, h = 1) ----
 cudaError_t launch_f64_to_df(cudaStream_t st, long long n, const double* x, float2* out,

@@ -198,7 +198,8 @@ gbmg_status solve_fp64(gbmg_ctx* c, const double* F, double* phi, double tol, in
   return GBMG_OK;
 }
 
-gbmg_status solve_mixed(gbmg_ctx* c, const double* F, double* phi, double tol, int maxv, gbmg_stats& st) {
+gbmg_status solve_mixed(gbmg_ctx* c, const double* F, const double* phi, double* phi_out, double tol, int maxv,
+                        gbmg_stats& st) {
   const Level& L0 = c->lv[0];
   const long long n = ncell(L0.d);
   double* part = c->partials;
@@ -269,7 +270,7 @@ gbmg_status solve_mixed(gbmg_ctx* c, const double* F, double* phi, double tol, i
     TRY(launch_df_update(c->stream, n, phi_cur, nullptr, part2));
     TRY(launch_finalize(c->stream, part2, pr, sc + S_MEAN_PHI, 1.0 / (double)n));
   }
-  TRY(launch_df_to_f64(c->stream, n, phi_cur, sc + S_MEAN_PHI, phi));
+  TRY(launch_df_to_f64(c->stream, n, phi_cur, sc + S_MEAN_PHI, phi_out));
   return GBMG_OK;
 }
 
@@ -292,6 +293,21 @@ gbmg_status comp_scratch(gbmg_ctx* c, int dtype, void** out) {
   return GBMG_OK;
 }
 
+// One solve on the context's stream, without waiting for it: phi_in is the initial
+// guess, phi_out receives the result (the same buffer for the in-place mg_solve).
+gbmg_status solve_core(gbmg_ctx* c, const double* F, const double* phi_in, double* phi_out, double tol, int maxv,
+                       gbmg_stats& st) {
+  std::memset(&st, 0, sizeof(st));
+  if (c->o.op == GBMG_OP_FLAT7 && c->o.prec != GBMG_FP64) return solve_mixed(c, F, phi_in, phi_out, tol, maxv, st);
+  if (c->o.op == GBMG_OP_CURV19 && !c->geom_ready)
+    return fail(GBMG_ERR_STATE, "mg_solve: curvilinear solve before mg_set_geometry");
+  // the FP64 and curvilinear solves iterate in place
+  if (phi_out != phi_in)
+    TRY(cudaMemcpyAsync(phi_out, phi_in, (size_t)ncell(c->lv[0].d) * sizeof(double), cudaMemcpyDeviceToDevice,
+                        c->stream));
+  return c->o.op == GBMG_OP_CURV19 ? curv_solve(c, F, phi_out, tol, maxv, st) : solve_fp64(c, F, phi_out, tol, maxv, st);
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ solve
@@ -305,19 +321,11 @@ extern "C" gbmg_status mg_solve(gbmg_ctx* ctx, const double* source_dev, const d
   if (!(tol >= 0.0)) return fail(GBMG_ERR_INVALID_ARG, "mg_solve: tol must be >= 0");
   DeviceGuard g(ctx->device);
   gbmg_stats st;
-  std::memset(&st, 0, sizeof(st));
-  gbmg_status s;
-  if (ctx->o.op == GBMG_OP_CURV19) {
-    if (coeffs_dev) {
-      s = mg_set_geometry(ctx, coeffs_dev);
-      if (s != GBMG_OK) return s;
-    }
-    if (!ctx->geom_ready) return fail(GBMG_ERR_STATE, "mg_solve: curvilinear solve before mg_set_geometry");
-    s = curv_solve(ctx, source_dev, phi_inout_dev, tol, max_vcycles, st);
-  } else {
-    s = ctx->o.prec == GBMG_FP64 ? solve_fp64(ctx, source_dev, phi_inout_dev, tol, max_vcycles, st)
-                                 : solve_mixed(ctx, source_dev, phi_inout_dev, tol, max_vcycles, st);
+  if (ctx->o.op == GBMG_OP_CURV19 && coeffs_dev) {
+    gbmg_status s = mg_set_geometry(ctx, coeffs_dev);
+    if (s != GBMG_OK) return s;
   }
+  gbmg_status s = solve_core(ctx, source_dev, phi_inout_dev, phi_inout_dev, tol, max_vcycles, st);
   if (s != GBMG_OK) return s;
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(e, "mg_solve");
@@ -332,11 +340,30 @@ extern "C" gbmg_status mg_solve(gbmg_ctx* ctx, const double* source_dev, const d
   return (gbmg_status)st.status;
 }
 
+// The device address of a page-locked host buffer (cudaHostAlloc, cudaHostRegister,
+// a pinned torch tensor), or NULL for memory the device cannot address.
+static void* device_view(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 extern "C" gbmg_status mg_solve_host(gbmg_ctx* ctx, const double* source_host, double* phi_inout_host, double tol,
                                      int max_vcycles, gbmg_stats* stats) {
   g_last_error.clear();
   if (!ctx || !source_host || !phi_inout_host) return fail(GBMG_ERR_INVALID_ARG, "mg_solve_host: NULL argument");
   DeviceGuard g(ctx->device);
+  // Mixed precision touches the FP64 source and phi only in the conversions to and from
+  // double-float: with page-locked buffers those kernels read and write host memory
+  // over the host link themselves, and no staging copy is made.
+  if (ctx->o.prec == GBMG_MIXED) {
+    void* Fv = device_view(source_host);
+    void* Pv = device_view(phi_inout_host);
+    if (Fv && Pv) return mg_solve(ctx, (const double*)Fv, nullptr, (double*)Pv, tol, max_vcycles, stats);
+  }
   const size_t bytes = (size_t)ncell(ctx->lv[0].d) * sizeof(double);
   if (!ctx->stage_F) {
     TRY(cudaMalloc((void**)&ctx->stage_F, bytes));
@@ -351,6 +378,94 @@ extern "C" gbmg_status mg_solve_host(gbmg_ctx* ctx, const double* source_host, d
   TRY(cudaMemcpyAsync(phi_inout_host, ctx->stage_phi, bytes, cudaMemcpyDeviceToHost, ctx->stream));
   TRY(cudaStreamSynchronize(ctx->stream));
   return s;
+}
+
+// Lazily created copy streams, events and device buffers of mg_solve_host_sequence.
+static gbmg_status seq_resources(gbmg_ctx* c) {
+  const size_t bytes = (size_t)ncell(c->lv[0].d) * sizeof(double);
+  for (int k = 0; k < 2; ++k) {
+    if (!c->seq_F[k]) {
+      TRY(cudaMalloc((void**)&c->seq_F[k], bytes));
+      c->owned.push_back(c->seq_F[k]);
+    }
+    if (!c->seq_phi[k]) {
+      TRY(cudaMalloc((void**)&c->seq_phi[k], bytes));
+      c->owned.push_back(c->seq_phi[k]);
+    }
+  }
+  for (cudaEvent_t& e : c->seq_ev)
+    if (!e) TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  if (!c->seq_d2h) TRY(cudaStreamCreateWithFlags(&c->seq_d2h, cudaStreamNonBlocking));
+  if (!c->seq_h2d) TRY(cudaStreamCreateWithFlags(&c->seq_h2d, cudaStreamNonBlocking));
+  return GBMG_OK;
+}
+
+extern "C" gbmg_status mg_solve_host_sequence(gbmg_ctx* ctx, int count, const double* const* sources_host,
+                                              double* const* phi_host, const double* phi0_host, double tol,
+                                              int max_vcycles, gbmg_stats* stats) {
+  g_last_error.clear();
+  if (!ctx || count < 0 || (count > 0 && (!sources_host || !phi_host)))
+    return fail(GBMG_ERR_INVALID_ARG, "mg_solve_host_sequence: bad argument");
+  for (int t = 0; t < count; ++t)
+    if (!sources_host[t] || !phi_host[t]) return fail(GBMG_ERR_INVALID_ARG, "mg_solve_host_sequence: NULL buffer");
+  if (!(tol >= 0.0)) return fail(GBMG_ERR_INVALID_ARG, "mg_solve_host_sequence: tol must be >= 0");
+  if (count == 0) return GBMG_OK;
+  if (ctx->o.op == GBMG_OP_CURV19 && !ctx->geom_ready)
+    return fail(GBMG_ERR_STATE, "mg_solve_host_sequence: curvilinear solve before mg_set_geometry");
+  DeviceGuard g(ctx->device);
+  TRYS(seq_resources(ctx));
+  const size_t bytes = (size_t)ncell(ctx->lv[0].d) * sizeof(double);
+  // events: 0,1 source k landed; 2,3 source buffer k read by its solve; 4,5 phi buffer
+  // k copied out; 6 solve done
+  cudaEvent_t* ev = ctx->seq_ev;
+  cudaStream_t cs = ctx->stream, h2d = ctx->seq_h2d, d2h = ctx->seq_d2h;
+  // the compute stream's earlier work (and whatever wrote the host buffers' device
+  // views) comes first
+  TRY(cudaEventRecord(ev[6], cs));
+  TRY(cudaStreamWaitEvent(h2d, ev[6], 0));
+  TRY(cudaStreamWaitEvent(d2h, ev[6], 0));
+  TRY(cudaMemcpyAsync(ctx->seq_F[0], sources_host[0], bytes, cudaMemcpyHostToDevice, h2d));
+  TRY(cudaEventRecord(ev[0], h2d));
+  if (phi0_host) {
+    TRY(cudaMemcpyAsync(ctx->seq_phi[0], phi0_host, bytes, cudaMemcpyHostToDevice, h2d));
+    TRY(cudaEventRecord(ev[0], h2d));
+  } else {
+    TRY(cudaMemsetAsync(ctx->seq_phi[0], 0, bytes, cs));
+  }
+  gbmg_status worst = GBMG_OK;
+  for (int t = 0; t < count; ++t) {
+    const int k = t & 1, o = k ^ 1;
+    // prefetch the next source into the other buffer once the solve that read it is done
+    if (t + 1 < count) {
+      if (t >= 1) TRY(cudaStreamWaitEvent(h2d, ev[2 + o], 0));
+      TRY(cudaMemcpyAsync(ctx->seq_F[o], sources_host[t + 1], bytes, cudaMemcpyHostToDevice, h2d));
+      TRY(cudaEventRecord(ev[o], h2d));
+    }
+    // solve t: source k, initial guess phi k (phi_{t-1}), result into phi o, whose
+    // previous content (phi_{t-2}) must have been copied out
+    TRY(cudaStreamWaitEvent(cs, ev[k], 0));
+    if (t >= 2) TRY(cudaStreamWaitEvent(cs, ev[4 + o], 0));
+    gbmg_stats st;
+    const gbmg_status s = solve_core(ctx, ctx->seq_F[k], ctx->seq_phi[k], ctx->seq_phi[o], tol, max_vcycles, st);
+    if (s != GBMG_OK) {
+      cudaStreamSynchronize(h2d);
+      cudaStreamSynchronize(d2h);
+      return s;
+    }
+    TRY(cudaEventRecord(ev[2 + k], cs));
+    TRY(cudaEventRecord(ev[6], cs));
+    TRY(cudaStreamWaitEvent(d2h, ev[6], 0));
+    TRY(cudaMemcpyAsync(phi_host[t], ctx->seq_phi[o], bytes, cudaMemcpyDeviceToHost, d2h));
+    TRY(cudaEventRecord(ev[4 + o], d2h));
+    ctx->last = st;
+    if (stats) stats[t] = st;
+    if (st.status != GBMG_OK && worst == GBMG_OK) worst = (gbmg_status)st.status;
+  }
+  TRY(cudaStreamSynchronize(ctx->seq_d2h));
+  TRY(cudaStreamSynchronize(ctx->seq_h2d));
+  TRY(cudaStreamSynchronize(cs));
+  if (worst != GBMG_OK) g_last_error = std::string("mg_solve_host_sequence: ") + mg_status_string(worst);
+  return worst;
 }
 
 // ------------------------------------------------------------------ components

@@ -77,6 +77,7 @@ struct gbmg_ctx {
   long long npart = 0;
   double* scal = nullptr;       // 64 device scalars (enum Scal)
   double* host_scal = nullptr;  // 64 pinned host scalars
+  double* host_scal_dev = nullptr;  // its device address (the device writes it directly)
   std::vector<double> cc1, cc2; // Chebyshev schedule
   gbmg_stats last{};
   std::vector<void*> owned;     // lazily allocated buffers (component scratch, staging)
@@ -86,6 +87,10 @@ struct gbmg_ctx {
   std::vector<cudaEvent_t> prof_ev[8];  // start/stop event pairs per family
   double* stage_F = nullptr;    // mg_solve_host device staging
   double* stage_phi = nullptr;
+  double* seq_F[2] = {nullptr, nullptr};    // mg_solve_host_sequence: sources in flight
+  double* seq_phi[2] = {nullptr, nullptr};  // and the iterate, ping-pong
+  cudaStream_t seq_h2d = nullptr, seq_d2h = nullptr;
+  cudaEvent_t seq_ev[7] = {};
   ~gbmg_ctx();
 };
 
@@ -138,7 +143,7 @@ struct ProfScope {
 
 // Reads ||F||^2 and ||r||^2 back and returns the relative residual.
 inline gbmg_status read_rel(gbmg_ctx* c, double& rel) {
-  TRY(cudaMemcpyAsync(c->host_scal, c->scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  TRY(launch_scalars_to_host(c->stream, c->scal, c->host_scal_dev, 8));
   TRY(cudaStreamSynchronize(c->stream));
   const double f2 = c->host_scal[S_F2], r2 = c->host_scal[S_R2];
   rel = f2 > 0.0 ? std::sqrt(r2 / f2) : std::sqrt(r2);

@@ -51,6 +51,7 @@ def test_status_strings_and_bad_arguments_without_gpu(libpath):
     assert b"must be >= 4" in L.mg_last_error()
     assert L.mg_setup(None, 8, 8, 8, 0, 3, None, None) == 1
     assert L.mg_solve(None, None, None, None, 1e-6, 10, None) == 1
+    assert L.mg_solve_host_sequence(None, 0, None, None, None, 1e-6, 10, None) == 1
 
 
 def test_python_binding_fails_loudly_without_library(monkeypatch, tmp_path):

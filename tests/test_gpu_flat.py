@@ -200,10 +200,85 @@ def test_host_buffer_solve_matches_device(gb):
     F = grf(n, 16)
     s = gb.Solver(n, prec="mixed")
     phi_d, st_d = s.solve(to_dev(F), tol=1e-8)
+    # pageable numpy buffers: staged through device copies
     phi_h = np.zeros_like(F)
     _, st_h = s.solve_host(F, phi_h, tol=1e-8)
     assert st_h.cycles == st_d.cycles
     np.testing.assert_array_equal(phi_h, phi_d.cpu().numpy())
+    # page-locked buffers, read and written in place by the conversion kernels, from a
+    # nonzero initial guess (the initial phi is read from host memory too)
+    phi0 = grf(n, 19)
+    phi_d2, st_d2 = s.solve(to_dev(F), to_dev(phi0), tol=1e-8)
+    Fp = torch.from_numpy(F.copy()).pin_memory()
+    phi_p = torch.from_numpy(phi0.copy()).pin_memory()
+    _, st_p = s.solve_host(Fp, phi_p, tol=1e-8)
+    assert st_p.cycles == st_d2.cycles
+    np.testing.assert_array_equal(phi_p.numpy(), phi_d2.cpu().numpy())
+    np.testing.assert_array_equal(Fp.numpy(), F)   # the source is not written
+    # FP64 precision with page-locked buffers takes the staged path
+    s64 = gb.Solver(n, prec="fp64")
+    phi_d3, st_d3 = s64.solve(to_dev(F), tol=1e-10)
+    phi_p3 = torch.zeros((n, n, n), dtype=torch.float64).pin_memory()
+    _, st_p3 = s64.solve_host(Fp, phi_p3, tol=1e-10)
+    assert st_p3.cycles == st_d3.cycles
+    np.testing.assert_array_equal(phi_p3.numpy(), phi_d3.cpu().numpy())
+
+
+def _device_chain(s, Fs, phi0, tol):
+    phi = to_dev(phi0) if phi0 is not None else torch.zeros((s.shape), dtype=torch.float64, device="cuda")
+    out, stats = [], []
+    for F in Fs:
+        phi = phi.clone()
+        phi, st = s.solve(to_dev(F), phi, tol=tol)
+        out.append(phi.cpu().numpy())
+        stats.append(st)
+    return out, stats
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_host_sequence_matches_chained_device_solves(gb, prec):
+    n, T = 32, 5
+    tol = 1e-8 if prec == "mixed" else 1e-10
+    rng = np.random.default_rng(3)
+    base = grf(n, 40)
+    Fs = [base + 0.05 * t * grf(n, 41) + 0.01 * rng.standard_normal(base.shape) for t in range(T)]
+    s = gb.Solver(n, prec=prec)
+    # page-locked buffers, zero start
+    ref, ref_st = _device_chain(s, Fs, None, tol)
+    src = [torch.from_numpy(F.copy()).pin_memory() for F in Fs]
+    outs = [torch.full((n, n, n), 7.0, dtype=torch.float64).pin_memory() for _ in Fs]
+    sts = s.solve_host_sequence(src, outs, tol=tol)
+    assert [st.cycles for st in sts] == [st.cycles for st in ref_st]
+    assert sts[1].cycles < sts[0].cycles          # warm start from the previous solution
+    for t in range(T):
+        np.testing.assert_array_equal(outs[t].numpy(), ref[t])
+        np.testing.assert_array_equal(src[t].numpy(), Fs[t])
+    # pageable buffers and an initial guess for the first solve
+    phi0 = grf(n, 42)
+    ref, ref_st = _device_chain(s, Fs[:3], phi0, tol)
+    outs = [np.empty((n, n, n)) for _ in range(3)]
+    sts = s.solve_host_sequence(Fs[:3], outs, phi0=phi0, tol=tol)
+    assert [st.cycles for st in sts] == [st.cycles for st in ref_st]
+    for t in range(3):
+        np.testing.assert_array_equal(outs[t], ref[t])
+    # one solve, then an empty sequence
+    ref, _ = _device_chain(s, Fs[:1], None, tol)
+    one = [np.empty((n, n, n))]
+    s.solve_host_sequence(Fs[:1], one, tol=tol)
+    np.testing.assert_array_equal(one[0], ref[0])
+    assert s.solve_host_sequence([], []) == []
+    with pytest.raises(ValueError):
+        s.solve_host_sequence(Fs[:2], one)
+
+
+def test_host_sequence_reports_nonconvergence(gb):
+    n = 16
+    s = gb.Solver(n, prec="mixed")
+    Fs = [grf(n, 60), grf(n, 61)]
+    outs = [np.empty((n, n, n)) for _ in Fs]
+    sts = s.solve_host_sequence(Fs, outs, tol=1e-30, max_vcycles=2)
+    assert [st.status for st in sts] == [4, 4] and [st.cycles for st in sts] == [2, 2]
+    assert np.isfinite(outs[1]).all()
 
 
 def test_error_statuses(gb):
