@@ -31,13 +31,21 @@ Readings taken where the paper is silent or ambiguous:
 * The adjoint is written in M-form: M phi~ = b, b = J (delta - <delta>_J),
   phi = phi~ - mean(phi~); M^T lambda = g with g the mean-free cotangent.
 * Coarsest level: exact least-squares minimum-norm solve (dense pseudo-inverse).
+* Symmetric variant (sym=True; not the paper's scheme, which is the literal one
+  above): the same face terms B^{aa}, and the cross terms a != b moved to the cell
+  edges, -sum_{a != b} E_a^T C_ab E_b with C_ab the mean of B^{ab} over the four cells
+  around the edge and E_a the a-difference averaged over the two b-positions of the
+  edge.  M = M^T exactly; for constant B both schemes have the same Fourier symbol.
 
 Parity pins (tests/test_oracle_curv.py): psi = 0 reduces to the 7-point
 operator; constant-B Fourier symbol; M 1 = 0 and 1^T M = 0; second-order
 consistency with the continuum divergence on smooth fields; dot-product test of
 the transpose; triad/determinant against closed forms and numpy.linalg;
 central finite differences of the full solve for the delta- and psi-gradients;
-dense pseudo-inverse solves at 8^3.
+dense pseudo-inverse solves at 8^3.  Symmetric variant: psi = 0 and constant-B
+symbol, dense M = M^T with its diagonal and a 19-point stencil, second-order
+consistency (and an O(h^2) gap to the literal scheme), the B-cotangent as the exact
+derivative of the bilinear form, dense pseudo-inverse solve and FD gradients.
 """
 from __future__ import annotations
 
@@ -162,29 +170,95 @@ def diag_M(B: np.ndarray, h: float = 1.0) -> np.ndarray:
     return d
 
 
+# ---------------------------------------------------------------- symmetric variant
+
+
+def edge_coeff(B: np.ndarray, a: int, b: int) -> np.ndarray:
+    """C_ab on the edge e + (e_a + e_b)/2 (array index e): mean of B^{ab} over its four cells."""
+    c = B[a, b]
+    return 0.25 * (c + at(c, a, 1) + at(c, b, 1) + at2(c, a, 1, b, 1))
+
+
+def edge_grad(u: np.ndarray, a: int, b: int, h: float) -> np.ndarray:
+    """E_a u on the ab-edges: the a-difference averaged over the edge's two b-positions."""
+    return 0.5 * ((at(u, a, 1) - u) + (at2(u, a, 1, b, 1) - at(u, b, 1))) / h
+
+
+def edge_grad_T(q: np.ndarray, a: int, b: int, h: float) -> np.ndarray:
+    """Transpose of edge_grad(., a, b): cells from ab-edge values."""
+    return 0.5 * ((at(q, a, -1) - q) + (at2(q, a, -1, b, -1) - at(q, b, -1))) / h
+
+
+def apply_M_sym(u: np.ndarray, B: np.ndarray, h: float = 1.0) -> np.ndarray:
+    """Symmetric variant: sum_a (face flux differences of B^{aa}) - sum_{a != b} E_a^T C_ab E_b u."""
+    out = np.zeros_like(u, dtype=np.float64)
+    for a in range(3):
+        Fa = face_coeff(B, a, a) * (at(u, a, 1) - u) / h
+        out += (Fa - at(Fa, a, -1)) / h
+        for b in range(3):
+            if b == a:
+                continue
+            lo, hi = min(a, b), max(a, b)           # the edge set of the unordered pair
+            C = edge_coeff(B, lo, hi)
+            out -= edge_grad_T(C * edge_grad(u, b, a, h), a, b, h)
+    return out
+
+
+def diag_M_sym(B: np.ndarray, h: float = 1.0) -> np.ndarray:
+    """Diagonal of apply_M_sym: the face part of diag_M plus, per pair a < b,
+    (1/2h^2)(-C(e) + C(e-a) + C(e-b) - C(e-a-b)) from the four edges around the cell."""
+    d = diag_M(B, h)
+    for a in range(3):
+        for b in range(a + 1, 3):
+            C = edge_coeff(B, a, b)
+            d += 0.5 * (-C + at(C, a, -1) + at(C, b, -1) - at2(C, a, -1, b, -1)) / (h * h)
+    return d
+
+
+def Bbar_from_operator_sym(lam: np.ndarray, phi: np.ndarray, h: float = 1.0) -> np.ndarray:
+    """Cotangent of B for <lam, M_sym(B) phi>: the face part as Bbar_from_operator's
+    b == a terms; per pair a < b, dC(e) = -[(E_a lam)(E_b phi) + (E_b lam)(E_a phi)](e),
+    spread as 1/4 onto the edge's four cells (all of it in Bbar[a, b], none in Bbar[b, a])."""
+    Bbar = np.zeros((3, 3) + phi.shape)
+    for a in range(3):
+        Lam = (lam - at(lam, a, 1)) / h
+        fbar = (at(phi, a, 1) - phi) / h * Lam
+        Bbar[a, a] += 0.5 * (fbar + at(fbar, a, -1))
+        for b in range(a + 1, 3):
+            cbar = -(edge_grad(lam, a, b, h) * edge_grad(phi, b, a, h)
+                     + edge_grad(lam, b, a, h) * edge_grad(phi, a, b, h))
+            Bbar[a, b] += 0.25 * (cbar + at(cbar, a, -1) + at(cbar, b, -1) + at2(cbar, a, -1, b, -1))
+    return Bbar
+
+
 # ---------------------------------------------------------------- hierarchy
 
 
 class Level:
-    def __init__(self, psi: np.ndarray, h: float):
+    def __init__(self, psi: np.ndarray, h: float, sym: bool = False):
         self.psi = psi
         self.h = h
+        self.sym = sym
         self.J, self.B = geometry(psi, h)
-        self.D = diag_M(self.B, h)          # diagonal of M (same for M^T)
+        # diagonal of M (same for M^T)
+        self.D = diag_M_sym(self.B, h) if sym else diag_M(self.B, h)
 
     def L(self, u, transpose=False):
         """L u = M u / J (forward) or M^T u / J (operator of the transposed solve)."""
-        Mu = apply_MT(u, self.B, self.h) if transpose else apply_M(u, self.B, self.h)
+        if self.sym:
+            Mu = apply_M_sym(u, self.B, self.h)
+        else:
+            Mu = apply_MT(u, self.B, self.h) if transpose else apply_M(u, self.B, self.h)
         return Mu / self.J
 
 
-def hierarchy(psi: np.ndarray, levels: int = 0) -> list[Level]:
+def hierarchy(psi: np.ndarray, levels: int = 0, sym: bool = False) -> list[Level]:
     """psi_{l+1} = R psi_l (full weighting), geometry rebuilt with h_l = 2^l (Appendix B, Sec. 4.3)."""
     shapes = flat.level_shapes(psi.shape, levels)
     out = []
     p = np.asarray(psi, dtype=np.float64)
     for l in range(len(shapes)):
-        out.append(Level(p, float(2 ** l)))
+        out.append(Level(p, float(2 ** l), sym))
         if l + 1 < len(shapes):
             p = flat.restrict_fw(p)
     return out
@@ -246,13 +320,13 @@ def weighted_projection(delta: np.ndarray, J: np.ndarray) -> np.ndarray:
 def solve(delta: np.ndarray, psi: np.ndarray, tol: float = 1e-10, max_cycles: int = 100,
           levels: int = 0, nu1: int = 2, nu2: int = 2, omega: float = 2.0 / 3.0,
           phi0: np.ndarray | None = None, fixed_cycles: int | None = None,
-          hier: list[Level] | None = None):
+          hier: list[Level] | None = None, sym: bool = False):
     """Curvilinear Poisson solve L_psi phi = f with f the volume-weighted projection of delta.
 
     V-cycles until ||f - L phi|| / ||f|| <= tol; the mean of phi is removed at
     the end (Sec. 4.3.2 gauge).  Returns (phi, history).
     """
-    hier = hierarchy(psi, levels) if hier is None else hier
+    hier = hierarchy(psi, levels, sym) if hier is None else hier
     f = weighted_projection(np.asarray(delta, dtype=np.float64), hier[0].J)
     phi = np.zeros_like(f) if phi0 is None else np.array(phi0, dtype=np.float64, copy=True)
     nf = float(np.linalg.norm(f))
@@ -347,7 +421,7 @@ def Abar_from_J(A: np.ndarray, Jbar: np.ndarray) -> np.ndarray:
 
 def solve_vjp(delta: np.ndarray, psi: np.ndarray, phi: np.ndarray, phi_bar: np.ndarray,
               tol: float = 1e-11, max_cycles: int = 200, levels: int = 0,
-              nu1: int = 2, nu2: int = 2, omega: float = 2.0 / 3.0):
+              nu1: int = 2, nu2: int = 2, omega: float = 2.0 / 3.0, sym: bool = False):
     """Gradients of <phi_bar, phi> for phi = solve(delta, psi): returns (delta_bar, psi_bar).
 
     M-form of Eq. (adj_rhs) and (adj_op): M phi~ = b with b = J (delta - <delta>_J)
@@ -359,7 +433,7 @@ def solve_vjp(delta: np.ndarray, psi: np.ndarray, phi: np.ndarray, phi_bar: np.n
     dependence on J and Bbar is the operator's dependence on B contracted with
     lam and phi.  `phi` is the converged forward solution.
     """
-    hier = hierarchy(psi, levels)
+    hier = hierarchy(psi, levels, sym)
     lev0 = hier[0]
     J = lev0.J
     g = phi_bar - phi_bar.mean()
@@ -370,7 +444,8 @@ def solve_vjp(delta: np.ndarray, psi: np.ndarray, phi: np.ndarray, phi_bar: np.n
     f = weighted_projection(delta, J)
     Jbar = f * (lam - lamJ)
     A = triad(psi, lev0.h)
-    Abar = Abar_from_J(A, Jbar) - Abar_from_B(A, Bbar_from_operator(lam, phi, lev0.h))
+    Bbar = Bbar_from_operator_sym(lam, phi, lev0.h) if sym else Bbar_from_operator(lam, phi, lev0.h)
+    Abar = Abar_from_J(A, Jbar) - Abar_from_B(A, Bbar)
     psi_bar = hessian_T(Abar, lev0.h)
     return delta_bar, psi_bar
 

@@ -214,3 +214,118 @@ def test_mesh_motion_equal_mass_per_cell_is_stationary():
     new, psidot = curv.mesh_motion_step(psi, rho, 2.0, 1.3, 0.5, passes=1)
     assert np.abs(psidot).max() < 1e-12
     np.testing.assert_allclose(new, psi - psi.mean(), rtol=0, atol=1e-12)
+
+
+# ---------------------------------------------------------------- symmetric variant
+
+
+def test_sym_psi_zero_and_constant_B_symbol():
+    # psi = 0: the 7-point operator; constant B: the same symbol as the literal scheme,
+    # -sum_a 4 B_aa sin^2(k_a/2) - 2 sum_{a<b} B_ab sin k_a sin k_b (edge differences of
+    # cos(k.x): E_a E_b products give sin k_a sin k_b)
+    rng = np.random.default_rng(20)
+    u = rng.standard_normal((8, 12, 16))
+    for h in (1.0, 2.0):
+        _, B = curv.geometry(np.zeros(u.shape), h)
+        np.testing.assert_allclose(curv.apply_M_sym(u, B, h), flat.apply_A(u, h), atol=1e-13)
+        np.testing.assert_allclose(curv.diag_M_sym(B, h), -6.0 / h ** 2, atol=1e-15)
+    shape = (8, 12, 16)
+    Bc = np.array([[1.3, 0.2, -0.15], [0.2, 0.9, 0.1], [-0.15, 0.1, 1.1]])
+    B = np.broadcast_to(Bc[:, :, None, None, None], (3, 3) + shape).copy()
+    z, y, x = coords(shape)
+    for n in [(1, 2, 1), (3, 1, 2), (8, 6, 4), (5, 5, 3)]:
+        k = (2 * np.pi * n[0] / shape[2], 2 * np.pi * n[1] / shape[1], 2 * np.pi * n[2] / shape[0])
+        u = np.cos(k[0] * x + k[1] * y + k[2] * z + 0.4)
+        sym = -sum(4 * Bc[a, a] * math.sin(k[a] / 2) ** 2 for a in range(3))
+        sym -= 2 * sum(Bc[a, b] * math.sin(k[a]) * math.sin(k[b]) for a in range(3) for b in range(a + 1, 3))
+        np.testing.assert_allclose(curv.apply_M_sym(u, B), sym * u, atol=1e-12)
+
+
+def test_sym_operator_is_symmetric_with_19_points():
+    lev = curv.Level(smoothed_grf((4, 6, 6), 21, 1.0, 0.4), 1.0, sym=True)
+    M = curv.dense_L(lev) * lev.J.ravel()[:, None]            # M = J L
+    np.testing.assert_allclose(M, M.T, atol=1e-14 * np.abs(M).max())
+    np.testing.assert_allclose(np.diag(M), curv.diag_M_sym(lev.B).ravel(), atol=1e-13)
+    np.testing.assert_allclose(M.sum(axis=0), 0.0, atol=1e-13)   # 1^T M = 0
+    np.testing.assert_allclose(M.sum(axis=1), 0.0, atol=1e-13)   # M 1 = 0
+    # the stencil: the centre, 6 face and 12 edge neighbours, no corners
+    shape = (4, 6, 6)
+    i = np.ravel_multi_index((1, 2, 3), shape)
+    nz = {tuple(int(v) for v in np.subtract(np.unravel_index(j, shape), (1, 2, 3)))
+          for j in np.nonzero(np.abs(M[i]) > 1e-15)[0]}
+    assert len(nz) == 19 and all(sum(abs(c) for c in o) <= 2 for o in nz)
+    # the literal scheme is not symmetric on the same geometry
+    Ml = curv.dense_L(curv.Level(lev.psi, 1.0)) * lev.J.ravel()[:, None]
+    assert np.abs(Ml - Ml.T).max() > 1e-4 * np.abs(Ml).max()
+
+
+def test_sym_second_order_consistency_and_agreement_with_literal():
+    sp = pytest.importorskip("sympy")
+    X, Y, Z, N = sp.symbols("X Y Z N")
+    w = 2 * sp.pi / N
+    Bs = {(0, 0): 1 + sp.Rational(3, 10) * sp.sin(w * X), (1, 1): 1 + sp.Rational(1, 5) * sp.cos(w * Y),
+          (2, 2): 1 + sp.Rational(1, 10) * sp.sin(w * (Z + X)), (0, 1): sp.Rational(1, 10) * sp.cos(w * (X + Y)),
+          (0, 2): sp.Rational(1, 20) * sp.sin(w * Z), (1, 2): sp.Rational(2, 25) * sp.cos(w * (Y - Z))}
+    for (a, b) in list(Bs):
+        Bs[(b, a)] = Bs[(a, b)]
+    us = sp.sin(w * X) * sp.cos(w * Y) + sp.Rational(1, 2) * sp.sin(w * (2 * Z + Y))
+    var = (X, Y, Z)
+    cont = sum(sp.diff(Bs[(a, b)] * sp.diff(us, var[b]), var[a]) for a in range(3) for b in range(3))
+    fB = {k: sp.lambdify((X, Y, Z, N), v, "numpy") for k, v in Bs.items()}
+    fu = sp.lambdify((X, Y, Z, N), us, "numpy")
+    fc = sp.lambdify((X, Y, Z, N), cont, "numpy")
+    errs, gaps = [], []
+    for n in (16, 32, 64):
+        z, y, x = coords((n, n, n))
+        B = np.empty((3, 3, n, n, n))
+        for a in range(3):
+            for b in range(3):
+                B[a, b] = fB[(a, b)](x, y, z, n) * np.ones_like(x)
+        u = fu(x, y, z, n)
+        num = curv.apply_M_sym(u, B)
+        ref = fc(x, y, z, n)
+        errs.append(np.abs(num - ref).max() / np.abs(ref).max())
+        gaps.append(np.abs(num - curv.apply_M(u, B)).max() / np.abs(ref).max())
+    assert errs[0] / errs[1] > 3.5 and errs[1] / errs[2] > 3.5, errs
+    assert gaps[0] / gaps[1] > 3.5 and gaps[1] / gaps[2] > 3.5, gaps   # the schemes differ at O(h^2)
+
+
+def test_sym_Bbar_is_the_derivative_of_the_bilinear_form():
+    # <lam, M_sym(B) phi> is linear in B: <Bbar, dB> = <lam, M_sym(dB) phi> exactly
+    shape = (6, 8, 10)
+    rng = np.random.default_rng(22)
+    lam, phi = rng.standard_normal(shape), rng.standard_normal(shape)
+    Bbar = curv.Bbar_from_operator_sym(lam, phi, 2.0)
+    for trial in range(3):
+        dB = rng.standard_normal((3, 3) + shape)
+        dB = 0.5 * (dB + dB.transpose(1, 0, 2, 3, 4))
+        lhs = float((Bbar * dB).sum())
+        rhs = float((lam * curv.apply_M_sym(phi, dB, 2.0)).sum())
+        assert abs(lhs - rhs) < 1e-12 * max(1.0, abs(rhs))
+
+
+def test_sym_solve_dense_pinv_and_vjp_central_differences():
+    n = 8
+    psi = smoothed_grf(n, 23, 1.5, 0.4)
+    delta = grf(n, 24)
+    kw = dict(tol=1e-13, max_cycles=300, sym=True)
+    phi, hist = curv.solve(delta, psi, **kw)
+    lev = curv.hierarchy(psi, sym=True)[0]
+    f = curv.weighted_projection(delta, lev.J)
+    ref = (np.linalg.pinv(curv.dense_L(lev), rcond=1e-10) @ f.ravel()).reshape(f.shape)
+    np.testing.assert_allclose(phi, ref - ref.mean(), atol=1e-10 * np.abs(ref).max())
+    rng = np.random.default_rng(25)
+    pbar = rng.standard_normal((n, n, n))
+    dbar, psibar = curv.solve_vjp(delta, psi, phi, pbar, **kw)
+
+    def loss(d, p):
+        return float((curv.solve(d, p, **kw)[0] * pbar).sum())
+
+    v = rng.standard_normal((n, n, n))
+    eps = 1e-4
+    fd = (loss(delta + eps * v, psi) - loss(delta - eps * v, psi)) / (2 * eps)
+    assert abs(fd - float((dbar * v).sum())) < 1e-6 * max(1.0, abs(fd))
+    wdir = smoothed_grf(n, 26, 1.5, 0.4)
+    eps = 1e-3
+    fd = (loss(delta, psi + eps * wdir) - loss(delta, psi - eps * wdir)) / (2 * eps)
+    assert abs(fd - float((psibar * wdir).sum())) < 1e-5 * max(1.0, abs(fd))
