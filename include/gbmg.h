@@ -78,6 +78,14 @@ typedef struct {
                  /* flat + GBMG_MIXED + Chebyshev): k steps of conjugate gradients      */
                  /* preconditioned by the V-cycle (Sec. 3.2) on the FP32 error equation */
                  /* of each step; stats count defect-correction steps                  */
+  int curv_sym;  /* GBMG_OP_CURV19 only.  0: the paper's scheme (Sec. 4.3.1): face fluxes */
+                 /* with the tangential derivatives averaged onto the face; not exactly   */
+                 /* symmetric for variable B, so adjoint solves use its exact transpose.  */
+                 /* 1: symmetric variant: the same B^aa face terms, the cross terms on   */
+                 /* the cell edges, -sum_{a!=b} E_a^T C_ab E_b with C_ab the mean of B^ab */
+                 /* over the edge's four cells and E_a the a-difference averaged over   */
+                 /* the edge's two b-positions; M = M^T, 19 points, the same Fourier     */
+                 /* symbol for constant B; forward and adjoint solves use M itself.     */
 } gbmg_opts;
 
 typedef struct {
@@ -348,14 +356,16 @@ gbmg_status mg_coarse_solve(gbmg_ctx* ctx, int dtype, const void* r_dev, void* e
 gbmg_status mg_vcycle(gbmg_ctx* ctx, const void* r_dev, void* e_dev);
 
 /* Curvilinear components (geometry must be set).  out = op(u) or op(u) / J on level
- * `level`, op = M (transpose 0) or its exact transpose M^T (transpose 1). */
+ * `level`, op = M (transpose 0) or its exact transpose M^T (transpose 1); with
+ * opts.curv_sym, op = S (the symmetric variant) for either value. */
 gbmg_status mg_curv_apply(gbmg_ctx* ctx, int level, int dtype, int transpose, int divide_by_J,
                           const void* u_dev, void* out_dev);
 /* Copy the geometry of a level: J (n floats) and B packed xx, yy, zz, xy, xz, yz (6 n
  * floats); either pointer may be NULL. */
 gbmg_status mg_curv_geometry(gbmg_ctx* ctx, int level, float* J_dev, float* B_dev);
 /* One FP32 curvilinear V-cycle (weighted Jacobi nu1/nu2) on L e = r (transpose 0) or on
- * the transposed-solve operator M^T / J (transpose 1), from e = 0. */
+ * the transposed-solve operator M^T / J (transpose 1), from e = 0 (S / J for either
+ * value with opts.curv_sym). */
 gbmg_status mg_curv_vcycle(gbmg_ctx* ctx, int transpose, const float* r_dev, float* e_dev);
 
 /* Finite-difference gradient on the finest level, spacing 1, periodic: order 4 is the

@@ -40,7 +40,7 @@ class _Opts(ctypes.Structure):
     _fields_ = [("op", ctypes.c_int), ("prec", ctypes.c_int), ("smoother", ctypes.c_int),
                 ("degree", ctypes.c_int), ("alpha", ctypes.c_double), ("nu1", ctypes.c_int),
                 ("nu2", ctypes.c_int), ("omega", ctypes.c_double), ("fused", ctypes.c_int),
-                ("krylov", ctypes.c_int)]
+                ("krylov", ctypes.c_int), ("curv_sym", ctypes.c_int)]
 
 
 class _Stats(ctypes.Structure):
@@ -191,7 +191,8 @@ class Solver:
 
     def __init__(self, shape, levels: int = 0, degree: int = 3, prec: str = "mixed",
                  smoother: str | None = None, fused: bool = True, alpha: float = 8.0,
-                 nu1: int = 2, nu2: int = 2, omega: float = 2.0 / 3.0, op: str = "flat", krylov: int = 0):
+                 nu1: int = 2, nu2: int = 2, omega: float = 2.0 / 3.0, op: str = "flat", krylov: int = 0,
+                 curv_sym: bool = False):
         L = lib()
         if smoother is None:
             smoother = "jacobi" if op == "curv" else "chebyshev"
@@ -204,6 +205,7 @@ class Solver:
         o.smoother = {"chebyshev": CHEBYSHEV, "jacobi": JACOBI}[smoother]
         o.degree, o.alpha, o.nu1, o.nu2, o.omega, o.fused = degree, alpha, nu1, nu2, omega, int(fused)
         o.krylov = int(krylov)
+        o.curv_sym = int(curv_sym)
         self.prec = prec
         self.work_dtype = torch.float64 if prec == "fp64" else torch.float32
         ctx = _P()

@@ -12,6 +12,13 @@
 // the two adjacent cells averaged onto the face.  L = M / J is the operator the
 // V-cycle solves (Eq. curv_linsys); the transposed solve of the adjoint uses the
 // exact transpose M^T (by summation by parts) with the same 1/J.
+//
+// Symmetric variant S (an option; not the paper's scheme): the same B^{aa} face terms,
+// the cross terms on the cell edges, -sum_{a != b} E_a^T C_ab E_b, C_ab the mean of B^{ab}
+// over the edge's four cells and E_a the a-difference averaged over the edge's two
+// b-positions.  S = S^T; it is its own transpose in the adjoint.
+//
+// Operator form of a launch: 0 = M, 1 = M^T, 2 = S.
 #include "kernels.h"
 #include "stencil.cuh"
 
@@ -144,6 +151,93 @@ __device__ __forceinline__ T diag_M_h2(const BF& Bc) {
   return d;
 }
 
+// Edge coefficient C_ab of the ab-edge at c + (e_a + e_b)/2: mean of B^{ab} over its four cells.
+template <typename T, typename BF>
+__device__ __forceinline__ T edge_B(const BF& Bc, int a, int b, int cx, int cy, int cz) {
+  int ax = cx, ay = cy, az = cz, bx = cx, by = cy, bz = cz;
+  shift(a, 1, ax, ay, az);
+  shift(b, 1, bx, by, bz);
+  int px = ax, py = ay, pz = az;
+  shift(b, 1, px, py, pz);
+  const int k = bidx(a, b);
+  return T(0.25) * ((T(Bc(k, cx, cy, cz)) + T(Bc(k, ax, ay, az))) + (T(Bc(k, bx, by, bz)) + T(Bc(k, px, py, pz))));
+}
+
+// Offsets of the four edges around the centre cell in the ab-plane and of the edge
+// neighbour each couples to: edge k has its base at -a (k & 1), -b (k & 2); the
+// neighbour is at (k & 1 ? -a : +a) + (k & 2 ? -b : +b).  -(E_a^T C E_b + E_b^T C E_a) u
+// at the centre is (1/2) sum_k sgn_k C(edge k) (u(nbr k) - u_0), sgn = +1 for k = 0, 3
+// and -1 for k = 1, 2 (written out from the two transposed edge differences).
+__device__ __forceinline__ void edge_k(int a, int b, int k, int& ex, int& ey, int& ez, int& nx, int& ny, int& nz) {
+  ex = ey = ez = 0;
+  if (k & 1) shift(a, -1, ex, ey, ez);
+  if (k & 2) shift(b, -1, ex, ey, ez);
+  nx = ny = nz = 0;
+  shift(a, (k & 1) ? -1 : 1, nx, ny, nz);
+  shift(b, (k & 2) ? -1 : 1, nx, ny, nz);
+}
+
+// h^2 (S u) at the centre cell (symmetric variant).
+template <typename T, typename UF, typename BF>
+__device__ __forceinline__ T apply_S_h2(const UF& u, const BF& Bc) {
+  const T u0 = u(0, 0, 0);
+  T out = T(0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    int px = 0, py = 0, pz = 0, mx = 0, my = 0, mz = 0;
+    shift(a, 1, px, py, pz);
+    shift(a, -1, mx, my, mz);
+    out += face_B<T>(Bc, a, a, 0, 0, 0) * (u(px, py, pz) - u0) - face_B<T>(Bc, a, a, mx, my, mz) * (u0 - u(mx, my, mz));
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = a + 1; b < 3; ++b) {
+      T c = T(0);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        int ex, ey, ez, nx, ny, nz;
+        edge_k(a, b, k, ex, ey, ez, nx, ny, nz);
+        const T t = edge_B<T>(Bc, a, b, ex, ey, ez) * (u(nx, ny, nz) - u0);
+        c += (k == 1 || k == 2) ? -t : t;
+      }
+      out += T(0.5) * c;
+    }
+  return out;
+}
+
+// h^2 times the diagonal of S: the face part of diag_M_h2 and, per pair a < b,
+// (1/2) (-C(edge 0) + C(edge 1) + C(edge 2) - C(edge 3)).
+template <typename T, typename BF>
+__device__ __forceinline__ T diag_S_h2(const BF& Bc) {
+  T d = diag_M_h2<T>(Bc);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = a + 1; b < 3; ++b) {
+      T c = T(0);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        int ex, ey, ez, nx, ny, nz;
+        edge_k(a, b, k, ex, ey, ez, nx, ny, nz);
+        const T t = edge_B<T>(Bc, a, b, ex, ey, ez);
+        c += (k == 1 || k == 2) ? t : -t;
+      }
+      d += T(0.5) * c;
+    }
+  return d;
+}
+
+// operator of form 0 / 1 / 2 (M, M^T, S) and its diagonal
+template <typename T, typename UF, typename BF>
+__device__ __forceinline__ T op_form_h2(const UF& u, const BF& Bc, int form) {
+  return form == 2 ? apply_S_h2<T>(u, Bc) : (form == 1 ? apply_MT_h2<T>(u, Bc) : apply_M_h2<T>(u, Bc));
+}
+template <typename T, typename BF>
+__device__ __forceinline__ T diag_form_h2(const BF& Bc, int form) {
+  return form == 2 ? diag_S_h2<T>(Bc) : diag_M_h2<T>(Bc);
+}
+
 template <typename V>
 struct FieldAt {
   const V* __restrict__ p;
@@ -160,8 +254,8 @@ struct CoefAt {
 };
 
 template <typename T>
-__device__ __forceinline__ T op_h2(const FieldAt<T>& u, const CoefAt& B, bool transpose) {
-  return transpose ? apply_MT_h2<T>(u, B) : apply_M_h2<T>(u, B);
+__device__ __forceinline__ T op_h2(const FieldAt<T>& u, const CoefAt& B, int form) {
+  return op_form_h2<T>(u, B, form);
 }
 
 // ------------------------------------------------------------------ kernels
@@ -194,17 +288,17 @@ __global__ void k_geom(Dims d, const double* __restrict__ psi, double h, CurvCoe
   out.B[5][i] = (float)((j01 * j02 + j11 * j12 + j12 * j22) * iJ);
 }
 
-// out = op(u) / J (divide_J) or op(u), op = M or M^T
+// out = op(u) / J (divide_J) or op(u), op of the given form
 template <typename T>
 __global__ void k_curv_apply(Dims d, CurvCoef cf, const T* __restrict__ u, T* __restrict__ out, T inv_h2,
-                             int transpose, int divide_J) {
+                             int form, int divide_J) {
   const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y, z = blockIdx.z;
   if (x >= d.nx || y >= d.ny) return;
   const Nbhd nb(d, x, y, z);
   const FieldAt<T> U{u, &nb};
   const CoefAt Bc{cf, &nb};
   const long long i = nb(0, 0, 0);
-  T v = op_h2<T>(U, Bc, transpose) * inv_h2;
+  T v = op_h2<T>(U, Bc, form) * inv_h2;
   if (divide_J) v /= T(cf.J[i]);
   out[i] = v;
 }
@@ -212,7 +306,7 @@ __global__ void k_curv_apply(Dims d, CurvCoef cf, const T* __restrict__ u, T* __
 // out = r - op(u) / J, with optional block partial sums of out^2
 template <typename T>
 __global__ void k_curv_residual(Dims d, CurvCoef cf, const T* __restrict__ r, const T* __restrict__ u,
-                                T* __restrict__ out, T inv_h2, int transpose, double* __restrict__ partials) {
+                                T* __restrict__ out, T inv_h2, int form, double* __restrict__ partials) {
   __shared__ double sh[32];
   const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y, z = blockIdx.z;
   T res = T(0);
@@ -221,7 +315,7 @@ __global__ void k_curv_residual(Dims d, CurvCoef cf, const T* __restrict__ r, co
     const FieldAt<T> U{u, &nb};
     const CoefAt Bc{cf, &nb};
     const long long i = nb(0, 0, 0);
-    res = r[i] - op_h2<T>(U, Bc, transpose) * inv_h2 / T(cf.J[i]);
+    res = r[i] - op_h2<T>(U, Bc, form) * inv_h2 / T(cf.J[i]);
     out[i] = res;
   }
   if (partials) {
@@ -236,15 +330,15 @@ __global__ void k_curv_residual(Dims d, CurvCoef cf, const T* __restrict__ r, co
 // written as e + omega (J r - M e) / diag(M).
 template <typename T>
 __global__ void k_curv_jacobi(Dims d, CurvCoef cf, const T* __restrict__ r, const T* __restrict__ e_in,
-                              T* __restrict__ e_out, int transpose, T omega) {
+                              T* __restrict__ e_out, int form, T omega) {
   const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y, z = blockIdx.z;
   if (x >= d.nx || y >= d.ny) return;
   const Nbhd nb(d, x, y, z);
   const FieldAt<T> U{e_in, &nb};
   const CoefAt Bc{cf, &nb};
   const long long i = nb(0, 0, 0);
-  const T Mh2 = op_h2<T>(U, Bc, transpose);
-  const T Dh2 = diag_M_h2<T>(Bc);
+  const T Mh2 = op_h2<T>(U, Bc, form);
+  const T Dh2 = diag_form_h2<T>(Bc, form);
   // (J r - M e) / diag(M) with h^2 scalings cancelling: (J r h^2 - M e h^2) / (diag h^2)
   e_out[i] = e_in[i] + omega * ((T(cf.J[i]) * r[i] * cf.h2 - Mh2) / Dh2);
 }
@@ -256,7 +350,7 @@ struct UnitAt {
   __device__ __forceinline__ double operator()(int dx, int dy, int dz) const { return (*nb)(dx, dy, dz) == j ? 1.0 : 0.0; }
 };
 
-__global__ void k_curv_dense(Dims d, CurvCoef cf, int transpose, double* __restrict__ out) {
+__global__ void k_curv_dense(Dims d, CurvCoef cf, int form, double* __restrict__ out) {
   const long long n = ncell(d);
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= n * n) return;
@@ -265,7 +359,7 @@ __global__ void k_curv_dense(Dims d, CurvCoef cf, int transpose, double* __restr
   const Nbhd nb(d, x, y, z);
   const UnitAt U{&nb, j};
   const CoefAt Bc{cf, &nb};
-  const double v = transpose ? apply_MT_h2<double>(U, Bc) : apply_M_h2<double>(U, Bc);
+  const double v = op_form_h2<double>(U, Bc, form);
   out[idx] = v / ((double)cf.h2 * (double)cf.J[i]);
 }
 
@@ -352,6 +446,30 @@ __device__ __forceinline__ void df_apply_MT(DfAcc& acc, const UF& y, const BF& B
   }
 }
 
+// acc += sign * h^2 (S u) (symmetric variant) with u double-float, every difference in double-float.
+template <typename UF, typename BF>
+__device__ __forceinline__ void df_apply_S(DfAcc& acc, const UF& u, const BF& Bc, float sign) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    int px = 0, py = 0, pz = 0, mx = 0, my = 0, mz = 0;
+    shift(a, 1, px, py, pz);
+    shift(a, -1, mx, my, mz);
+    df_acc_prod(acc, sign * face_B<float>(Bc, a, a, 0, 0, 0), df_sub(u(px, py, pz), u(0, 0, 0)));
+    df_acc_prod(acc, -sign * face_B<float>(Bc, a, a, mx, my, mz), df_sub(u(0, 0, 0), u(mx, my, mz)));
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = a + 1; b < 3; ++b)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        int ex, ey, ez, nx, ny, nz;
+        edge_k(a, b, k, ex, ey, ez, nx, ny, nz);
+        const float w = ((k == 1 || k == 2) ? -0.5f : 0.5f) * sign * edge_B<float>(Bc, a, b, ex, ey, ez);
+        df_acc_prod(acc, w, df_sub(u(nx, ny, nz), u(0, 0, 0)));
+      }
+}
+
 // partial sums of x * J and of J (volume-weighted mean, Eq. solvability)
 __global__ void k_wsum(long long n, const double* __restrict__ x, const float* __restrict__ J,
                        double* __restrict__ pxj, double* __restrict__ pj) {
@@ -391,7 +509,7 @@ __global__ void k_ratio(const double* a, const double* b, double* out) {
 __global__ void k_psibar_A(Dims d, const double* __restrict__ psi, const double* __restrict__ phi,
                            const double* __restrict__ lam, const double* __restrict__ delta,
                            const double* __restrict__ mw_dev, const double* __restrict__ slam_dev,
-                           double h, double* __restrict__ S) {
+                           double h, int sym, double* __restrict__ S) {
   const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y, z = blockIdx.z;
   if (x >= d.nx || y >= d.ny) return;
   const long long n = ncell(d);
@@ -447,7 +565,32 @@ __global__ void k_psibar_A(Dims d, const double* __restrict__ psi, const double*
   for (int a = 0; a < 3; ++a) {
     int mx = 0, my = 0, mz = 0;
     shift(a, -1, mx, my, mz);
-    for (int b = 0; b < 3; ++b) Bb[a][b] = 0.5 * (fbar(a, b, 0, 0, 0) + fbar(a, b, mx, my, mz));
+    for (int b = 0; b < 3; ++b)
+      Bb[a][b] = (sym && b != a) ? 0.0 : 0.5 * (fbar(a, b, 0, 0, 0) + fbar(a, b, mx, my, mz));
+  }
+  if (sym) {
+    // symmetric variant: d<lam, S phi>/dC on the ab-edge at base e is
+    //   (1/2h^2) [lam_e (phi_{e+a+b} - phi_e) - lam_{e+a} (phi_{e+b} - phi_{e+a})
+    //             - lam_{e+b} (phi_{e+a} - phi_{e+b}) + lam_{e+a+b} (phi_e - phi_{e+a+b})],
+    // and each of the four edges around this cell takes a quarter of its B^{ab} (a < b).
+    for (int a = 0; a < 3; ++a)
+      for (int b = a + 1; b < 3; ++b) {
+        double acc = 0.0;
+        for (int k = 0; k < 4; ++k) {
+          int ex = 0, ey = 0, ez = 0;
+          if (k & 1) shift(a, -1, ex, ey, ez);
+          if (k & 2) shift(b, -1, ex, ey, ez);
+          int ax = ex, ay = ey, az = ez, bx = ex, by = ey, bz = ez;
+          shift(a, 1, ax, ay, az);
+          shift(b, 1, bx, by, bz);
+          int px = ax, py = ay, pz = az;
+          shift(b, 1, px, py, pz);
+          const double pe = PH(ex, ey, ez), pa = PH(ax, ay, az), pb = PH(bx, by, bz), pp = PH(px, py, pz);
+          acc += LA(ex, ey, ez) * (pp - pe) - LA(ax, ay, az) * (pb - pa) - LA(bx, by, bz) * (pa - pb) +
+                 LA(px, py, pz) * (pe - pp);
+        }
+        Bb[a][b] = 0.25 * 0.5 * acc / (h * h);
+      }
   }
   // Abar_B = J <Bbar, A^-2> A^-1 - J (A^-1 Bbar A^-2 + A^-2 Bbar A^-1)   (A symmetric)
   double inner = 0.0;
@@ -634,9 +777,9 @@ __global__ void __launch_bounds__(CNT) k_curv_tiled(Dims d, CurvCoef cf, const f
       const RingU<float> U{{ring.u(slot(t - 1)), ring.u(slot(t)), ring.u(slot(t + 1))}, c};
       const RingB Bc{{ring.b(slot(t - 1)), ring.b(slot(t)), ring.b(slot(t + 1))}, c};
       const long long i = (long long)t * pst + (long long)y * d.nx + x;
-      const float Mh2 = TR ? apply_MT_h2<float>(U, Bc) : apply_M_h2<float>(U, Bc);
+      const float Mh2 = TR == 2 ? apply_S_h2<float>(U, Bc) : (TR ? apply_MT_h2<float>(U, Bc) : apply_M_h2<float>(U, Bc));
       if (MODE == CM_JACOBI) {
-        const float Dh2 = diag_M_h2<float>(Bc);
+        const float Dh2 = TR == 2 ? diag_S_h2<float>(Bc) : diag_M_h2<float>(Bc);
         out[i] = U(0, 0, 0) + omega * ((cf.J[i] * r[i] * cf.h2 - Mh2) / Dh2);
       } else {
         const float res = r[i] - Mh2 * inv_h2 / cf.J[i];
@@ -662,7 +805,7 @@ struct DfRingAt {
 // of r^2 and of (b / J)^2.
 __global__ void __launch_bounds__(CNT) k_curv_df_residual_tiled(Dims d, CurvCoef cf, const float2* __restrict__ src,
                                                                  const double* __restrict__ m_dev, int scale_J,
-                                                                 const float2* __restrict__ u, int transpose,
+                                                                 const float2* __restrict__ u, int form,
                                                                  float* __restrict__ r, double* __restrict__ pr2,
                                                                  double* __restrict__ pf2, int zc) {
   extern __shared__ __align__(16) char smc[];
@@ -699,7 +842,8 @@ __global__ void __launch_bounds__(CNT) k_curv_df_residual_tiled(Dims d, CurvCoef
       df_acc_prod(acc, wb, b);
       const DfRingAt U{{ring.u(slot(t - 1)), ring.u(slot(t)), ring.u(slot(t + 1))}, c};
       const RingB Bc{{ring.b(slot(t - 1)), ring.b(slot(t)), ring.b(slot(t + 1))}, c};
-      if (transpose) df_apply_MT(acc, U, Bc, -1.f);
+      if (form == 2) df_apply_S(acc, U, Bc, -1.f);
+      else if (form == 1) df_apply_MT(acc, U, Bc, -1.f);
       else df_apply_M(acc, U, Bc, -1.f);
       const float rv = (acc.s + acc.c) / (J * cf.h2);
       r[i] = rv;
@@ -721,9 +865,9 @@ __global__ void __launch_bounds__(CNT) k_curv_df_residual_tiled(Dims d, CurvCoef
 }  // namespace
 
 cudaError_t launch_psibar(cudaStream_t st, Dims d, const double* psi, const double* phi, const double* lam,
-                          const double* delta, const double* mw_dev, const double* slam_dev, double h, double* S,
-                          double* out) {
-  k_psibar_A<<<cell_grid(d), dim3(BX, BY), 0, st>>>(d, psi, phi, lam, delta, mw_dev, slam_dev, h, S);
+                          const double* delta, const double* mw_dev, const double* slam_dev, double h, int sym,
+                          double* S, double* out) {
+  k_psibar_A<<<cell_grid(d), dim3(BX, BY), 0, st>>>(d, psi, phi, lam, delta, mw_dev, slam_dev, h, sym, S);
   note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -746,8 +890,8 @@ cudaError_t launch_geom(cudaStream_t st, Dims d, const double* psi, double h, Cu
 }
 
 template <typename T>
-cudaError_t launch_curv_apply(cudaStream_t st, Dims d, CurvCoef cf, const T* u, T* out, int transpose, int divide_J) {
-  k_curv_apply<T><<<cell_grid(d), dim3(BX, BY), 0, st>>>(d, cf, u, out, (T)(1.0 / cf.h2), transpose, divide_J);
+cudaError_t launch_curv_apply(cudaStream_t st, Dims d, CurvCoef cf, const T* u, T* out, int form, int divide_J) {
+  k_curv_apply<T><<<cell_grid(d), dim3(BX, BY), 0, st>>>(d, cf, u, out, (T)(1.0 / cf.h2), form, divide_J);
   note_launch();
   return cudaGetLastError();
 }
@@ -758,49 +902,54 @@ long long curv_partial_count(Dims d) {
 }
 
 template <typename T>
-cudaError_t launch_curv_residual(cudaStream_t st, Dims d, CurvCoef cf, const T* r, const T* u, T* out, int transpose,
+cudaError_t launch_curv_residual(cudaStream_t st, Dims d, CurvCoef cf, const T* r, const T* u, T* out, int form,
                                  double* partials) {
+  if (form < 0 || form > 2) return cudaErrorInvalidValue;
   if constexpr (sizeof(T) == 4) {
     const size_t sm = 4 * ring_slot_bytes<float>();
     const float ih2 = (float)(1.0 / cf.h2);
-    if (transpose)
-      k_curv_tiled<CM_RESID, 1><<<curv_tiled_grid(d), CNT, sm, st>>>(d, cf, r, u, out, 0.f, ih2, partials, curv_zchunk(d));
-    else
-      k_curv_tiled<CM_RESID, 0><<<curv_tiled_grid(d), CNT, sm, st>>>(d, cf, r, u, out, 0.f, ih2, partials, curv_zchunk(d));
+    const dim3 g = curv_tiled_grid(d);
+    const int zc = curv_zchunk(d);
+    if (form == 2) k_curv_tiled<CM_RESID, 2><<<g, CNT, sm, st>>>(d, cf, r, u, out, 0.f, ih2, partials, zc);
+    else if (form == 1) k_curv_tiled<CM_RESID, 1><<<g, CNT, sm, st>>>(d, cf, r, u, out, 0.f, ih2, partials, zc);
+    else k_curv_tiled<CM_RESID, 0><<<g, CNT, sm, st>>>(d, cf, r, u, out, 0.f, ih2, partials, zc);
   } else {
-    k_curv_residual<T><<<cell_grid(d), dim3(BX, BY), 0, st>>>(d, cf, r, u, out, (T)(1.0 / cf.h2), transpose, partials);
+    k_curv_residual<T><<<cell_grid(d), dim3(BX, BY), 0, st>>>(d, cf, r, u, out, (T)(1.0 / cf.h2), form, partials);
   }
   note_launch();
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_curv_jacobi(cudaStream_t st, Dims d, CurvCoef cf, const T* r, const T* e_in, T* e_out, int transpose,
+cudaError_t launch_curv_jacobi(cudaStream_t st, Dims d, CurvCoef cf, const T* r, const T* e_in, T* e_out, int form,
                                T omega) {
+  if (form < 0 || form > 2) return cudaErrorInvalidValue;
   if constexpr (sizeof(T) == 4) {
     const size_t sm = 4 * ring_slot_bytes<float>();
-    if (transpose)
-      k_curv_tiled<CM_JACOBI, 1><<<curv_tiled_grid(d), CNT, sm, st>>>(d, cf, r, e_in, e_out, omega, 0.f, nullptr, curv_zchunk(d));
-    else
-      k_curv_tiled<CM_JACOBI, 0><<<curv_tiled_grid(d), CNT, sm, st>>>(d, cf, r, e_in, e_out, omega, 0.f, nullptr, curv_zchunk(d));
+    const dim3 g = curv_tiled_grid(d);
+    const int zc = curv_zchunk(d);
+    if (form == 2) k_curv_tiled<CM_JACOBI, 2><<<g, CNT, sm, st>>>(d, cf, r, e_in, e_out, omega, 0.f, nullptr, zc);
+    else if (form == 1) k_curv_tiled<CM_JACOBI, 1><<<g, CNT, sm, st>>>(d, cf, r, e_in, e_out, omega, 0.f, nullptr, zc);
+    else k_curv_tiled<CM_JACOBI, 0><<<g, CNT, sm, st>>>(d, cf, r, e_in, e_out, omega, 0.f, nullptr, zc);
   } else {
-    k_curv_jacobi<T><<<cell_grid(d), dim3(BX, BY), 0, st>>>(d, cf, r, e_in, e_out, transpose, omega);
+    k_curv_jacobi<T><<<cell_grid(d), dim3(BX, BY), 0, st>>>(d, cf, r, e_in, e_out, form, omega);
   }
   note_launch();
   return cudaGetLastError();
 }
 
-cudaError_t launch_curv_dense(cudaStream_t st, Dims d, CurvCoef cf, int transpose, double* out) {
+cudaError_t launch_curv_dense(cudaStream_t st, Dims d, CurvCoef cf, int form, double* out) {
   const long long n = ncell(d);
-  k_curv_dense<<<(unsigned)((n * n + 255) / 256), 256, 0, st>>>(d, cf, transpose, out);
+  k_curv_dense<<<(unsigned)((n * n + 255) / 256), 256, 0, st>>>(d, cf, form, out);
   note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_curv_df_residual(cudaStream_t st, Dims d, CurvCoef cf, const float2* src, const double* m_dev,
-                                    int scale_J, const float2* u, int transpose, float* r, double* pr2, double* pf2) {
+                                    int scale_J, const float2* u, int form, float* r, double* pr2, double* pf2) {
+  if (form < 0 || form > 2) return cudaErrorInvalidValue;
   k_curv_df_residual_tiled<<<curv_tiled_grid(d), CNT, 4 * ring_slot_bytes<float2>(), st>>>(
-      d, cf, src, m_dev, scale_J, u, transpose, r, pr2, pf2, curv_zchunk(d));
+      d, cf, src, m_dev, scale_J, u, form, r, pr2, pf2, curv_zchunk(d));
   note_launch();
   return cudaGetLastError();
 }

@@ -9,6 +9,7 @@
 // Adjoint (Sec. 4.8, Eq. adj_rhs / adj_op, written with the exact transpose):
 // M^T lam = phi_bar - mean(phi_bar) by the same V-cycle on M^T / J,
 // delta_bar = J (lam - sum(J lam)/sum(J)), psi_bar through the geometry.
+// With the symmetric variant (opts.curv_sym) both solves use S, its own transpose.
 #include <cstring>
 #include <vector>
 
@@ -20,6 +21,9 @@ using namespace gbmg;
 namespace {
 
 enum CurvScal { S_SUMJ = 6, S_MW = 9, S_SLAM = 10 };
+
+// operator form of the forward (tr false) or transposed (tr true) problem: 0 = M, 1 = M^T, 2 = S
+int curv_form(const gbmg_ctx* c, bool tr) { return c->o.curv_sym ? 2 : (tr ? 1 : 0); }
 
 template <typename T>
 const T* curv_G(const gbmg_ctx* c, bool tr);
@@ -33,7 +37,7 @@ gbmg_status curv_smooth(gbmg_ctx* c, int l, T*& e, T*& eo, const T* r, int nu, b
   const Level& L = c->lv[l];
   for (int k = 0; k < nu; ++k) {
     ProfScope ps(c, l == 0 ? GBMG_PROF_CURV0 : GBMG_PROF_OFF);
-    TRY(launch_curv_jacobi<T>(c->stream, L.d, L.cc, r, e, eo, tr ? 1 : 0, (T)c->o.omega));
+    TRY(launch_curv_jacobi<T>(c->stream, L.d, L.cc, r, e, eo, curv_form(c, tr), (T)c->o.omega));
     std::swap(e, eo);
   }
   return GBMG_OK;
@@ -49,7 +53,7 @@ gbmg_status vcycle_curv(gbmg_ctx* c, int l, T*& e, T*& eo, const T* r, bool tr) 
     return GBMG_OK;
   }
   TRYS(curv_smooth<T>(c, l, e, eo, r, c->o.nu1, tr));
-  TRY(launch_curv_residual<T>(c->stream, L.d, L.cc, r, e, (T*)L.t, tr ? 1 : 0, nullptr));
+  TRY(launch_curv_residual<T>(c->stream, L.d, L.cc, r, e, (T*)L.t, curv_form(c, tr), nullptr));
   const Level& C = c->lv[l + 1];
   TRY(launch_restrict<T>(c->stream, L.d, (const T*)L.t, (T*)C.r));
   T* ce = (T*)C.e;
@@ -88,7 +92,7 @@ gbmg_status curv_solve_impl(gbmg_ctx* c, const double* src, const double* u_in, 
     TRY(cudaMemsetAsync(c->phi_df, 0, (size_t)n * sizeof(float2), c->stream));
   }
   float* r0 = (float*)L0.r;
-  const int itr = tr ? 1 : 0;
+  const int itr = curv_form(c, tr);
   TRY(launch_curv_df_residual(c->stream, L0.d, L0.cc, c->F_df, sc + S_MEAN_F, tr ? 0 : 1, c->phi_df, itr, r0, part,
                               part1));
   TRY(launch_finalize(c->stream, part, pc, sc + S_R2, 1.0));
@@ -163,7 +167,7 @@ extern "C" gbmg_status mg_set_geometry(gbmg_ctx* c, const double* psi_dev) {
   TRY(cudaMemcpyAsync(Jc.data(), C.cc.J, (size_t)nc * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
   std::vector<double> Lm((size_t)nc * nc), G;
   for (int tr = 0; tr < 2; ++tr) {
-    TRY(launch_curv_dense(c->stream, C.d, C.cc, tr, c->dense));
+    TRY(launch_curv_dense(c->stream, C.d, C.cc, curv_form(c, tr != 0), c->dense));
     TRY(cudaMemcpyAsync(Lm.data(), c->dense, Lm.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     TRY(cudaStreamSynchronize(c->stream));
     std::vector<double> w(Jc.begin(), Jc.end());
@@ -216,8 +220,8 @@ extern "C" gbmg_status mg_solve_adjoint(gbmg_ctx* c, const double* phi_bar_dev, 
     TRY(launch_finalize(c->stream, part, pr, sc + S_SUM_F, 1.0));
     TRY(launch_finalize(c->stream, part1, pr, sc + S_SUMJ, 1.0));
     TRY(launch_ratio(c->stream, sc + S_SUM_F, sc + S_SUMJ, sc + S_MW));
-    TRY(launch_psibar(c->stream, L0.d, L0.psi, phi_dev, c->adj_lam, source_dev, sc + S_MW, sc + S_SLAM, L0.h, c->adj_S,
-                      psi_bar_dev));
+    TRY(launch_psibar(c->stream, L0.d, L0.psi, phi_dev, c->adj_lam, source_dev, sc + S_MW, sc + S_SLAM, L0.h,
+                      c->o.curv_sym, c->adj_S, psi_bar_dev));
   }
   TRY(cudaStreamSynchronize(c->stream));
   c->last = st;
@@ -235,9 +239,9 @@ extern "C" gbmg_status mg_curv_apply(gbmg_ctx* c, int level, int dtype, int tran
   DeviceGuard g(c->device);
   const Level& L = c->lv[level];
   if (dtype == GBMG_F64)
-    TRY(launch_curv_apply<double>(c->stream, L.d, L.cc, (const double*)u, (double*)out, transpose ? 1 : 0, divide_by_J ? 1 : 0));
+    TRY(launch_curv_apply<double>(c->stream, L.d, L.cc, (const double*)u, (double*)out, curv_form(c, transpose != 0), divide_by_J ? 1 : 0));
   else
-    TRY(launch_curv_apply<float>(c->stream, L.d, L.cc, (const float*)u, (float*)out, transpose ? 1 : 0, divide_by_J ? 1 : 0));
+    TRY(launch_curv_apply<float>(c->stream, L.d, L.cc, (const float*)u, (float*)out, curv_form(c, transpose != 0), divide_by_J ? 1 : 0));
   return GBMG_OK;
 }
 

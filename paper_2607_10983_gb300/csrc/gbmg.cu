@@ -181,6 +181,7 @@ extern "C" void gbmg_default_opts(gbmg_opts* o) {
   o->omega = 2.0 / 3.0;
   o->fused = 1;
   o->krylov = 0;
+  o->curv_sym = 0;
 }
 
 extern "C" const char* mg_status_string(gbmg_status s) {
@@ -228,6 +229,9 @@ extern "C" gbmg_status mg_setup(gbmg_ctx** out, int nx, int ny, int nz, int leve
   if (o.krylov < 0 || o.krylov > 16) return fail(GBMG_ERR_INVALID_ARG, "mg_setup: krylov must be in [0, 16]");
   if (o.krylov && !(o.op == GBMG_OP_FLAT7 && o.prec == GBMG_MIXED && o.smoother == GBMG_SMOOTH_CHEBYSHEV))
     return fail(GBMG_ERR_INVALID_ARG, "mg_setup: krylov needs the flat operator, mixed precision and Chebyshev");
+  if (o.curv_sym != 0 && o.curv_sym != 1) return fail(GBMG_ERR_INVALID_ARG, "mg_setup: curv_sym must be 0 or 1");
+  if (o.curv_sym && o.op != GBMG_OP_CURV19)
+    return fail(GBMG_ERR_INVALID_ARG, "mg_setup: curv_sym needs the curvilinear operator");
   const bool curv = o.op == GBMG_OP_CURV19;
 
   std::vector<Dims> dims = level_dims(nx, ny, nz, levels);

@@ -99,29 +99,32 @@ struct CurvCoefOut {
   float* B[6];
 };
 cudaError_t launch_geom(cudaStream_t st, Dims d, const double* psi, double h, CurvCoefOut out);
-// out = op(u) (/ J when divide_J), op = M or M^T (transpose)
+// Curvilinear operator form: 0 = M (the paper's scheme), 1 = its exact transpose M^T,
+// 2 = the symmetric variant S (its own transpose).
+// out = op(u) (/ J when divide_J)
 template <typename T>
-cudaError_t launch_curv_apply(cudaStream_t st, Dims d, CurvCoef cf, const T* u, T* out, int transpose, int divide_J);
+cudaError_t launch_curv_apply(cudaStream_t st, Dims d, CurvCoef cf, const T* u, T* out, int form, int divide_J);
 // out = r - op(u) / J; partials (nullable): block sums of out^2
 template <typename T>
-cudaError_t launch_curv_residual(cudaStream_t st, Dims d, CurvCoef cf, const T* r, const T* u, T* out, int transpose,
+cudaError_t launch_curv_residual(cudaStream_t st, Dims d, CurvCoef cf, const T* r, const T* u, T* out, int form,
                                  double* partials);
 template <typename T>
-cudaError_t launch_curv_jacobi(cudaStream_t st, Dims d, CurvCoef cf, const T* r, const T* e_in, T* e_out, int transpose,
+cudaError_t launch_curv_jacobi(cudaStream_t st, Dims d, CurvCoef cf, const T* r, const T* e_in, T* e_out, int form,
                                T omega);
 // dense n x n matrix of op / J on a (small) level, FP64 row-major
-cudaError_t launch_curv_dense(cudaStream_t st, Dims d, CurvCoef cf, int transpose, double* out);
+cudaError_t launch_curv_dense(cudaStream_t st, Dims d, CurvCoef cf, int form, double* out);
 // double-float outer residual: r = b - op(u)/J with b = J (src - m) (scale_J) or src
 // block partial sums written by launch_curv_df_residual and launch_curv_residual<float>
 long long curv_partial_count(Dims d);
 cudaError_t launch_curv_df_residual(cudaStream_t st, Dims d, CurvCoef cf, const float2* src, const double* m_dev,
-                                    int scale_J, const float2* u, int transpose, float* r, double* pr2, double* pf2);
+                                    int scale_J, const float2* u, int form, float* r, double* pr2, double* pf2);
 // partial sums of x * J and of J (df_partial_count(n) blocks each)
 cudaError_t launch_wsum(cudaStream_t st, long long n, const double* x, const float* J, double* pxj, double* pj);
-// psi_bar of the curvilinear adjoint on the finest level (S: 6 n doubles of scratch).
+// psi_bar of the curvilinear adjoint on the finest level (S: 6 n doubles of scratch);
+// sym: the operator is the symmetric variant.
 cudaError_t launch_psibar(cudaStream_t st, Dims d, const double* psi, const double* phi, const double* lam,
-                          const double* delta, const double* mw_dev, const double* slam_dev, double h, double* S,
-                          double* out);
+                          const double* delta, const double* mw_dev, const double* slam_dev, double h, int sym,
+                          double* S, double* out);
 // out = J (lam - s) (nullable) and lam64 = lam (nullable), from double-float lam
 cudaError_t launch_jscale(cudaStream_t st, long long n, const float2* lam, const float* J, const double* s_dev,
                           double* out, double* lam64);

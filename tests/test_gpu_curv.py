@@ -237,3 +237,97 @@ def test_mesh_motion_matches_oracle(gb, shape, passes):
         s.solve(to_dev(rho))
     with pytest.raises(gb.GbmgError):
         gb.Solver(shape).mesh_motion(to_dev(rho), to_dev(psi), kappa, m_init, dtau)
+
+
+# ---------------------------------------------------------------- symmetric variant
+
+
+def make_sym(gb, shape, psi):
+    s = gb.Solver(shape, op="curv", curv_sym=True)
+    s.set_geometry(to_dev(psi))
+    return s
+
+
+def test_sym_operator_matches_oracle_stencil(gb):
+    shape = (16, 24, 32)
+    psi = psi_field(shape, 30)
+    s = make_sym(gb, shape, psi)
+    order = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+    rng = np.random.default_rng(31)
+    for level in range(2):
+        shp = s.level_shape(level)
+        h = 2.0 ** level
+        J, B6 = s.curv_geometry(level)
+        J, B6 = J.double().cpu().numpy(), B6.double().cpu().numpy()
+        B = np.empty((3, 3) + shp)
+        for k, (a, b) in enumerate(order):
+            B[a, b] = B6[k]
+            B[b, a] = B6[k]
+        u = rng.standard_normal(shp)
+        ref = curv.apply_M_sym(u, B, h) / J
+        for tr in (False, True):           # S is its own transpose
+            got = s.curv_apply(level, to_dev(u), transpose=tr, divide_by_J=True).cpu().numpy()
+            assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
+        got32 = s.curv_apply(level, to_dev(u, torch.float32)).double().cpu().numpy()
+        assert np.abs(got32 - ref).max() < 2e-5 * np.abs(ref).max()
+        # and it differs from the literal scheme on the same geometry
+        lit = curv.apply_M(u, B, h) / J
+        assert np.abs(lit - ref).max() > 1e-3 * np.abs(ref).max()
+
+
+def test_sym_operator_is_symmetric_on_gpu(gb):
+    shape = (24, 24, 24)
+    s = make_sym(gb, shape, psi_field(shape, 32))
+    rng = np.random.default_rng(33)
+    x, y = to_dev(rng.standard_normal(shape)), to_dev(rng.standard_normal(shape))
+    Sx = s.curv_apply(0, x, divide_by_J=False)
+    Sy = s.curv_apply(0, y, divide_by_J=False)
+    lhs, rhs = float((y * Sx).sum()), float((x * Sy).sum())
+    assert abs(lhs - rhs) < 1e-11 * float((y * Sx).abs().sum())
+    assert float(s.curv_apply(0, torch.ones_like(x), divide_by_J=False).abs().max()) < 1e-12
+
+
+def test_sym_vcycle_and_solve_match_oracle(gb):
+    shape = (32, 32, 32)
+    psi = psi_field(shape, 34)
+    s = make_sym(gb, shape, psi)
+    hier = curv.hierarchy(psi, sym=True)
+    r = grf(shape, 35)
+    rd = to_dev(r, torch.float32)
+    got = s.curv_vcycle(rd).double().cpu().numpy()
+    ref = curv.vcycle(0, np.zeros(shape), rd.double().cpu().numpy(), hier, cache={})
+    assert rel_l2(got, ref) < 2e-5
+    for shp in [(16, 16, 16), (16, 24, 32)]:
+        psi = psi_field(shp, 36)
+        delta = grf(shp, 37)
+        s = make_sym(gb, shp, psi)
+        ref, hist = curv.solve(delta, psi, tol=1e-12, max_cycles=300, sym=True)
+        phi, st = s.solve(to_dev(delta), tol=1e-10, max_vcycles=200)
+        assert st.status == 0
+        assert rel_l2(phi.cpu().numpy(), ref) < 3e-7
+        rho_gpu = (st.history[-1] / st.history[0]) ** (1.0 / max(1, len(st.history) - 1))
+        rho_ora = (hist[-1] / hist[1]) ** (1.0 / (len(hist) - 2))
+        assert rho_gpu < 1.2 * rho_ora + 0.02
+        lit, _ = curv.solve(delta, psi, tol=1e-12, max_cycles=300)
+        assert rel_l2(lit, ref) > 1e-4             # the two discretisations differ
+
+
+def test_sym_adjoint_matches_oracle(gb):
+    shape = (16, 16, 16)
+    psi = psi_field(shape, 38, 1.5, 0.4)
+    delta = grf(shape, 39)
+    pbar = np.random.default_rng(40).standard_normal(shape)
+    s = make_sym(gb, shape, psi)
+    phi, _ = s.solve(to_dev(delta), tol=1e-11, max_vcycles=200)
+    dbar, psibar, st = s.solve_adjoint(to_dev(pbar), phi=phi, source=to_dev(delta), want_psi_bar=True,
+                                       tol=1e-11, max_vcycles=200)
+    assert st.status == 0
+    ref_phi, _ = curv.solve(delta, psi, tol=1e-13, max_cycles=400, sym=True)
+    rd, rp = curv.solve_vjp(delta, psi, ref_phi, pbar, tol=1e-13, max_cycles=400, sym=True)
+    assert rel_l2(dbar.cpu().numpy(), rd) < 1e-6
+    assert rel_l2(psibar.cpu().numpy(), rp) < 1e-5
+
+
+def test_sym_option_needs_the_curvilinear_operator(gb):
+    with pytest.raises(gb.GbmgError):
+        gb.Solver((16, 16, 16), curv_sym=True)
