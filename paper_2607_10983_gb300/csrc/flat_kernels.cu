@@ -212,6 +212,59 @@ __global__ void k_f64_to_df(long long n, const double* __restrict__ x, float2* _
   }
 }
 
+// Two consecutive elements per thread and iteration (16-byte accesses; x, out 16-byte
+// aligned, n2 = n / 2 pairs, the odd last element by thread 0 of block 0).
+__global__ void k_f64_to_df_x2(long long n, const double2* __restrict__ x, float4* __restrict__ out,
+                               double* __restrict__ ps) {
+  __shared__ double sh[32];
+  DfAcc s{0.f, 0.f};
+  const long long n2 = n / 2;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+    const double2 v = x[i];
+    const float2 a = f64_to_df(v.x), b = f64_to_df(v.y);
+    out[i] = make_float4(a.x, a.y, b.x, b.y);
+    s.add(a.x);
+    s.c += a.y;
+    s.add(b.x);
+    s.c += b.y;
+  }
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+    const float2 a = f64_to_df(reinterpret_cast<const double*>(x)[n - 1]);
+    reinterpret_cast<float2*>(out)[n - 1] = a;
+    s.add(a.x);
+    s.c += a.y;
+  }
+  if (ps) {
+    const double b = block_sum_acc(s, sh);
+    if (threadIdx.x == 0) ps[blockIdx.x] = b;
+  }
+}
+
+__global__ void k_df_to_f64_x2(long long n, const float4* __restrict__ in, const double* __restrict__ shift,
+                               double2* __restrict__ out) {
+  float2 ms = make_float2(0.f, 0.f);
+  if (shift) {
+    ms = f64_to_df(shift[0]);
+    ms.x = -ms.x;
+    ms.y = -ms.y;
+  }
+  const long long n2 = n / 2;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+    const float4 v = in[i];
+    float2 a = make_float2(v.x, v.y), b = make_float2(v.z, v.w);
+    if (shift) {
+      a = df_add(a, ms);
+      b = df_add(b, ms);
+    }
+    out[i] = make_double2(df_to_f64(a), df_to_f64(b));
+  }
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+    float2 a = reinterpret_cast<const float2*>(in)[n - 1];
+    if (shift) a = df_add(a, ms);
+    reinterpret_cast<double*>(out)[n - 1] = df_to_f64(a);
+  }
+}
+
 __global__ void k_df_to_f64(long long n, const float2* __restrict__ in, const double* __restrict__ shift,
                             double* __restrict__ out) {
   float2 ms = make_float2(0.f, 0.f);
@@ -351,13 +404,26 @@ cudaError_t launch_scalars_to_host(cudaStream_t st, const double* src, double* d
   return cudaGetLastError();
 }
 
+static bool aligned16(const void* a, const void* b) {
+  return ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15) == 0;
+}
+
+// df_partial_count(n) partials either way (the pair form runs red_blocks(n) blocks too)
 cudaError_t launch_f64_to_df(cudaStream_t st, long long n, const double* x, float2* out, double* ps) {
-  k_f64_to_df<<<red_blocks(n), RED_THREADS, 0, st>>>(n, x, out, ps);
+  if (aligned16(x, out))
+    k_f64_to_df_x2<<<red_blocks(n), RED_THREADS, 0, st>>>(n, reinterpret_cast<const double2*>(x),
+                                                           reinterpret_cast<float4*>(out), ps);
+  else
+    k_f64_to_df<<<red_blocks(n), RED_THREADS, 0, st>>>(n, x, out, ps);
   note_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_df_to_f64(cudaStream_t st, long long n, const float2* in, const double* shift, double* out) {
-  k_df_to_f64<<<red_blocks(n), RED_THREADS, 0, st>>>(n, in, shift, out);
+  if (aligned16(in, out))
+    k_df_to_f64_x2<<<red_blocks(n), RED_THREADS, 0, st>>>(n, reinterpret_cast<const float4*>(in), shift,
+                                                           reinterpret_cast<double2*>(out));
+  else
+    k_df_to_f64<<<red_blocks(n), RED_THREADS, 0, st>>>(n, in, shift, out);
   note_launch();
   return cudaGetLastError();
 }

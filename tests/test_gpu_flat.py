@@ -123,6 +123,11 @@ def test_df_conversions_bit_exact(gb):
     assert err.max() < 2.0 ** -46
     special = s.f64_to_df(to_dev(np.array([np.inf, -np.inf, np.nan]))).cpu().numpy()
     assert np.isposinf(special[0, 0]) and np.isneginf(special[1, 0]) and np.isnan(special[2, 0])
+    # 8-byte-aligned views take the one-element kernels; same values
+    xd = to_dev(x)
+    np.testing.assert_array_equal(s.f64_to_df(xd[1:]).cpu().numpy(), df[1:])
+    dd = to_dev(df, torch.float32)
+    np.testing.assert_array_equal(s.df_to_f64(dd[1:]).cpu().numpy(), back[1:])
 
 
 @pytest.mark.parametrize("n", [32, 64])
