@@ -196,15 +196,28 @@ __global__ void k_finalize(const double* __restrict__ p, long long count, double
 
 // ---- double-float ----
 
+// One element per access (any alignment); elements are visited in the pair order of
+// k_f64_to_df_x2 (pair q = elements 2q, 2q + 1) so that the partial sums, and with them
+// the mean, do not depend on the alignment of x.
 __global__ void k_f64_to_df(long long n, const double* __restrict__ x, float2* __restrict__ out,
                             double* __restrict__ ps) {
   __shared__ double sh[32];
   DfAcc s{0.f, 0.f};
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const float2 v = f64_to_df(x[i]);
-    out[i] = v;
-    s.add(v.x);
-    s.c += v.y;
+  const long long n2 = n / 2;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n2; q += (long long)gridDim.x * blockDim.x) {
+    const float2 a = f64_to_df(x[2 * q]), b = f64_to_df(x[2 * q + 1]);
+    out[2 * q] = a;
+    out[2 * q + 1] = b;
+    s.add(a.x);
+    s.c += a.y;
+    s.add(b.x);
+    s.c += b.y;
+  }
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+    const float2 a = f64_to_df(x[n - 1]);
+    out[n - 1] = a;
+    s.add(a.x);
+    s.c += a.y;
   }
   if (ps) {
     const double b = block_sum_acc(s, sh);

@@ -286,6 +286,24 @@ def test_host_sequence_reports_nonconvergence(gb):
     assert np.isfinite(outs[1]).all()
 
 
+def test_results_do_not_depend_on_buffer_alignment(gb):
+    # 16-byte-aligned F and phi take the pair conversion kernels, 8-byte-offset views the
+    # one-element kernels; both visit the elements in the same order for the mean of F,
+    # so copies, residuals and iterates are identical.
+    n = 32
+    F, phi0 = grf(n, 70), grf(n, 71)
+    s = gb.Solver(n, prec="mixed")
+    phi_a, st_a = s.solve(to_dev(F), to_dev(phi0), tol=1e-10)
+    bf = torch.empty(n ** 3 + 1, dtype=torch.float64, device=DEV)
+    bp = torch.empty(n ** 3 + 1, dtype=torch.float64, device=DEV)
+    Fb, pb = bf[1:].view(n, n, n), bp[1:].view(n, n, n)
+    Fb.copy_(to_dev(F))
+    pb.copy_(to_dev(phi0))
+    phi_b, st_b = s.solve(Fb, pb, tol=1e-10)
+    assert st_a.cycles == st_b.cycles and st_a.history == st_b.history
+    np.testing.assert_array_equal(phi_a.cpu().numpy(), phi_b.cpu().numpy())
+
+
 def test_error_statuses(gb):
     n = 16
     s = gb.Solver(n, prec="mixed")
