@@ -38,6 +38,27 @@ template <typename T>
 cudaError_t launch_prolong_add(cudaStream_t st, Dims coarse, const T* c, T* f);
 template <typename T>
 cudaError_t launch_coarse_matvec(cudaStream_t st, int n, const T* G, const T* r, T* e);
+
+// The bottom of the FP32 Chebyshev V-cycle in one CTA (levels that fit in shared
+// memory): levels 0 .. nl-1 of the sub-hierarchy, the last the coarsest (e = G r).
+// Bit-identical to the one-kernel-per-operation chain from e = 0 on level 0.
+constexpr int kSmallMaxL = 4;               // levels of the sub-hierarchy
+constexpr int kSmallCells = 4096;           // cells of its first level at most (16^3)
+constexpr int kSmallThreads = 1024;
+constexpr size_t kSmallSmem = 200 * 1024;   // shared memory bound (bytes)
+struct SmallCycle {
+  int nl;
+  Dims d[kSmallMaxL];
+  float inv_h2[kSmallMaxL];
+  float a[kSmallMaxL][16], b[kSmallMaxL][16];  // folded Chebyshev constants per level and step
+  float c1[16];
+  int degree;
+  int nc;           // unknowns of the coarsest level
+  const float* G;   // its nc x nc pseudo-inverse (FP32, row-major)
+};
+size_t small_cycle_smem(const SmallCycle& P);
+// e_out = V-cycle(r_in) on level 0 of P (device buffers of level 0's size)
+cudaError_t launch_small_vcycle(cudaStream_t st, const SmallCycle& P, const float* r_in, float* e_out);
 template <typename T>
 cudaError_t launch_sum(cudaStream_t st, long long n, const T* x, double* partials_sum,
                        double* partials_sq);

@@ -43,6 +43,34 @@ gbmg_status smooth_pass(gbmg_ctx* c, int l, T*& e, T*& eo, const T* r, T* dv, bo
   return GBMG_OK;
 }
 
+// With the fused path on, the levels from l down, when they fit in shared memory, run
+// as one single-CTA kernel (bit-identical to the chain below).
+bool small_cycle_from(const gbmg_ctx* c, int l, SmallCycle* out) {
+  if (!c->o.fused || c->o.smoother != GBMG_SMOOTH_CHEBYSHEV || c->o.degree > 16) return false;
+  const int nl = c->L - l;
+  if (nl < 2 || nl > kSmallMaxL || ncell(c->lv[l].d) > kSmallCells) return false;
+  SmallCycle P{};
+  P.nl = nl;
+  P.degree = c->o.degree;
+  for (int k = 0; k < c->o.degree; ++k) P.c1[k] = (float)c->cc1[k];
+  for (int i = 0; i < nl; ++i) {
+    const Level& L = c->lv[l + i];
+    P.d[i] = L.d;
+    P.inv_h2[i] = (float)(1.0 / (L.h * L.h));
+    for (int k = 0; k < c->o.degree; ++k) {
+      double a, b;
+      cheb_constants(c->cc2[k], L.h, a, b);
+      P.a[i][k] = (float)a;
+      P.b[i][k] = (float)b;
+    }
+  }
+  P.nc = c->nc;
+  P.G = c->G32;
+  if (small_cycle_smem(P) > kSmallSmem) return false;
+  if (out) *out = P;
+  return true;
+}
+
 // V-cycle (Sec. 2.3) on level l for A_l e = r, one kernel per operation.  e / eo are
 // the level's ping-pong buffers; on return e points at the result.
 template <typename T>
@@ -52,6 +80,13 @@ gbmg_status vcycle_unfused(gbmg_ctx* c, int l, T*& e, T*& eo, const T* r) {
     TRY(launch_coarse_matvec<T>(c->stream, c->nc, coarse_G<T>(c), r, e));
     return GBMG_OK;
   }
+  if constexpr (sizeof(T) == 4) {
+    SmallCycle P;
+    if (small_cycle_from(c, l, &P)) {
+      TRY(launch_small_vcycle(c->stream, P, r, e));
+      return GBMG_OK;
+    }
+  }
   T* dv = (T*)L.dv;
   TRYS(smooth_pass<T>(c, l, e, eo, r, dv, false));
   const T inv_h2 = (T)(1.0 / (L.h * L.h));
@@ -60,7 +95,8 @@ gbmg_status vcycle_unfused(gbmg_ctx* c, int l, T*& e, T*& eo, const T* r) {
   TRY(launch_restrict<T>(c->stream, L.d, (const T*)L.t, (T*)C.r));
   T* ce = (T*)C.e;
   T* ceo = (T*)C.e2;
-  if (l + 1 < c->L - 1) TRY(cudaMemsetAsync(ce, 0, (size_t)ncell(C.d) * sizeof(T), c->stream));
+  if (l + 1 < c->L - 1 && !(sizeof(T) == 4 && small_cycle_from(c, l + 1, nullptr)))
+    TRY(cudaMemsetAsync(ce, 0, (size_t)ncell(C.d) * sizeof(T), c->stream));
   TRYS(vcycle_unfused<T>(c, l + 1, ce, ceo, (const T*)C.r));
   TRY(launch_prolong_add<T>(c->stream, C.d, ce, e));
   TRYS(smooth_pass<T>(c, l, e, eo, r, dv, true));
@@ -86,7 +122,8 @@ gbmg_status vcycle_fused(gbmg_ctx* c, int l, float*& e, const float* r) {
   if (!level_fused(c, l)) {
     float* ee = (float*)L.e;
     float* eo = (float*)L.e2;
-    if (l < c->L - 1) TRY(cudaMemsetAsync(ee, 0, (size_t)ncell(L.d) * sizeof(float), c->stream));
+    if (l < c->L - 1 && !small_cycle_from(c, l, nullptr))
+      TRY(cudaMemsetAsync(ee, 0, (size_t)ncell(L.d) * sizeof(float), c->stream));
     TRYS(vcycle_unfused<float>(c, l, ee, eo, r));
     e = ee;
     return GBMG_OK;
