@@ -26,6 +26,7 @@
 #include "dfk.cuh"
 #include "kernels.h"
 #include "legs.cuh"
+#include "small_cycle.cuh"
 #include "solver.h"
 #include "stencil.cuh"
 
@@ -79,6 +80,7 @@ struct BProb {
   int c0, nch;      // first level-0 chunk and count
   unsigned fmask;   // bit l: level l runs the fused legs
   int dffused;      // the finest level runs the fused double-float update (even nx)
+  int ls;           // first level of the single-CTA bottom cycle (levels ls .. L-1), 0: none
 };
 
 struct BDesc {
@@ -98,7 +100,9 @@ struct BDesc {
   double* dfpart;                // per double-float item: partial sum of r^2
   double* dfpart2;               // per double-float item: partial sum of (F - m)^2 (first residual)
   unsigned perop;                // bit l: some problem runs level l per operation (not the coarsest)
-  unsigned coarse;               // bit l: some problem's coarsest level is l
+  unsigned coarse;               // bit l: some problem's coarsest level is l (outside a bottom cycle)
+  const SmallCycle* small;       // per problem: parameters of its bottom cycle (ls > 0)
+  int anysmall;                  // some problem runs a bottom cycle
   int* phicur;                   // per problem: 0 = phi, 1 = phi2 holds the current iterate
   BProb* p;
   // chunk tables per level: problem index and first cell
@@ -402,7 +406,9 @@ __global__ void __launch_bounds__(BT, 1) k_batched_solve(BDesc B) {
     // down: levels 0 .. maxL-2, then the coarsest solves
     for (int l = 0; l + 1 < B.maxL; ++l) {
       // per-operation levels (smaller than 16^3, or every level for V = 0)
-      auto smoothed = [&](const BProb& P, int lv) { return lv < P.L - 1 && !(V > 0 && lv_fused(P, lv)); };
+      auto smoothed = [&](const BProb& P, int lv) {
+        return lv < P.L - 1 && !(V > 0 && lv_fused(P, lv)) && !(P.ls > 0 && lv >= P.ls);
+      };
       if constexpr (V > 0) fused_down<V>(B, l, smf);
       const bool perop = V == 0 || (B.perop >> l & 1u);
       bool cur_a = true;  // current e in ea
@@ -465,13 +471,15 @@ __global__ void __launch_bounds__(BT, 1) k_batched_solve(BDesc B) {
               P.r[lv][I] = fw3(yv[0], yv[1], yv[2]);
             });
       }
-      grid.sync();
+      // (a level without fused or per-operation work, below every problem's bottom-cycle
+      // start, has nothing to publish)
+      if ((V > 0 && B.dtot[l] > 0) || perop) grid.sync();
       // coarsest solves of the problems whose hierarchy ends at level l + 1
       if (B.coarse >> (l + 1) & 1u) {
         const int warps = blockDim.x / 32, lane = threadIdx.x & 31;
         for (int pi = blockIdx.x; pi < B.count; pi += gridDim.x) {
           const BProb& P = B.p[pi];
-          if (B.status[pi] != ST_ACTIVE || P.L - 1 != l + 1) continue;
+          if (B.status[pi] != ST_ACTIVE || P.L - 1 != l + 1 || P.ls > 0) continue;
           const float* r = P.r[l + 1];
           float* e = P.ea[l + 1];
           for (int row = threadIdx.x / 32; row < P.nc; row += warps) {
@@ -485,12 +493,25 @@ __global__ void __launch_bounds__(BT, 1) k_batched_solve(BDesc B) {
         grid.sync();
       }
     }
+    // bottom cycles: the levels of each problem that fit in shared memory, one CTA per
+    // problem (its correction at level ls lands in ea, where final_e reads it)
+    if (V > 0 && B.anysmall) {
+      for (int pi = blockIdx.x; pi < B.count; pi += gridDim.x) {
+        const BProb& P = B.p[pi];
+        if (B.status[pi] != ST_ACTIVE || P.ls == 0) continue;
+        smallc::block_vcycle(B.small[pi], P.r[P.ls], P.ea[P.ls], smf);
+        __syncthreads();
+      }
+      grid.sync();
+    }
     // up: levels maxL-2 .. 0.  Per operation: pre-smoothing from zero leaves e in eb
     // when V is odd and in ea when V is even; V more steps then always end in ea,
     // which is where the coarser level's correction is read from and where the
     // coarsest solve writes.  Fused levels end in eb (final_e).
     for (int l = B.maxL - 2; l >= 0; --l) {
-      auto smoothed = [&](const BProb& P, int lv) { return lv < P.L - 1 && !(V > 0 && lv_fused(P, lv)); };
+      auto smoothed = [&](const BProb& P, int lv) {
+        return lv < P.L - 1 && !(V > 0 && lv_fused(P, lv)) && !(P.ls > 0 && lv >= P.ls);
+      };
       if constexpr (V > 0) fused_up<V>(B, l, smf);
       const bool perop = V == 0 || (B.perop >> l & 1u);
       bool cur_a = (Vd % 2) == 0;
@@ -502,7 +523,7 @@ __global__ void __launch_bounds__(BT, 1) k_batched_solve(BDesc B) {
           float* e = cur_a ? P.ea[lv] : P.eb[lv];
           e[i] = t_add(e[i], prolong_value(final_e(P, lv + 1), P.d[lv + 1], x, y, z));
         });
-      grid.sync();
+      if ((V > 0 && B.utot[l] > 0) || perop) grid.sync();
       for (int k = 0; perop && k < Vd; ++k) {
         const float c1 = B.c1[k];
         const float a = B.ca[l][k], b = B.cb[l][k];
@@ -809,18 +830,30 @@ extern "C" gbmg_status mg_batch_create(gbmg_batch** out, gbmg_ctx* const* ctxs, 
   std::vector<long long> doff((size_t)maxL * (count + 1), 0), uoff((size_t)maxL * (count + 1), 0);
   std::vector<int> dfoff(count + 1, 0);
   long long phi2_cells = 0;
+  // bottom cycles: from the first level below the finest whose sub-hierarchy fits in
+  // shared memory (fused degrees only); those levels leave the fused and per-operation
+  // phases
+  std::vector<SmallCycle> small(count);
   for (int i = 0; i < count; ++i) {
     const gbmg_ctx* c = b->ctx[i];
     BProb& P = b->hprob[i];
-    for (int l = 0; V > 0 && l + 1 < c->L; ++l) {
+    for (int l = 1; V > 0 && l + 1 < c->L; ++l)
+      if (small_cycle_params(c, l, &small[i])) {
+        P.ls = l;
+        D.anysmall = 1;
+        b->smem = std::max(b->smem, small_cycle_smem(small[i]));
+        break;
+      }
+    const int top = P.ls > 0 ? P.ls : c->L - 1;  // levels below top are fused or per operation
+    for (int l = 0; V > 0 && l < top; ++l) {
       const Dims d = c->lv[l].d;
       if (d.nx >= 16 && d.ny >= 16 && d.nz >= 16) P.fmask |= 1u << l;
     }
     P.dffused = V > 0 && c->lv[0].d.nx % 2 == 0;
     if (P.dffused) phi2_cells += ncell(c->lv[0].d);
-    for (int l = 0; l + 1 < c->L; ++l)
+    for (int l = 0; l < top; ++l)
       if (!(P.fmask >> l & 1u)) D.perop |= 1u << l;
-    D.coarse |= 1u << (c->L - 1);
+    if (P.ls == 0) D.coarse |= 1u << (c->L - 1);
   }
   for (int l = 0; l < maxL; ++l)
     for (int i = 0; i < count; ++i) {
@@ -863,11 +896,13 @@ extern "C" gbmg_status mg_batch_create(gbmg_batch** out, gbmg_ctx* const* ctxs, 
     const size_t oDfp = take2(sizeof(double) * (size_t)std::max(dfoff[count], 1));
     const size_t oDfp2 = take2(sizeof(double) * (size_t)std::max(dfoff[count], 1));
     const size_t oCur = take2(sizeof(int) * count), oCoef = take2(sizeof(legs::Coef) * maxL);
+    const size_t oSmall = take2(sizeof(SmallCycle) * count);
     e = cudaMalloc((void**)&b->mem2, off2);
     if (e == cudaSuccess) e = cudaMemcpy(b->mem2 + oDoff, doff.data(), sizeof(long long) * doff.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->mem2 + oUoff, uoff.data(), sizeof(long long) * uoff.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->mem2 + oDf, dfoff.data(), sizeof(int) * dfoff.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->mem2 + oCoef, coef.data(), sizeof(legs::Coef) * maxL, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->mem2 + oSmall, small.data(), sizeof(SmallCycle) * count, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
       delete b;
       return cuda_fail(e, "mg_batch_create: fused-phase tables");
@@ -890,6 +925,7 @@ extern "C" gbmg_status mg_batch_create(gbmg_batch** out, gbmg_ctx* const* ctxs, 
     D.dfpart2 = reinterpret_cast<double*>(b->mem2 + oDfp2);
     D.phicur = reinterpret_cast<int*>(b->mem2 + oCur);
     D.coef = reinterpret_cast<const legs::Coef*>(b->mem2 + oCoef);
+    D.small = reinterpret_cast<const SmallCycle*>(b->mem2 + oSmall);
   }
   if (b->smem > 0) {
     e = cudaFuncSetAttribute(b->kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);

@@ -46,7 +46,15 @@ gbmg_status smooth_pass(gbmg_ctx* c, int l, T*& e, T*& eo, const T* r, T* dv, bo
 // With the fused path on, the levels from l down, when they fit in shared memory, run
 // as one single-CTA kernel (bit-identical to the chain below).
 bool small_cycle_from(const gbmg_ctx* c, int l, SmallCycle* out) {
-  if (!c->o.fused || c->o.smoother != GBMG_SMOOTH_CHEBYSHEV || c->o.degree > 16) return false;
+  return c->o.fused && small_cycle_params(c, l, out);
+}
+
+}  // namespace
+
+// Parameters of the single-CTA bottom cycle from level l of c's hierarchy, when the
+// Chebyshev smoother runs and levels l .. L-1 fit (false otherwise).
+bool gbmg::small_cycle_params(const gbmg_ctx* c, int l, SmallCycle* out) {
+  if (c->o.smoother != GBMG_SMOOTH_CHEBYSHEV || c->o.degree > 16) return false;
   const int nl = c->L - l;
   if (nl < 2 || nl > kSmallMaxL || ncell(c->lv[l].d) > kSmallCells) return false;
   SmallCycle P{};
@@ -70,6 +78,8 @@ bool small_cycle_from(const gbmg_ctx* c, int l, SmallCycle* out) {
   if (out) *out = P;
   return true;
 }
+
+namespace {
 
 // V-cycle (Sec. 2.3) on level l for A_l e = r, one kernel per operation.  e / eo are
 // the level's ping-pong buffers; on return e points at the result.

@@ -34,6 +34,8 @@ gbmg_status curv_solve(gbmg_ctx* c, const double* F, double* phi, double tol, in
 bool dense_pinv(int n, const std::vector<double>& Lm, const std::vector<double>& w, std::vector<double>& G);
 std::vector<double> dense_flat(Dims d, double h);
 void chebyshev_schedule(int degree, double alpha, std::vector<double>& c1, std::vector<double>& c2);
+// Parameters of the single-CTA bottom cycle from level l (false when it does not apply).
+bool small_cycle_params(const gbmg_ctx* c, int l, SmallCycle* out);
 
 // Slots of the device scalar area gbmg_ctx::scal.
 enum Scal {
