@@ -29,39 +29,70 @@ __device__ __forceinline__ Nbrs6<float> nbrs(const float* u, Dims d, int x, int 
 }
 __device__ __forceinline__ float nsum6(const Nbrs6<float>& n) { return nbr_sum(n.xm, n.xp, n.ym, n.yp, n.zm, n.zp); }
 
-__device__ __forceinline__ void cell_of(Dims d, int i, int& x, int& y, int& z) {
-  x = i % d.nx;
-  y = (i / d.nx) % d.ny;
-  z = i / (d.nx * d.ny);
-}
 
-// The whole sub-cycle by the calling CTA (any block size, a multiple of 32); sm:
-// small_cycle_smem(P) bytes of shared memory.  Ends with the result stored (no barrier
-// after the last store).
-__device__ __forceinline__ void block_vcycle(const SmallCycle& P, const float* __restrict__ r_in,
-                                             float* __restrict__ e_out, float* sm) {
+// Cells i = tid, tid + nt, ... of a level with their (x, y, z), advanced by mixed-radix
+// addition of nt instead of a division per cell.
+struct Walk {
+  int i, x, y, z;
+  int sx, sy, sz;
+  __device__ __forceinline__ Walk(Dims d, int tid, int nt) : i(tid) {
+    x = tid % d.nx;
+    const int q = tid / d.nx;
+    y = q % d.ny;
+    z = q / d.ny;
+    sx = nt % d.nx;
+    const int q2 = nt / d.nx;
+    sy = q2 % d.ny;
+    sz = q2 / d.ny;
+  }
+  __device__ __forceinline__ void next(Dims d, int nt) {
+    i += nt;
+    x += sx;
+    int c = 0;
+    if (x >= d.nx) {
+      x -= d.nx;
+      c = 1;
+    }
+    y += sy + c;
+    c = 0;
+    if (y >= d.ny) {
+      y -= d.ny;
+      c = 1;
+    }
+    z += sz + c;
+  }
+};
+
+// The whole sub-cycle by the calling CTA (any block size, a multiple of 32), NL levels;
+// sm: small_cycle_smem(P) bytes of shared memory.  Ends with the result stored (no
+// barrier after the last store).
+template <int NL>
+__device__ __forceinline__ void block_vcycle_n(const SmallCycle& P, const float* __restrict__ r_in,
+                                               float* __restrict__ e_out, float* sm) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  // per level: r, e, e2, d, t (the coarsest: r, e)
-  float *R[kSmallMaxL], *E[kSmallMaxL], *E2[kSmallMaxL], *DV[kSmallMaxL], *T[kSmallMaxL];
+  // per level: r, e, e2, d, t (the coarsest: r, e), as offsets into sm
+  int oR[NL], oE[NL], oE2[NL], oDV[NL], oT[NL];
   {
-    float* p = sm;
-    for (int l = 0; l < P.nl; ++l) {
+    int p = 0;
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
       const int n = ncell(P.d[l]);
-      R[l] = p;
-      E[l] = p + n;
+      oR[l] = p;
+      oE[l] = p + n;
       p += 2 * n;
-      if (l < P.nl - 1) {
-        E2[l] = p;
-        DV[l] = p + n;
-        T[l] = p + 2 * n;
+      oE2[l] = oDV[l] = oT[l] = 0;
+      if (l < NL - 1) {
+        oE2[l] = p;
+        oDV[l] = p + n;
+        oT[l] = p + 2 * n;
         p += 3 * n;
       }
     }
   }
   const int n0 = ncell(P.d[0]);
   for (int i = tid; i < n0; i += nt) {
-    R[0][i] = r_in[i];
-    E[0][i] = 0.f;
+    sm[oR[0] + i] = r_in[i];
+    sm[oE[0] + i] = 0.f;
   }
   __syncthreads();
   auto smooth = [&](int l) {
@@ -69,86 +100,106 @@ __device__ __forceinline__ void block_vcycle(const SmallCycle& P, const float* _
     const int n = ncell(d);
     for (int k = 0; k < P.degree; ++k) {
       const float a = P.a[l][k], b = P.b[l][k], c1 = P.c1[k];
-      for (int i = tid; i < n; i += nt) {
-        int x, y, z;
-        cell_of(d, i, x, y, z);
-        const float c = E[l][i];
-        float dv = c1 == 0.f ? 0.f : DV[l][i];
-        E2[l][i] = cheb_step(c, R[l][i], nsum6(nbrs(E[l], d, x, y, z, i)), c, dv, a, b, c1);
-        DV[l][i] = dv;
+      const float* E = sm + oE[l];
+      float* E2 = sm + oE2[l];
+      float* DV = sm + oDV[l];
+      const float* R = sm + oR[l];
+      for (Walk w(d, tid, nt); w.i < n; w.next(d, nt)) {
+        const int i = w.i;
+        const float c = E[i];
+        float dv = c1 == 0.f ? 0.f : DV[i];
+        E2[i] = cheb_step(c, R[i], nsum6(nbrs(E, d, w.x, w.y, w.z, i)), c, dv, a, b, c1);
+        DV[i] = dv;
       }
       __syncthreads();
-      float* s = E[l];
-      E[l] = E2[l];
-      E2[l] = s;
+      const int t = oE[l];
+      oE[l] = oE2[l];
+      oE2[l] = t;
     }
   };
   // down: pre-smoothing, residual, restriction
-  for (int l = 0; l + 1 < P.nl; ++l) {
+#pragma unroll
+  for (int l = 0; l + 1 < NL; ++l) {
     smooth(l);
     const Dims d = P.d[l];
     const int n = ncell(d);
-    for (int i = tid; i < n; i += nt) {
-      int x, y, z;
-      cell_of(d, i, x, y, z);
-      T[l][i] = resid_from_sum(R[l][i], nsum6(nbrs(E[l], d, x, y, z, i)), E[l][i], P.inv_h2[l]);
+    {
+      const float* E = sm + oE[l];
+      const float* R = sm + oR[l];
+      float* T = sm + oT[l];
+      const float ih2 = P.inv_h2[l];
+      for (Walk w(d, tid, nt); w.i < n; w.next(d, nt))
+        T[w.i] = resid_from_sum(R[w.i], nsum6(nbrs(E, d, w.x, w.y, w.z, w.i)), E[w.i], ih2);
     }
     __syncthreads();
     const Dims dc = P.d[l + 1];
     const int nc = ncell(dc);
-    for (int i = tid; i < nc; i += nt) {
-      int X, Y, Z;
-      cell_of(dc, i, X, Y, Z);
-      int xs[3], ys[3], zs[3];
+    {
+      const float* T = sm + oT[l];
+      float* Rc = sm + oR[l + 1];
+      float* Ec = sm + oE[l + 1];
+      for (Walk w(dc, tid, nt); w.i < nc; w.next(dc, nt)) {
+        int xs[3], ys[3], zs[3];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        xs[k] = wrapi(2 * X + k - 1, d.nx);
-        ys[k] = wrapi(2 * Y + k - 1, d.ny);
-        zs[k] = wrapi(2 * Z + k - 1, d.nz);
+        for (int k = 0; k < 3; ++k) {
+          xs[k] = wrapi(2 * w.x + k - 1, d.nx);
+          ys[k] = wrapi(2 * w.y + k - 1, d.ny);
+          zs[k] = wrapi(2 * w.z + k - 1, d.nz);
+        }
+        float yv[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          float zv[3];
+#pragma unroll
+          for (int b = 0; b < 3; ++b)
+            zv[b] = fw3(T[(int)lin(d, xs[a], ys[b], zs[0])], T[(int)lin(d, xs[a], ys[b], zs[1])],
+                        T[(int)lin(d, xs[a], ys[b], zs[2])]);
+          yv[a] = fw3(zv[0], zv[1], zv[2]);
+        }
+        Rc[w.i] = fw3(yv[0], yv[1], yv[2]);
+        if (l + 2 < NL) Ec[w.i] = 0.f;
       }
-      float yv[3];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        float zv[3];
-#pragma unroll
-        for (int b = 0; b < 3; ++b)
-          zv[b] = fw3(T[l][(int)lin(d, xs[a], ys[b], zs[0])], T[l][(int)lin(d, xs[a], ys[b], zs[1])],
-                      T[l][(int)lin(d, xs[a], ys[b], zs[2])]);
-        yv[a] = fw3(zv[0], zv[1], zv[2]);
-      }
-      R[l + 1][i] = fw3(yv[0], yv[1], yv[2]);
-      if (l + 2 < P.nl) E[l + 1][i] = 0.f;
     }
     __syncthreads();
   }
   // coarsest: e = G r, one warp per row, lanes stride the columns
   {
-    const int lc = P.nl - 1;
+    const float* R = sm + oR[NL - 1];
+    float* E = sm + oE[NL - 1];
     const int lane = tid & 31;
     for (int row = tid >> 5; row < P.nc; row += nt >> 5) {
       float acc = 0.f;
-      for (int j = lane; j < P.nc; j += 32) acc = t_fma(P.G[(long long)row * P.nc + j], R[lc][j], acc);
+      for (int j = lane; j < P.nc; j += 32) acc = t_fma(P.G[(long long)row * P.nc + j], R[j], acc);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) acc = t_add(acc, __shfl_xor_sync(0xffffffffu, acc, o));
-      if (lane == 0) E[lc][row] = acc;
+      if (lane == 0) E[row] = acc;
     }
     __syncthreads();
   }
   // up: prolongation + correction, post-smoothing
-  for (int l = P.nl - 2; l >= 0; --l) {
+#pragma unroll
+  for (int l = NL - 2; l >= 0; --l) {
     const Dims d = P.d[l], dc = P.d[l + 1];
     const int n = ncell(d);
-    for (int i = tid; i < n; i += nt) {
-      int x, y, z;
-      cell_of(d, i, x, y, z);
-      E[l][i] = t_add(E[l][i], prolong_value(E[l + 1], dc, x, y, z));
+    {
+      float* E = sm + oE[l];
+      const float* Ec = sm + oE[l + 1];
+      for (Walk w(d, tid, nt); w.i < n; w.next(d, nt)) E[w.i] = t_add(E[w.i], prolong_value(Ec, dc, w.x, w.y, w.z));
     }
     __syncthreads();
     smooth(l);
   }
-  for (int i = tid; i < n0; i += nt) e_out[i] = E[0][i];
+  for (int i = tid; i < n0; i += nt) e_out[i] = sm[oE[0] + i];
 }
 
+__device__ __forceinline__ void block_vcycle(const SmallCycle& P, const float* __restrict__ r_in,
+                                             float* __restrict__ e_out, float* sm) {
+  switch (P.nl) {
+    case 2: block_vcycle_n<2>(P, r_in, e_out, sm); break;
+    case 3: block_vcycle_n<3>(P, r_in, e_out, sm); break;
+    default: block_vcycle_n<4>(P, r_in, e_out, sm); break;
+  }
+}
 
 }  // namespace smallc
 }  // namespace gbmg
