@@ -331,3 +331,25 @@ def test_sym_adjoint_matches_oracle(gb):
 def test_sym_option_needs_the_curvilinear_operator(gb):
     with pytest.raises(gb.GbmgError):
         gb.Solver((16, 16, 16), curv_sym=True)
+
+
+def test_curvilinear_host_buffer_entry_points(gb):
+    # mg_solve_host (page-locked buffers read in place by the conversion kernels) and
+    # mg_solve_host_sequence (copies overlapped, warm start on the device) on the
+    # curvilinear operator equal the device-buffer solves
+    shape = (16, 16, 16)
+    psi = psi_field(shape, 41)
+    s = make(gb, shape, psi)
+    d0, d1 = grf(shape, 42), grf(shape, 43)
+    ref0, st0 = s.solve(to_dev(d0), tol=1e-9, max_vcycles=100)
+    ref1, st1 = s.solve(to_dev(d1), ref0.clone(), tol=1e-9, max_vcycles=100)
+    src = torch.from_numpy(d0.copy()).pin_memory()
+    out = torch.zeros(shape, dtype=torch.float64).pin_memory()
+    _, st = s.solve_host(src, out, tol=1e-9, max_vcycles=100)
+    assert st.cycles == st0.cycles
+    np.testing.assert_array_equal(out.numpy(), ref0.cpu().numpy())
+    outs = [torch.empty(shape, dtype=torch.float64).pin_memory() for _ in range(2)]
+    sts = s.solve_host_sequence([src, torch.from_numpy(d1.copy()).pin_memory()], outs, tol=1e-9, max_vcycles=100)
+    assert [x.cycles for x in sts] == [st0.cycles, st1.cycles]
+    np.testing.assert_array_equal(outs[0].numpy(), ref0.cpu().numpy())
+    np.testing.assert_array_equal(outs[1].numpy(), ref1.cpu().numpy())
