@@ -40,7 +40,7 @@ constexpr int CHUNK = 4096;      // default tile (chunk) size in cells
 constexpr int MINCHUNK = 1024;   // smallest tile the tables are sized for
 constexpr int MAXCHUNK = 65536;
 constexpr int BT = 384;          // block size (the fused legs' thread-column layout)
-constexpr int DFZC = 16;         // z planes per item of the fused double-float phase
+constexpr int DFZC = 32;         // z planes per item of the fused double-float phase
 
 // tiles of the fused device code at BT threads
 // (columns of 3 pairs for both legs: this kernel holds the state of every phase under
