@@ -365,14 +365,15 @@ __global__ void k_curv_dense(Dims d, CurvCoef cf, int form, double* __restrict__
 
 // ---- double-float residual of the outer defect correction on the finest level ----
 
-// DF difference a - b of two double-float values.
+// DF difference a - b of two double-float values, as an unnormalised pair (s, e):
+// s = RN(a.hi - b.hi) with its exact error, plus the low parts' difference in e.  Its
+// only use is the product with an FP32 weight in df_acc_prod, where e enters one FP32
+// multiply, so the pair is not renormalised.
 __device__ __forceinline__ float2 df_sub(float2 a, float2 b) {
   float s, e;
   two_sum(a.x, -b.x, s, e);
   e += a.y - b.y;
-  float h, l;
-  quick_two_sum(s, e, h, l);
-  return make_float2(h, l);
+  return make_float2(s, e);
 }
 
 // acc += w * v exactly up to the rounding of the small terms (w float, v double-float).
