@@ -326,11 +326,15 @@ def test_error_statuses(gb):
 
 
 @pytest.mark.parametrize("shape", [(32, 32, 32), (64, 64, 64), (32, 48, 64), (96, 96, 96)])
-@pytest.mark.parametrize("degree", [2, 3, 4])
-def test_fused_vcycle_bit_identical_to_unfused(gb, shape, degree):
-    # the temporally blocked kernels round exactly like the one-kernel-per-operation chain
+@pytest.mark.parametrize("degree", [1, 2, 3, 4])
+@pytest.mark.parametrize("fused", [1, 2])
+def test_fused_vcycle_bit_identical_to_unfused(gb, shape, degree, fused):
+    # the temporally blocked kernels and the single-CTA bottom cycle round exactly like
+    # the one-kernel-per-operation chain (fused 1: blocked from 2^18 cells, the bottom
+    # cycle from the first level of at most 16^3; fused 2: blocked on every level of at
+    # least 16^3)
     r = to_dev(grf(shape, 19), torch.float32)
-    a = gb.Solver(shape, prec="mixed", fused=2, degree=degree).vcycle(r)
+    a = gb.Solver(shape, prec="mixed", fused=fused, degree=degree).vcycle(r)
     b = gb.Solver(shape, prec="mixed", fused=False, degree=degree).vcycle(r)
     torch.cuda.synchronize()
     assert torch.equal(a, b)
