@@ -1,7 +1,8 @@
 """Full-size parity checks of each workload in the launch configuration bench.py uses (GPU).
 
-512^3 warm-started sequence, 256^3 differentiable flat solve, 256^3 moving-mesh solve
-with its adjoint, and the 48-problem batch.  The oracle computes what it can at these
+512^3 warm-started sequence (device buffers, and host buffers through the sequence entry
+point), 256^3 differentiable flat solve, 256^3 moving-mesh solve with its adjoint, and the
+48-problem batch.  The oracle computes what it can at these
 sizes in seconds (FFT solves, one application of the FP64 curvilinear operator);
 the rest is checked through properties that hold at any size (residual of the FP64
 operator, central finite differences of the GPU forward map).
@@ -38,6 +39,26 @@ def test_warm_sequence_512(gb):
     assert max(cycles[1:]) < cycles[0]   # warm starts save cycles (Eq. kwarm)
     ref = flat.fft_solve(F)
     assert rel_l2(phi.cpu().numpy(), ref) < 1e-6
+
+
+def test_host_sequence_512(gb):
+    # the e2e path of the bench: page-locked sources in, page-locked solutions out, warm
+    # starts on the device; equal to device-buffer solves of the same sequence, and the
+    # last solution matches the FFT solve
+    n, T = 512, 3
+    d0, eta = grf(n, 2), grf(n, 3)
+    Fs = [d0 + (0.05 * t) * eta for t in range(T)]
+    s = gb.Solver(n)
+    src = [torch.from_numpy(F).pin_memory() for F in Fs]
+    outs = [torch.empty((n, n, n), dtype=torch.float64).pin_memory() for _ in range(T)]
+    sts = s.solve_host_sequence(src, outs, tol=1e-6, max_vcycles=40)
+    assert all(st.status == 0 and st.rel_res <= 1e-6 for st in sts)
+    phi = torch.zeros((n, n, n), dtype=torch.float64, device="cuda")
+    for t in range(T):
+        _, st = s.solve(src[t].cuda(), phi, tol=1e-6, max_vcycles=40)
+        assert st.cycles == sts[t].cycles
+        assert torch.equal(phi.cpu(), outs[t])
+    assert rel_l2(outs[-1].numpy(), flat.fft_solve(Fs[-1])) < 1e-6
 
 
 def test_differentiable_flat_256(gb):
