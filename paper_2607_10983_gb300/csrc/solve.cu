@@ -468,49 +468,63 @@ extern "C" gbmg_status mg_solve_host_sequence(gbmg_ctx* ctx, int count, const do
   cudaStream_t cs = ctx->stream, h2d = ctx->seq_h2d, d2h = ctx->seq_d2h;
   // the compute stream's earlier work (and whatever wrote the host buffers' device
   // views) comes first
-  TRY(cudaEventRecord(ev[6], cs));
-  TRY(cudaStreamWaitEvent(h2d, ev[6], 0));
-  TRY(cudaStreamWaitEvent(d2h, ev[6], 0));
-  TRY(cudaMemcpyAsync(ctx->seq_F[0], sources_host[0], bytes, cudaMemcpyHostToDevice, h2d));
-  TRY(cudaEventRecord(ev[0], h2d));
+  // any exit from here on first drains the copy streams, which may still read or write
+  // the caller's host buffers
+  auto drain = [&]() {
+    cudaStreamSynchronize(h2d);
+    cudaStreamSynchronize(d2h);
+  };
+#define STRY(call)                     \
+  do {                                 \
+    cudaError_t e_ = (call);           \
+    if (e_ != cudaSuccess) {           \
+      drain();                         \
+      return cuda_fail(e_, #call);     \
+    }                                  \
+  } while (0)
+  STRY(cudaEventRecord(ev[6], cs));
+  STRY(cudaStreamWaitEvent(h2d, ev[6], 0));
+  STRY(cudaStreamWaitEvent(d2h, ev[6], 0));
+  STRY(cudaMemcpyAsync(ctx->seq_F[0], sources_host[0], bytes, cudaMemcpyHostToDevice, h2d));
+  STRY(cudaEventRecord(ev[0], h2d));
   if (phi0_host) {
-    TRY(cudaMemcpyAsync(ctx->seq_phi[0], phi0_host, bytes, cudaMemcpyHostToDevice, h2d));
-    TRY(cudaEventRecord(ev[0], h2d));
+    STRY(cudaMemcpyAsync(ctx->seq_phi[0], phi0_host, bytes, cudaMemcpyHostToDevice, h2d));
+    STRY(cudaEventRecord(ev[0], h2d));
   } else {
-    TRY(cudaMemsetAsync(ctx->seq_phi[0], 0, bytes, cs));
+    STRY(cudaMemsetAsync(ctx->seq_phi[0], 0, bytes, cs));
   }
   gbmg_status worst = GBMG_OK;
   for (int t = 0; t < count; ++t) {
     const int k = t & 1, o = k ^ 1;
     // prefetch the next source into the other buffer once the solve that read it is done
     if (t + 1 < count) {
-      if (t >= 1) TRY(cudaStreamWaitEvent(h2d, ev[2 + o], 0));
-      TRY(cudaMemcpyAsync(ctx->seq_F[o], sources_host[t + 1], bytes, cudaMemcpyHostToDevice, h2d));
-      TRY(cudaEventRecord(ev[o], h2d));
+      if (t >= 1) STRY(cudaStreamWaitEvent(h2d, ev[2 + o], 0));
+      STRY(cudaMemcpyAsync(ctx->seq_F[o], sources_host[t + 1], bytes, cudaMemcpyHostToDevice, h2d));
+      STRY(cudaEventRecord(ev[o], h2d));
     }
     // solve t: source k, initial guess phi k (phi_{t-1}), result into phi o, whose
     // previous content (phi_{t-2}) must have been copied out
-    TRY(cudaStreamWaitEvent(cs, ev[k], 0));
-    if (t >= 2) TRY(cudaStreamWaitEvent(cs, ev[4 + o], 0));
+    STRY(cudaStreamWaitEvent(cs, ev[k], 0));
+    if (t >= 2) STRY(cudaStreamWaitEvent(cs, ev[4 + o], 0));
     gbmg_stats st;
     const gbmg_status s = solve_core(ctx, ctx->seq_F[k], ctx->seq_phi[k], ctx->seq_phi[o], tol, max_vcycles, st);
     if (s != GBMG_OK) {
-      cudaStreamSynchronize(h2d);
-      cudaStreamSynchronize(d2h);
+      drain();
       return s;
     }
-    TRY(cudaEventRecord(ev[2 + k], cs));
-    TRY(cudaEventRecord(ev[6], cs));
-    TRY(cudaStreamWaitEvent(d2h, ev[6], 0));
-    TRY(cudaMemcpyAsync(phi_host[t], ctx->seq_phi[o], bytes, cudaMemcpyDeviceToHost, d2h));
-    TRY(cudaEventRecord(ev[4 + o], d2h));
+    STRY(cudaEventRecord(ev[2 + k], cs));
+    STRY(cudaEventRecord(ev[6], cs));
+    STRY(cudaStreamWaitEvent(d2h, ev[6], 0));
+    STRY(cudaMemcpyAsync(phi_host[t], ctx->seq_phi[o], bytes, cudaMemcpyDeviceToHost, d2h));
+    STRY(cudaEventRecord(ev[4 + o], d2h));
     ctx->last = st;
     if (stats) stats[t] = st;
     if (st.status != GBMG_OK && worst == GBMG_OK) worst = (gbmg_status)st.status;
   }
-  TRY(cudaStreamSynchronize(ctx->seq_d2h));
-  TRY(cudaStreamSynchronize(ctx->seq_h2d));
-  TRY(cudaStreamSynchronize(cs));
+  STRY(cudaStreamSynchronize(ctx->seq_d2h));
+  STRY(cudaStreamSynchronize(ctx->seq_h2d));
+  STRY(cudaStreamSynchronize(cs));
+#undef STRY
   if (worst != GBMG_OK) g_last_error = std::string("mg_solve_host_sequence: ") + mg_status_string(worst);
   return worst;
 }
