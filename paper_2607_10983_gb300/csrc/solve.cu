@@ -418,10 +418,19 @@ extern "C" gbmg_status mg_solve_host(gbmg_ctx* ctx, const double* source_host, d
     TRY(cudaMalloc((void**)&ctx->stage_phi, bytes));
     ctx->owned.push_back(ctx->stage_phi);
   }
-  TRY(cudaMemcpyAsync(ctx->stage_F, source_host, bytes, cudaMemcpyHostToDevice, ctx->stream));
-  TRY(cudaMemcpyAsync(ctx->stage_phi, phi_inout_host, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  // an error exit first waits for the copies that may still read the host buffers
+  cudaError_t e = cudaMemcpyAsync(ctx->stage_F, source_host, bytes, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ctx->stage_phi, phi_inout_host, bytes, cudaMemcpyHostToDevice, ctx->stream);
+  if (e != cudaSuccess) {
+    cudaStreamSynchronize(ctx->stream);
+    return cuda_fail(e, "mg_solve_host: copy to the device");
+  }
   const gbmg_status s = mg_solve(ctx, ctx->stage_F, nullptr, ctx->stage_phi, tol, max_vcycles, stats);
-  if (s != GBMG_OK && s != GBMG_ERR_NOT_CONVERGED && s != GBMG_ERR_NONFINITE && s != GBMG_ERR_DIVERGED) return s;
+  if (s != GBMG_OK && s != GBMG_ERR_NOT_CONVERGED && s != GBMG_ERR_NONFINITE && s != GBMG_ERR_DIVERGED) {
+    cudaStreamSynchronize(ctx->stream);
+    return s;
+  }
   TRY(cudaMemcpyAsync(phi_inout_host, ctx->stage_phi, bytes, cudaMemcpyDeviceToHost, ctx->stream));
   TRY(cudaStreamSynchronize(ctx->stream));
   return s;
