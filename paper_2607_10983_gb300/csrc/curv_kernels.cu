@@ -507,6 +507,10 @@ __global__ void k_ratio(const double* a, const double* b, double* out) {
 //   Abar_J = Jbar J A^-1,  Abar_B = J <Bbar, A^-2> A^-1 - J (A^-1 Bbar A^-2 + A^-2 Bbar A^-1).
 // Writes S = Abar_J - Abar_B symmetrised for the Hessian stencils:
 // S_aa = Abar_aa, S_ab = Abar_ab + Abar_ba (a < b), packed xx, yy, zz, xy, xz, yz.
+// Precision: the differences that cancel (second differences of psi, differences of phi
+// and lam across faces and edges) are formed in FP64; the pointwise algebra of the 3 x 3
+// triad (adjugate, J, A^-1, A^-2 and the cotangent products) runs in FP32, A having its
+// eigenvalues in [1/2, 3/2] (FP64 arithmetic runs at a small fraction of the FP32 rate).
 __global__ void k_psibar_A(Dims d, const double* __restrict__ psi, const double* __restrict__ phi,
                            const double* __restrict__ lam, const double* __restrict__ delta,
                            const double* __restrict__ mw_dev, const double* __restrict__ slam_dev,
@@ -516,41 +520,47 @@ __global__ void k_psibar_A(Dims d, const double* __restrict__ psi, const double*
   const long long n = ncell(d);
   const Nbhd nb(d, x, y, z);
   const long long i = nb(0, 0, 0);
-  // triad at this cell
+  // triad at this cell: FP64 second differences, then FP32
   auto P = [&](int dx, int dy, int dz) { return psi[nb(dx, dy, dz)]; };
   const double ih2 = 1.0 / (h * h), iq = 0.25 / (h * h);
   const double c0 = P(0, 0, 0);
-  double A[3][3];
-  A[0][0] = 1.0 + (P(1, 0, 0) - 2.0 * c0 + P(-1, 0, 0)) * ih2;
-  A[1][1] = 1.0 + (P(0, 1, 0) - 2.0 * c0 + P(0, -1, 0)) * ih2;
-  A[2][2] = 1.0 + (P(0, 0, 1) - 2.0 * c0 + P(0, 0, -1)) * ih2;
-  A[0][1] = A[1][0] = (P(1, 1, 0) - P(1, -1, 0) - P(-1, 1, 0) + P(-1, -1, 0)) * iq;
-  A[0][2] = A[2][0] = (P(1, 0, 1) - P(1, 0, -1) - P(-1, 0, 1) + P(-1, 0, -1)) * iq;
-  A[1][2] = A[2][1] = (P(0, 1, 1) - P(0, 1, -1) - P(0, -1, 1) + P(0, -1, -1)) * iq;
-  double adj[3][3];
+  float A[3][3];
+  A[0][0] = (float)(1.0 + (P(1, 0, 0) - 2.0 * c0 + P(-1, 0, 0)) * ih2);
+  A[1][1] = (float)(1.0 + (P(0, 1, 0) - 2.0 * c0 + P(0, -1, 0)) * ih2);
+  A[2][2] = (float)(1.0 + (P(0, 0, 1) - 2.0 * c0 + P(0, 0, -1)) * ih2);
+  A[0][1] = A[1][0] = (float)((P(1, 1, 0) - P(1, -1, 0) - P(-1, 1, 0) + P(-1, -1, 0)) * iq);
+  A[0][2] = A[2][0] = (float)((P(1, 0, 1) - P(1, 0, -1) - P(-1, 0, 1) + P(-1, 0, -1)) * iq);
+  A[1][2] = A[2][1] = (float)((P(0, 1, 1) - P(0, 1, -1) - P(0, -1, 1) + P(0, -1, -1)) * iq);
+  float adj[3][3];
   adj[0][0] = A[1][1] * A[2][2] - A[1][2] * A[1][2];
   adj[1][1] = A[0][0] * A[2][2] - A[0][2] * A[0][2];
   adj[2][2] = A[0][0] * A[1][1] - A[0][1] * A[0][1];
   adj[0][1] = adj[1][0] = A[0][2] * A[1][2] - A[0][1] * A[2][2];
   adj[0][2] = adj[2][0] = A[0][1] * A[1][2] - A[1][1] * A[0][2];
   adj[1][2] = adj[2][1] = A[0][1] * A[0][2] - A[0][0] * A[1][2];
-  const double J = A[0][0] * adj[0][0] + A[0][1] * adj[0][1] + A[0][2] * adj[0][2];
-  double Ai[3][3], Ai2[3][3];
+  const float J = A[0][0] * adj[0][0] + A[0][1] * adj[0][1] + A[0][2] * adj[0][2];
+  const float iJ = 1.0f / J;
+  float Ai[3][3], Ai2[3][3];
+#pragma unroll
   for (int a = 0; a < 3; ++a)
-    for (int b = 0; b < 3; ++b) Ai[a][b] = adj[a][b] / J;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) Ai[a][b] = adj[a][b] * iJ;
+#pragma unroll
   for (int a = 0; a < 3; ++a)
+#pragma unroll
     for (int b = 0; b < 3; ++b) Ai2[a][b] = Ai[a][0] * Ai[0][b] + Ai[a][1] * Ai[1][b] + Ai[a][2] * Ai[2][b];
   // Bbar at this cell: faces a at i (own) and i - a (left neighbour's face)
   auto PH = [&](int dx, int dy, int dz) { return phi[nb(dx, dy, dz)]; };
   auto LA = [&](int dx, int dy, int dz) { return lam[nb(dx, dy, dz)]; };
   // face value of G^a_b[phi] * (lam_c - lam_{c+a}) / h on the a-face between c and c + a
+  const double ih = 1.0 / h;  // h is a power of two: multiplying by 1/h equals dividing by h
   auto fbar = [&](int a, int b, int cx, int cy, int cz) -> double {
     int px = cx, py = cy, pz = cz;
     shift(a, 1, px, py, pz);
-    const double Lam = (LA(cx, cy, cz) - LA(px, py, pz)) / h;
+    const double Lam = (LA(cx, cy, cz) - LA(px, py, pz)) * ih;
     double G;
     if (a == b) {
-      G = (PH(px, py, pz) - PH(cx, cy, cz)) / h;
+      G = (PH(px, py, pz) - PH(cx, cy, cz)) * ih;
     } else {
       int c1x = cx, c1y = cy, c1z = cz, c2x = cx, c2y = cy, c2z = cz;
       shift(b, 1, c1x, c1y, c1z);
@@ -558,16 +568,18 @@ __global__ void k_psibar_A(Dims d, const double* __restrict__ psi, const double*
       int d1x = px, d1y = py, d1z = pz, d2x = px, d2y = py, d2z = pz;
       shift(b, 1, d1x, d1y, d1z);
       shift(b, -1, d2x, d2y, d2z);
-      G = 0.25 * ((PH(c1x, c1y, c1z) - PH(c2x, c2y, c2z)) + (PH(d1x, d1y, d1z) - PH(d2x, d2y, d2z))) / h;
+      G = 0.25 * ((PH(c1x, c1y, c1z) - PH(c2x, c2y, c2z)) + (PH(d1x, d1y, d1z) - PH(d2x, d2y, d2z))) * ih;
     }
     return G * Lam;
   };
-  double Bb[3][3];
+  float Bb[3][3];
+#pragma unroll
   for (int a = 0; a < 3; ++a) {
     int mx = 0, my = 0, mz = 0;
     shift(a, -1, mx, my, mz);
+#pragma unroll
     for (int b = 0; b < 3; ++b)
-      Bb[a][b] = (sym && b != a) ? 0.0 : 0.5 * (fbar(a, b, 0, 0, 0) + fbar(a, b, mx, my, mz));
+      Bb[a][b] = (sym && b != a) ? 0.f : (float)(0.5 * (fbar(a, b, 0, 0, 0) + fbar(a, b, mx, my, mz)));
   }
   if (sym) {
     // symmetric variant: d<lam, S phi>/dC on the ab-edge at base e is
@@ -590,35 +602,41 @@ __global__ void k_psibar_A(Dims d, const double* __restrict__ psi, const double*
           acc += LA(ex, ey, ez) * (pp - pe) - LA(ax, ay, az) * (pb - pa) - LA(bx, by, bz) * (pa - pb) +
                  LA(px, py, pz) * (pe - pp);
         }
-        Bb[a][b] = 0.25 * 0.5 * acc / (h * h);
+        Bb[a][b] = (float)(0.25 * 0.5 * acc * (ih * ih));
       }
   }
   // Abar_B = J <Bbar, A^-2> A^-1 - J (A^-1 Bbar A^-2 + A^-2 Bbar A^-1)   (A symmetric)
-  double inner = 0.0;
+  float inner = 0.f;
+#pragma unroll
   for (int a = 0; a < 3; ++a)
+#pragma unroll
     for (int b = 0; b < 3; ++b) inner += Bb[a][b] * Ai2[a][b];
-  double T1[3][3], T2[3][3];
+  float T1[3][3], T2[3][3];
+#pragma unroll
   for (int a = 0; a < 3; ++a)
+#pragma unroll
     for (int b = 0; b < 3; ++b) {
       T1[a][b] = Bb[a][0] * Ai2[0][b] + Bb[a][1] * Ai2[1][b] + Bb[a][2] * Ai2[2][b];  // Bbar A^-2
       T2[a][b] = Bb[a][0] * Ai[0][b] + Bb[a][1] * Ai[1][b] + Bb[a][2] * Ai[2][b];     // Bbar A^-1
     }
   const double mw = mw_dev[0], sl = slam_dev[0];
-  const double Jbar = (delta[i] - mw) * (lam[i] - sl);
-  double Ab[3][3];
+  const float Jbar = (float)((delta[i] - mw) * (lam[i] - sl));
+  float Ab[3][3];
+#pragma unroll
   for (int a = 0; a < 3; ++a)
+#pragma unroll
     for (int b = 0; b < 3; ++b) {
-      const double t = Ai[a][0] * T1[0][b] + Ai[a][1] * T1[1][b] + Ai[a][2] * T1[2][b] +
-                       Ai2[a][0] * T2[0][b] + Ai2[a][1] * T2[1][b] + Ai2[a][2] * T2[2][b];
-      const double AbB = J * inner * Ai[a][b] - J * t;
+      const float t = Ai[a][0] * T1[0][b] + Ai[a][1] * T1[1][b] + Ai[a][2] * T1[2][b] +
+                      Ai2[a][0] * T2[0][b] + Ai2[a][1] * T2[1][b] + Ai2[a][2] * T2[2][b];
+      const float AbB = J * inner * Ai[a][b] - J * t;
       Ab[a][b] = Jbar * J * Ai[a][b] - AbB;
     }
   S[i] = Ab[0][0];
   S[n + i] = Ab[1][1];
   S[2 * n + i] = Ab[2][2];
-  S[3 * n + i] = Ab[0][1] + Ab[1][0];
-  S[4 * n + i] = Ab[0][2] + Ab[2][0];
-  S[5 * n + i] = Ab[1][2] + Ab[2][1];
+  S[3 * n + i] = (double)Ab[0][1] + (double)Ab[1][0];
+  S[4 * n + i] = (double)Ab[0][2] + (double)Ab[2][0];
+  S[5 * n + i] = (double)Ab[1][2] + (double)Ab[2][1];
 }
 
 // psi_bar = sum_a D_aa(S_aa) + sum_{a<b} D_ab(S_ab): the transpose of psi -> Hess psi,
