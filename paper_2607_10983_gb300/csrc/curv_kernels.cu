@@ -384,35 +384,38 @@ __device__ __forceinline__ void df_acc_prod(DfAcc& acc, float w, float2 v) {
   acc.c += pe + w * v.y;
 }
 
-// acc += h^2 (M u) (forward) with u double-float, every flux difference in double-float.
+// h * (flux F^a on the face between offset c and c + e_a) of a double-float u, as a
+// compensated pair (s, c): the five products of face_flux, each difference in
+// double-float, summed as in df_acc_prod.
 template <typename UF, typename BF>
-__device__ __forceinline__ void df_apply_M(DfAcc& acc, const UF& u, const BF& Bc, float sign) {
+__device__ __forceinline__ float2 df_face_flux(const UF& u, const BF& Bc, int a, int cx, int cy, int cz) {
+  int px = cx, py = cy, pz = cz;
+  shift(a, 1, px, py, pz);
+  const float wa = face_B<float>(Bc, a, a, cx, cy, cz);
+  const float2 v = df_sub(u(px, py, pz), u(cx, cy, cz));
+  DfAcc f;
+  f.s = wa * v.x;
+  f.c = __fmaf_rn(wa, v.x, -f.s) + wa * v.y;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-#pragma unroll
-    for (int side = 0; side < 2; ++side) {
-      // face between c and c + e_a; side 0: c = 0 (+), side 1: c = -e_a (-)
-      int cx = 0, cy = 0, cz = 0;
-      if (side) shift(a, -1, cx, cy, cz);
-      const float sg = side ? -sign : sign;
-      int px = cx, py = cy, pz = cz;
-      shift(a, 1, px, py, pz);
-      df_acc_prod(acc, sg * face_B<float>(Bc, a, a, cx, cy, cz), df_sub(u(px, py, pz), u(cx, cy, cz)));
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        if (b == a) continue;
-        const float w = sg * 0.25f * face_B<float>(Bc, a, b, cx, cy, cz);
-        int c1x = cx, c1y = cy, c1z = cz, c2x = cx, c2y = cy, c2z = cz;
-        shift(b, 1, c1x, c1y, c1z);
-        shift(b, -1, c2x, c2y, c2z);
-        int d1x = px, d1y = py, d1z = pz, d2x = px, d2y = py, d2z = pz;
-        shift(b, 1, d1x, d1y, d1z);
-        shift(b, -1, d2x, d2y, d2z);
-        df_acc_prod(acc, w, df_sub(u(c1x, c1y, c1z), u(c2x, c2y, c2z)));
-        df_acc_prod(acc, w, df_sub(u(d1x, d1y, d1z), u(d2x, d2y, d2z)));
-      }
-    }
+  for (int b = 0; b < 3; ++b) {
+    if (b == a) continue;
+    const float w = 0.25f * face_B<float>(Bc, a, b, cx, cy, cz);
+    int c1x = cx, c1y = cy, c1z = cz, c2x = cx, c2y = cy, c2z = cz;
+    shift(b, 1, c1x, c1y, c1z);
+    shift(b, -1, c2x, c2y, c2z);
+    int d1x = px, d1y = py, d1z = pz, d2x = px, d2y = py, d2z = pz;
+    shift(b, 1, d1x, d1y, d1z);
+    shift(b, -1, d2x, d2y, d2z);
+    df_acc_prod(f, w, df_sub(u(c1x, c1y, c1z), u(c2x, c2y, c2z)));
+    df_acc_prod(f, w, df_sub(u(d1x, d1y, d1z), u(d2x, d2y, d2z)));
   }
+  return make_float2(f.s, f.c);
+}
+
+// acc += sign * (s + c) of a face flux pair (sign +-1: exact).
+__device__ __forceinline__ void df_acc_face(DfAcc& acc, float2 f, float sign) {
+  acc.add(sign * f.x);
+  acc.c += sign * f.y;
 }
 
 // acc += sign * h^2 (M^T y) with y double-float.
@@ -675,9 +678,12 @@ __global__ void k_jscale(long long n, const float2* __restrict__ lam, const floa
 // and a chunk of z planes; the haloed planes (one cell of halo) of u and of the six
 // B components pass through a four-slot shared-memory ring, so every neighbour read
 // of the 19-point operator is a shared-memory load at a constant offset.  The
-// operator itself is the same template (apply_M_h2 / apply_MT_h2 / diag_M_h2) read
-// through shared-memory accessors.  Loads of the plane two ahead are issued before
-// the current plane is computed; one barrier per plane.
+// operator is the same template (face_flux / apply_MT_h2 / apply_S_h2 / diag_M_h2)
+// read through shared-memory accessors.  For M (form 0) each face flux is formed once
+// per plane and shared through shared memory (x and y faces) or carried in a register
+// (z faces), instead of once by each of the face's two cells.  Loads of the plane two
+// ahead (and of the cell's own J and right-hand side one plane ahead) are issued
+// before the current plane is computed; one barrier per plane, two for form 0.
 constexpr int CTX = 32, CTY = 8, CNT = CTX * CTY;
 constexpr int CSW = CTX + 2, CSH = CTY + 2, CSN = CSW * CSH;  // haloed plane
 constexpr int CQ = (CSN + CNT - 1) / CNT;                      // haloed cells per thread
@@ -718,16 +724,34 @@ struct PlaneRegs {
   float b[CQ][6];
 };
 
+// In-plane offsets of the thread's CQ haloed cells (periodic wrap in x and y), the same
+// for every plane of the chunk: computed once per CTA, before the z loop.
+struct PlaneIdx {
+  int off[CQ];
+};
+__device__ __forceinline__ PlaneIdx plane_idx(Dims d, int x0, int y0) {
+  PlaneIdx P;
+#pragma unroll
+  for (int k = 0; k < CQ; ++k) {
+    const int q = min((int)threadIdx.x + k * CNT, CSN - 1);
+    // full modulo: a tile may be wider than a coarse level
+    const int gx = ((x0 - 1 + q % CSW) % d.nx + d.nx) % d.nx, gy = ((y0 - 1 + q / CSW) % d.ny + d.ny) % d.ny;
+    P.off[k] = gy * d.nx + gx;
+  }
+  return P;
+}
+
+// Plane z in [-1, nz] (the chunk's planes and one on each side) wrapped onto the mesh.
 template <typename V>
-__device__ __forceinline__ void load_plane(Dims d, const V* __restrict__ u, const CurvCoef& cf, int x0, int y0, int z,
-                                           PlaneRegs<V>& R) {
-  const long long zo = (long long)(((z % d.nz) + d.nz) % d.nz) * d.nx * d.ny;
+__device__ __forceinline__ void load_plane(Dims d, const V* __restrict__ u, const CurvCoef& cf, const PlaneIdx& P,
+                                           int z, PlaneRegs<V>& R) {
+  const int zw = z < 0 ? z + d.nz : (z >= d.nz ? z - d.nz : z);
+  const long long zo = (long long)zw * d.nx * d.ny;
 #pragma unroll
   for (int k = 0; k < CQ; ++k) {
     const int q = threadIdx.x + k * CNT;
     if (q < CSN) {
-      const int gx = (((x0 - 1 + q % CSW) % d.nx) + d.nx) % d.nx, gy = (((y0 - 1 + q / CSW) % d.ny) + d.ny) % d.ny;
-      const long long gi = zo + (long long)gy * d.nx + gx;
+      const long long gi = zo + P.off[k];
       R.u[k] = u[gi];
 #pragma unroll
       for (int m = 0; m < 6; ++m) R.b[k][m] = __ldg(cf.B[m] + gi);
@@ -781,27 +805,64 @@ __global__ void __launch_bounds__(CNT) k_curv_tiled(Dims d, CurvCoef cf, const f
   const long long pst = (long long)d.nx * d.ny;
   const int c = (ty + 1) * CSW + tx + 1;
   float rr = 0.f;
+  __shared__ float sfx[CTY][CTX + 1], sfy[CTY + 1][CTX];  // x- and y-face fluxes of M (form 0)
+  float fzm = 0.f;                                         // -z face flux of M (form 0)
   PlaneRegs<float> R;
+  const PlaneIdx PI = plane_idx(d, x0, y0);
   auto slot = [&](int p) { return (p - (z0 - 1)) & 3; };
-  load_plane(d, u, cf, x0, y0, z0 - 1, R);
+  load_plane(d, u, cf, PI, z0 - 1, R);
   store_plane(ring, slot(z0 - 1), R);
-  load_plane(d, u, cf, x0, y0, z0, R);
+  load_plane(d, u, cf, PI, z0, R);
   store_plane(ring, slot(z0), R);
-  load_plane(d, u, cf, x0, y0, z0 + 1, R);
+  load_plane(d, u, cf, PI, z0 + 1, R);
+  // J and r of the thread's cell, one plane ahead
+  const long long i0 = (long long)y * d.nx + x;
+  float Jn = 0.f, rn = 0.f;
+  if (own) {
+    Jn = cf.J[(long long)z0 * pst + i0];
+    rn = r[(long long)z0 * pst + i0];
+  }
   for (int t = z0; t < zend; ++t) {
     store_plane(ring, slot(t + 1), R);
     __syncthreads();
-    if (t + 1 < zend) load_plane(d, u, cf, x0, y0, t + 2, R);
+    if (t + 1 < zend) load_plane(d, u, cf, PI, t + 2, R);
+    const float Jc = Jn, rc = rn;
+    if (own && t + 1 < zend) {
+      Jn = cf.J[(long long)(t + 1) * pst + i0];
+      rn = r[(long long)(t + 1) * pst + i0];
+    }
+    const RingU<float> U{{ring.u(slot(t - 1)), ring.u(slot(t)), ring.u(slot(t + 1))}, c};
+    const RingB Bc{{ring.b(slot(t - 1)), ring.b(slot(t)), ring.b(slot(t + 1))}, c};
+    float Mh2 = 0.f;
+    if constexpr (TR == 0) {
+      // Each face flux of M once: the thread's -x, -y and +z faces, the tile's last
+      // column and row of +x / +y faces by warp 0 (8 lanes) and warp CTY - 1, the -z
+      // face carried from the plane below.  Threads outside the mesh hold periodic
+      // images of its cells, so their fluxes are the wrapped ones.
+      if (t == z0) fzm = face_flux<float>(U, Bc, 2, 0, 0, -1);
+      sfx[ty][tx] = face_flux<float>(U, Bc, 0, -1, 0, 0);
+      sfy[ty][tx] = face_flux<float>(U, Bc, 1, 0, -1, 0);
+      const float fzp = face_flux<float>(U, Bc, 2, 0, 0, 0);
+      if (ty == CTY - 1) sfy[CTY][tx] = face_flux<float>(U, Bc, 1, 0, 0, 0);
+      if (ty == 0 && tx < CTY) {
+        const int ce = (tx + 1) * CSW + CTX;  // haloed index of the cell (CTX - 1, tx)
+        const RingU<float> Ue{{U.pl[0], U.pl[1], U.pl[2]}, ce};
+        const RingB Be{{Bc.pl[0], Bc.pl[1], Bc.pl[2]}, ce};
+        sfx[tx][CTX] = face_flux<float>(Ue, Be, 0, 0, 0, 0);
+      }
+      __syncthreads();
+      // same association as apply_M_h2: ((0 + x) + y) + z
+      Mh2 = ((0.f + (sfx[ty][tx + 1] - sfx[ty][tx])) + (sfy[ty + 1][tx] - sfy[ty][tx])) + (fzp - fzm);
+      fzm = fzp;
+    }
     if (own) {
-      const RingU<float> U{{ring.u(slot(t - 1)), ring.u(slot(t)), ring.u(slot(t + 1))}, c};
-      const RingB Bc{{ring.b(slot(t - 1)), ring.b(slot(t)), ring.b(slot(t + 1))}, c};
-      const long long i = (long long)t * pst + (long long)y * d.nx + x;
-      const float Mh2 = TR == 2 ? apply_S_h2<float>(U, Bc) : (TR ? apply_MT_h2<float>(U, Bc) : apply_M_h2<float>(U, Bc));
+      const long long i = (long long)t * pst + i0;
+      if constexpr (TR != 0) Mh2 = TR == 2 ? apply_S_h2<float>(U, Bc) : apply_MT_h2<float>(U, Bc);
       if (MODE == CM_JACOBI) {
         const float Dh2 = TR == 2 ? diag_S_h2<float>(Bc) : diag_M_h2<float>(Bc);
-        out[i] = U(0, 0, 0) + omega * ((cf.J[i] * r[i] * cf.h2 - Mh2) / Dh2);
+        out[i] = U(0, 0, 0) + omega * ((Jc * rc * cf.h2 - Mh2) / Dh2);
       } else {
-        const float res = r[i] - Mh2 * inv_h2 / cf.J[i];
+        const float res = rc - Mh2 * inv_h2 / Jc;
         out[i] = res;
         rr += res * res;
       }
@@ -840,36 +901,79 @@ __global__ void __launch_bounds__(CNT) k_curv_df_residual_tiled(Dims d, CurvCoef
   float2 m = make_float2(0.f, 0.f);
   if (m_dev) m = f64_to_df(m_dev[0]);
   float r2 = 0.f, f2 = 0.f;
+  __shared__ float2 sfx[CTY][CTX + 1], sfy[CTY + 1][CTX];  // x- and y-face fluxes of M (form 0), (s, c)
+  float2 fzm = make_float2(0.f, 0.f);                      // -z face flux of M (form 0)
   PlaneRegs<float2> R;
+  const PlaneIdx PI = plane_idx(d, x0, y0);
   auto slot = [&](int p) { return (p - (z0 - 1)) & 3; };
-  load_plane(d, u, cf, x0, y0, z0 - 1, R);
+  load_plane(d, u, cf, PI, z0 - 1, R);
   store_plane(ring, slot(z0 - 1), R);
-  load_plane(d, u, cf, x0, y0, z0, R);
+  load_plane(d, u, cf, PI, z0, R);
   store_plane(ring, slot(z0), R);
-  load_plane(d, u, cf, x0, y0, z0 + 1, R);
+  load_plane(d, u, cf, PI, z0 + 1, R);
+  // J and the source of the thread's cell, one plane ahead
+  const long long i0 = (long long)y * d.nx + x;
+  float Jn = 0.f;
+  float2 bn = make_float2(0.f, 0.f);
+  if (own) {
+    Jn = cf.J[(long long)z0 * pst + i0];
+    bn = src[(long long)z0 * pst + i0];
+  }
   for (int t = z0; t < zend; ++t) {
     store_plane(ring, slot(t + 1), R);
     __syncthreads();
-    if (t + 1 < zend) load_plane(d, u, cf, x0, y0, t + 2, R);
+    if (t + 1 < zend) load_plane(d, u, cf, PI, t + 2, R);
+    const float J = Jn;
+    float2 b = bn;
+    if (own && t + 1 < zend) {
+      Jn = cf.J[(long long)(t + 1) * pst + i0];
+      bn = src[(long long)(t + 1) * pst + i0];
+    }
+    const DfRingAt U{{ring.u(slot(t - 1)), ring.u(slot(t)), ring.u(slot(t + 1))}, c};
+    const RingB Bc{{ring.b(slot(t - 1)), ring.b(slot(t)), ring.b(slot(t + 1))}, c};
+    float2 fzp = make_float2(0.f, 0.f);
+    if (form == 0) {
+      // each face flux of M once, as in the FP32 sweep (the -x, -y, +z faces of every
+      // thread, the tile's last column / row of +x / +y faces, the -z face carried)
+      if (t == z0) fzm = df_face_flux(U, Bc, 2, 0, 0, -1);
+      sfx[ty][tx] = df_face_flux(U, Bc, 0, -1, 0, 0);
+      sfy[ty][tx] = df_face_flux(U, Bc, 1, 0, -1, 0);
+      fzp = df_face_flux(U, Bc, 2, 0, 0, 0);
+      if (ty == CTY - 1) sfy[CTY][tx] = df_face_flux(U, Bc, 1, 0, 0, 0);
+      if (ty == 0 && tx < CTY) {
+        const int ce = (tx + 1) * CSW + CTX;  // haloed index of the cell (CTX - 1, tx)
+        const DfRingAt Ue{{U.pl[0], U.pl[1], U.pl[2]}, ce};
+        const RingB Be{{Bc.pl[0], Bc.pl[1], Bc.pl[2]}, ce};
+        sfx[tx][CTX] = df_face_flux(Ue, Be, 0, 0, 0, 0);
+      }
+      __syncthreads();
+    }
     if (own) {
-      const long long i = (long long)t * pst + (long long)y * d.nx + x;
-      const float J = cf.J[i];
-      float2 b = src[i];
+      const long long i = (long long)t * pst + i0;
       if (m_dev) b = df_add(b, make_float2(-m.x, -m.y));
       DfAcc acc{0.f, 0.f};
       const float wb = scale_J ? J * cf.h2 : cf.h2;
       df_acc_prod(acc, wb, b);
-      const DfRingAt U{{ring.u(slot(t - 1)), ring.u(slot(t)), ring.u(slot(t + 1))}, c};
-      const RingB Bc{{ring.b(slot(t - 1)), ring.b(slot(t)), ring.b(slot(t + 1))}, c};
-      if (form == 2) df_apply_S(acc, U, Bc, -1.f);
-      else if (form == 1) df_apply_MT(acc, U, Bc, -1.f);
-      else df_apply_M(acc, U, Bc, -1.f);
+      if (form == 0) {
+        // acc -= sum_a (F_a(+) - F_a(-)), every face flux a compensated pair
+        df_acc_face(acc, sfx[ty][tx + 1], -1.f);
+        df_acc_face(acc, sfx[ty][tx], 1.f);
+        df_acc_face(acc, sfy[ty + 1][tx], -1.f);
+        df_acc_face(acc, sfy[ty][tx], 1.f);
+        df_acc_face(acc, fzp, -1.f);
+        df_acc_face(acc, fzm, 1.f);
+      } else if (form == 2) {
+        df_apply_S(acc, U, Bc, -1.f);
+      } else {
+        df_apply_MT(acc, U, Bc, -1.f);
+      }
       const float rv = (acc.s + acc.c) / (J * cf.h2);
       r[i] = rv;
       r2 += rv * rv;
       const float fv = scale_J ? (b.x + b.y) : (b.x + b.y) / J;
       f2 += fv * fv;
     }
+    fzm = fzp;
   }
   if (pr2) {
     const double s = block_sum_f(r2, shr);

@@ -121,6 +121,44 @@ def test_psi_zero_reduces_to_flat(gb):
     assert rel_l2(phi.cpu().numpy(), flat.fft_solve(F)) < 1e-9
 
 
+@pytest.mark.parametrize("sym", [False, True])
+@pytest.mark.parametrize("shape", [(16, 24, 32), (32, 32, 32)])
+def test_double_float_residual_is_the_fp64_residual(gb, shape, sym, monkeypatch):
+    # Solved to 1e-12, the solution's residual under the GPU's own FP32 coefficients,
+    # evaluated here in FP64 by the oracle stencil, is the residual the double-float
+    # kernel reported.  That kernel forms each face (and edge) mean of the FP32 cell
+    # coefficients in FP32 and everything else in double-float, so the stencil here
+    # takes the same FP32 means; the rest of its arithmetic is FP64.
+    def face32(B, a, b):
+        c = B[a, b].astype(np.float32)
+        return (np.float32(0.5) * (c + curv.at(c, a, 1))).astype(np.float64)
+
+    def edge32(B, a, b):
+        c = B[a, b].astype(np.float32)
+        return (np.float32(0.25) * ((c + curv.at(c, a, 1)) + (curv.at(c, b, 1) + curv.at2(c, a, 1, b, 1)))
+                ).astype(np.float64)
+
+    psi = psi_field(shape, 17)
+    delta = grf(shape, 18)
+    s = gb.Solver(shape, op="curv", curv_sym=sym)
+    s.set_geometry(to_dev(psi))
+    phi, st = s.solve(to_dev(delta), tol=1e-12, max_vcycles=300)
+    assert st.status == 0 and st.rel_res <= 1e-12
+    J, B6 = s.curv_geometry(0)
+    J, B6 = J.double().cpu().numpy(), B6.double().cpu().numpy()
+    B = np.empty((3, 3) + shape)
+    for k, (a, b) in enumerate([(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]):
+        B[a, b] = B6[k]
+        B[b, a] = B6[k]
+    f = delta - (delta * J).sum() / J.sum()
+    monkeypatch.setattr(curv, "face_coeff", face32)
+    monkeypatch.setattr(curv, "edge_coeff", edge32)
+    Mphi = (curv.apply_M_sym if sym else curv.apply_M)(phi.cpu().numpy(), B, 1.0)
+    rel = float(np.linalg.norm(f - Mphi / J) / np.linalg.norm(f))
+    assert rel < 2e-12
+    assert abs(rel - st.rel_res) < 0.05 * st.rel_res + 1e-14
+
+
 def test_adjoint_matches_oracle(gb):
     shape = (16, 16, 16)
     psi = psi_field(shape, 14, 1.5, 0.4)
