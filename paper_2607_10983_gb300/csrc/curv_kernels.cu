@@ -3,8 +3,8 @@
 // Geometry per level (Sec. 4.2, Eq. triad and Eq. metric): A = I + Hess psi with
 // second-order central differences (mixed terms by the four-point 1/(4h^2)
 // stencil), J = sqrt(g) = det A and B = sqrt(g) g^-1 = J A^-2 = adj(A)^2 / J.
-// Built in FP64 from the FP64 psi of the level, stored as FP32 (J and the six
-// components of the symmetric B).
+// Built in double-float arithmetic (about 48 bits) from the FP64 psi of the level,
+// stored as FP32 (J and the six components of the symmetric B).
 //
 // Operator (Sec. 4.3.1): (M u)_i = sum_a (F^a_{i+1/2} - F^a_{i-1/2}) / h with face
 // fluxes F^a = sum_b B^{ab}_face G_b, B_face the mean of the two adjacent cells,
@@ -19,6 +19,8 @@
 // b-positions.  S = S^T; it is its own transpose in the adjoint.
 //
 // Operator form of a launch: 0 = M, 1 = M^T, 2 = S.
+#include <cmath>
+
 #include "kernels.h"
 #include "stencil.cuh"
 
@@ -259,34 +261,6 @@ __device__ __forceinline__ T op_h2(const FieldAt<T>& u, const CoefAt& B, int for
 }
 
 // ------------------------------------------------------------------ kernels
-
-__global__ void k_geom(Dims d, const double* __restrict__ psi, double h, CurvCoefOut out) {
-  const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y, z = blockIdx.z;
-  if (x >= d.nx || y >= d.ny) return;
-  const Nbhd nb(d, x, y, z);
-  auto P = [&](int dx, int dy, int dz) { return psi[nb(dx, dy, dz)]; };
-  const double ih2 = 1.0 / (h * h), iq = 0.25 / (h * h);
-  const double c0 = P(0, 0, 0);
-  const double a = 1.0 + (P(1, 0, 0) - 2.0 * c0 + P(-1, 0, 0)) * ih2;
-  const double b = 1.0 + (P(0, 1, 0) - 2.0 * c0 + P(0, -1, 0)) * ih2;
-  const double c = 1.0 + (P(0, 0, 1) - 2.0 * c0 + P(0, 0, -1)) * ih2;
-  const double dxy = (P(1, 1, 0) - P(1, -1, 0) - P(-1, 1, 0) + P(-1, -1, 0)) * iq;
-  const double dxz = (P(1, 0, 1) - P(1, 0, -1) - P(-1, 0, 1) + P(-1, 0, -1)) * iq;
-  const double dyz = (P(0, 1, 1) - P(0, 1, -1) - P(0, -1, 1) + P(0, -1, -1)) * iq;
-  // adjugate of the symmetric triad [[a, dxy, dxz], [dxy, b, dyz], [dxz, dyz, c]]
-  const double j00 = b * c - dyz * dyz, j11 = a * c - dxz * dxz, j22 = a * b - dxy * dxy;
-  const double j01 = dxz * dyz - dxy * c, j02 = dxy * dyz - b * dxz, j12 = dxy * dxz - a * dyz;
-  const double J = a * j00 + dxy * j01 + dxz * j02;
-  const double iJ = 1.0 / J;
-  const long long i = nb(0, 0, 0);
-  out.J[i] = (float)J;
-  out.B[0][i] = (float)((j00 * j00 + j01 * j01 + j02 * j02) * iJ);
-  out.B[1][i] = (float)((j01 * j01 + j11 * j11 + j12 * j12) * iJ);
-  out.B[2][i] = (float)((j02 * j02 + j12 * j12 + j22 * j22) * iJ);
-  out.B[3][i] = (float)((j00 * j01 + j01 * j11 + j02 * j12) * iJ);
-  out.B[4][i] = (float)((j00 * j02 + j01 * j12 + j02 * j22) * iJ);
-  out.B[5][i] = (float)((j01 * j02 + j11 * j12 + j12 * j22) * iJ);
-}
 
 // out = op(u) / J (divide_J) or op(u), op of the given form
 template <typename T>
@@ -774,6 +748,113 @@ __device__ __forceinline__ void store_plane(const Ring<V>& ring, int slot, const
   }
 }
 
+// ---- geometry of a level in double-float arithmetic ----
+
+// (hi, lo) products and the reciprocal: Dekker's product with the error of a.hi b.hi
+// from one FMA, the cross terms added to it, renormalised.
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+  const float p = a.x * b.x;
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  float h, l;
+  quick_two_sum(p, e, h, l);
+  return make_float2(h, l);
+}
+__device__ __forceinline__ float2 df_scale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// 1 / a: q0 = RN(1 / a.hi), one Newton correction q0 (1 - a q0) with the residual in
+// double-float (1 - a.hi q0 is exact by Sterbenz's lemma once its rounding error is split off).
+__device__ __forceinline__ float2 df_recip(float2 a) {
+  const float q0 = 1.0f / a.x;
+  const float p = a.x * q0;
+  const float pe = __fmaf_rn(a.x, q0, -p);
+  const float r = ((1.0f - p) - pe) - a.y * q0;
+  float h, l;
+  quick_two_sum(q0, q0 * r, h, l);
+  return make_float2(h, l);
+}
+// a b + c d + e f
+__device__ __forceinline__ float2 df_dot3(float2 a, float2 b, float2 c, float2 d, float2 e, float2 f) {
+  return df_add(df_add(df_mul(a, b), df_mul(c, d)), df_mul(e, f));
+}
+
+// Geometry of one level (Sec. 4.2, Eq. triad and Eq. metric): A = I + Hess psi with the
+// central second differences, J = det A = a . adj(A) row 0, B = adj(A)^2 / J, every
+// step in double-float from the FP64 psi (each value converted once, in a z-streaming
+// tile with a three-plane ring) and rounded to FP32 at the end.  ih2 = 1 / h^2 and
+// iq = 1 / (4 h^2) are powers of two (h = 2^l), so the scalings are exact.
+__global__ void __launch_bounds__(CNT) k_geom_tiled(Dims d, const double* __restrict__ psi, float ih2,
+                                                    CurvCoefOut out, int zc) {
+  __shared__ float2 ring[4][CSN];
+  const int tx = threadIdx.x % CTX, ty = threadIdx.x / CTX;
+  const int x0 = blockIdx.x * CTX, y0 = blockIdx.y * CTY, z0 = blockIdx.z * zc;
+  const int zend = min(z0 + zc, d.nz);
+  const int x = x0 + tx, y = y0 + ty;
+  const bool own = x < d.nx && y < d.ny;
+  const long long pst = (long long)d.nx * d.ny;
+  const int c = (ty + 1) * CSW + tx + 1;
+  const PlaneIdx PI = plane_idx(d, x0, y0);
+  double pre[CQ];
+  auto load = [&](int z) {
+    const int zw = z < 0 ? z + d.nz : (z >= d.nz ? z - d.nz : z);
+#pragma unroll
+    for (int k = 0; k < CQ; ++k)
+      if (threadIdx.x + k * CNT < CSN) pre[k] = psi[(long long)zw * pst + PI.off[k]];
+  };
+  auto store = [&](int slot) {
+#pragma unroll
+    for (int k = 0; k < CQ; ++k) {
+      const int q = threadIdx.x + k * CNT;
+      if (q < CSN) ring[slot][q] = f64_to_df(pre[k]);
+    }
+  };
+  auto slot = [&](int p) { return (p - (z0 - 1)) & 3; };
+  load(z0 - 1);
+  store(slot(z0 - 1));
+  load(z0);
+  store(slot(z0));
+  load(z0 + 1);
+  const float iq = 0.25f * ih2;
+  for (int t = z0; t < zend; ++t) {
+    store(slot(t + 1));
+    __syncthreads();
+    if (t + 1 < zend) load(t + 2);
+    if (own) {
+      const float2* pl[3] = {ring[slot(t - 1)], ring[slot(t)], ring[slot(t + 1)]};
+      auto P = [&](int dx, int dy, int dz) { return pl[dz + 1][c + dy * CSW + dx]; };
+      const float2 c2 = df_scale(P(0, 0, 0), -2.0f);
+      auto second = [&](float2 p, float2 m) { return df_add_f(df_scale(df_add(df_add(p, m), c2), ih2), 1.0f); };
+      auto mixed = [&](float2 pp, float2 pm, float2 mp, float2 mm) {
+        return df_scale(df_add(df_add(pp, make_float2(-pm.x, -pm.y)), df_add(mm, make_float2(-mp.x, -mp.y))), iq);
+      };
+      const float2 a = second(P(1, 0, 0), P(-1, 0, 0));
+      const float2 b = second(P(0, 1, 0), P(0, -1, 0));
+      const float2 cc = second(P(0, 0, 1), P(0, 0, -1));
+      const float2 dxy = mixed(P(1, 1, 0), P(1, -1, 0), P(-1, 1, 0), P(-1, -1, 0));
+      const float2 dxz = mixed(P(1, 0, 1), P(1, 0, -1), P(-1, 0, 1), P(-1, 0, -1));
+      const float2 dyz = mixed(P(0, 1, 1), P(0, 1, -1), P(0, -1, 1), P(0, -1, -1));
+      auto neg = [](float2 v) { return make_float2(-v.x, -v.y); };
+      // adjugate of the symmetric triad [[a, dxy, dxz], [dxy, b, dyz], [dxz, dyz, c]]
+      const float2 j00 = df_add(df_mul(b, cc), neg(df_mul(dyz, dyz)));
+      const float2 j11 = df_add(df_mul(a, cc), neg(df_mul(dxz, dxz)));
+      const float2 j22 = df_add(df_mul(a, b), neg(df_mul(dxy, dxy)));
+      const float2 j01 = df_add(df_mul(dxz, dyz), neg(df_mul(dxy, cc)));
+      const float2 j02 = df_add(df_mul(dxy, dyz), neg(df_mul(b, dxz)));
+      const float2 j12 = df_add(df_mul(dxy, dxz), neg(df_mul(a, dyz)));
+      const float2 J = df_dot3(a, j00, dxy, j01, dxz, j02);
+      const float2 iJ = df_recip(J);
+      const long long i = (long long)t * pst + (long long)y * d.nx + x;
+      out.J[i] = J.x;
+      out.B[0][i] = df_mul(df_dot3(j00, j00, j01, j01, j02, j02), iJ).x;
+      out.B[1][i] = df_mul(df_dot3(j01, j01, j11, j11, j12, j12), iJ).x;
+      out.B[2][i] = df_mul(df_dot3(j02, j02, j12, j12, j22, j22), iJ).x;
+      out.B[3][i] = df_mul(df_dot3(j00, j01, j01, j11, j02, j12), iJ).x;
+      out.B[4][i] = df_mul(df_dot3(j00, j02, j01, j12, j02, j22), iJ).x;
+      out.B[5][i] = df_mul(df_dot3(j01, j02, j11, j12, j12, j22), iJ).x;
+    }
+  }
+}
+
 // z chunk: at least four waves of four CTAs per SM.
 int curv_zchunk(Dims d) {
   const long long tiles = (long long)((d.nx + CTX - 1) / CTX) * ((d.ny + CTY - 1) / CTY);
@@ -1007,7 +1088,9 @@ cudaError_t launch_jscale(cudaStream_t st, long long n, const float2* lam, const
 }
 
 cudaError_t launch_geom(cudaStream_t st, Dims d, const double* psi, double h, CurvCoefOut out) {
-  k_geom<<<cell_grid(d), dim3(BX, BY), 0, st>>>(d, psi, h, out);
+  int ex;
+  if (!(h > 0.0) || std::frexp(h, &ex) != 0.5 || ex < -20 || ex > 20) return cudaErrorInvalidValue;  // h = 2^l
+  k_geom_tiled<<<curv_tiled_grid(d), CNT, 0, st>>>(d, psi, (float)(1.0 / (h * h)), out, curv_zchunk(d));
   note_launch();
   return cudaGetLastError();
 }
