@@ -474,164 +474,45 @@ __global__ void k_ratio(const double* a, const double* b, double* out) {
 }
 
 
-// ---- adjoint of the geometry (Sec. 4.8, Eq. adj_op) ----
-
-// Per cell of the finest level: the cotangent of the triad A for the scalar
-//   <lam, b(J)> - <lam, M(B) phi>,  b = J (delta - m_w),
-// where Jbar = (delta - m_w)(lam - s_lam), s_lam = sum(J lam)/sum(J), and Bbar
-// comes from <lam, M phi> = sum_a sum_i sum_b B^{ab}_face(i) G^a_b[phi](i) (lam_i - lam_{i+a})/h,
-// B^{ab}_face(i) = (B^{ab}_i + B^{ab}_{i+a})/2.  With B = J A^-2 and J = det A:
-//   Abar_J = Jbar J A^-1,  Abar_B = J <Bbar, A^-2> A^-1 - J (A^-1 Bbar A^-2 + A^-2 Bbar A^-1).
-// Writes S = Abar_J - Abar_B symmetrised for the Hessian stencils:
-// S_aa = Abar_aa, S_ab = Abar_ab + Abar_ba (a < b), packed xx, yy, zz, xy, xz, yz.
-// Precision: the differences that cancel (second differences of psi, differences of phi
-// and lam across faces and edges) are formed in FP64; the pointwise algebra of the 3 x 3
-// triad (adjugate, J, A^-1, A^-2 and the cotangent products) runs in FP32, A having its
-// eigenvalues in [1/2, 3/2] (FP64 arithmetic runs at a small fraction of the FP32 rate).
-__global__ void k_psibar_A(Dims d, const double* __restrict__ psi, const double* __restrict__ phi,
-                           const double* __restrict__ lam, const double* __restrict__ delta,
-                           const double* __restrict__ mw_dev, const double* __restrict__ slam_dev,
-                           double h, int sym, double* __restrict__ S) {
-  const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y, z = blockIdx.z;
-  if (x >= d.nx || y >= d.ny) return;
-  const long long n = ncell(d);
-  const Nbhd nb(d, x, y, z);
-  const long long i = nb(0, 0, 0);
-  // triad at this cell: FP64 second differences, then FP32
-  auto P = [&](int dx, int dy, int dz) { return psi[nb(dx, dy, dz)]; };
-  const double ih2 = 1.0 / (h * h), iq = 0.25 / (h * h);
-  const double c0 = P(0, 0, 0);
-  float A[3][3];
-  A[0][0] = (float)(1.0 + (P(1, 0, 0) - 2.0 * c0 + P(-1, 0, 0)) * ih2);
-  A[1][1] = (float)(1.0 + (P(0, 1, 0) - 2.0 * c0 + P(0, -1, 0)) * ih2);
-  A[2][2] = (float)(1.0 + (P(0, 0, 1) - 2.0 * c0 + P(0, 0, -1)) * ih2);
-  A[0][1] = A[1][0] = (float)((P(1, 1, 0) - P(1, -1, 0) - P(-1, 1, 0) + P(-1, -1, 0)) * iq);
-  A[0][2] = A[2][0] = (float)((P(1, 0, 1) - P(1, 0, -1) - P(-1, 0, 1) + P(-1, 0, -1)) * iq);
-  A[1][2] = A[2][1] = (float)((P(0, 1, 1) - P(0, 1, -1) - P(0, -1, 1) + P(0, -1, -1)) * iq);
-  float adj[3][3];
-  adj[0][0] = A[1][1] * A[2][2] - A[1][2] * A[1][2];
-  adj[1][1] = A[0][0] * A[2][2] - A[0][2] * A[0][2];
-  adj[2][2] = A[0][0] * A[1][1] - A[0][1] * A[0][1];
-  adj[0][1] = adj[1][0] = A[0][2] * A[1][2] - A[0][1] * A[2][2];
-  adj[0][2] = adj[2][0] = A[0][1] * A[1][2] - A[1][1] * A[0][2];
-  adj[1][2] = adj[2][1] = A[0][1] * A[0][2] - A[0][0] * A[1][2];
-  const float J = A[0][0] * adj[0][0] + A[0][1] * adj[0][1] + A[0][2] * adj[0][2];
-  const float iJ = 1.0f / J;
-  float Ai[3][3], Ai2[3][3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) Ai[a][b] = adj[a][b] * iJ;
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) Ai2[a][b] = Ai[a][0] * Ai[0][b] + Ai[a][1] * Ai[1][b] + Ai[a][2] * Ai[2][b];
-  // Bbar at this cell: faces a at i (own) and i - a (left neighbour's face)
-  auto PH = [&](int dx, int dy, int dz) { return phi[nb(dx, dy, dz)]; };
-  auto LA = [&](int dx, int dy, int dz) { return lam[nb(dx, dy, dz)]; };
-  // face value of G^a_b[phi] * (lam_c - lam_{c+a}) / h on the a-face between c and c + a
-  const double ih = 1.0 / h;  // h is a power of two: multiplying by 1/h equals dividing by h
-  auto fbar = [&](int a, int b, int cx, int cy, int cz) -> double {
-    int px = cx, py = cy, pz = cz;
-    shift(a, 1, px, py, pz);
-    const double Lam = (LA(cx, cy, cz) - LA(px, py, pz)) * ih;
-    double G;
-    if (a == b) {
-      G = (PH(px, py, pz) - PH(cx, cy, cz)) * ih;
-    } else {
-      int c1x = cx, c1y = cy, c1z = cz, c2x = cx, c2y = cy, c2z = cz;
-      shift(b, 1, c1x, c1y, c1z);
-      shift(b, -1, c2x, c2y, c2z);
-      int d1x = px, d1y = py, d1z = pz, d2x = px, d2y = py, d2z = pz;
-      shift(b, 1, d1x, d1y, d1z);
-      shift(b, -1, d2x, d2y, d2z);
-      G = 0.25 * ((PH(c1x, c1y, c1z) - PH(c2x, c2y, c2z)) + (PH(d1x, d1y, d1z) - PH(d2x, d2y, d2z))) * ih;
-    }
-    return G * Lam;
-  };
-  float Bb[3][3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    int mx = 0, my = 0, mz = 0;
-    shift(a, -1, mx, my, mz);
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-      Bb[a][b] = (sym && b != a) ? 0.f : (float)(0.5 * (fbar(a, b, 0, 0, 0) + fbar(a, b, mx, my, mz)));
-  }
-  if (sym) {
-    // symmetric variant: d<lam, S phi>/dC on the ab-edge at base e is
-    //   (1/2h^2) [lam_e (phi_{e+a+b} - phi_e) - lam_{e+a} (phi_{e+b} - phi_{e+a})
-    //             - lam_{e+b} (phi_{e+a} - phi_{e+b}) + lam_{e+a+b} (phi_e - phi_{e+a+b})],
-    // and each of the four edges around this cell takes a quarter of its B^{ab} (a < b).
-    for (int a = 0; a < 3; ++a)
-      for (int b = a + 1; b < 3; ++b) {
-        double acc = 0.0;
-        for (int k = 0; k < 4; ++k) {
-          int ex = 0, ey = 0, ez = 0;
-          if (k & 1) shift(a, -1, ex, ey, ez);
-          if (k & 2) shift(b, -1, ex, ey, ez);
-          int ax = ex, ay = ey, az = ez, bx = ex, by = ey, bz = ez;
-          shift(a, 1, ax, ay, az);
-          shift(b, 1, bx, by, bz);
-          int px = ax, py = ay, pz = az;
-          shift(b, 1, px, py, pz);
-          const double pe = PH(ex, ey, ez), pa = PH(ax, ay, az), pb = PH(bx, by, bz), pp = PH(px, py, pz);
-          acc += LA(ex, ey, ez) * (pp - pe) - LA(ax, ay, az) * (pb - pa) - LA(bx, by, bz) * (pa - pb) +
-                 LA(px, py, pz) * (pe - pp);
-        }
-        Bb[a][b] = (float)(0.25 * 0.5 * acc * (ih * ih));
-      }
-  }
-  // Abar_B = J <Bbar, A^-2> A^-1 - J (A^-1 Bbar A^-2 + A^-2 Bbar A^-1)   (A symmetric)
-  float inner = 0.f;
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) inner += Bb[a][b] * Ai2[a][b];
-  float T1[3][3], T2[3][3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      T1[a][b] = Bb[a][0] * Ai2[0][b] + Bb[a][1] * Ai2[1][b] + Bb[a][2] * Ai2[2][b];  // Bbar A^-2
-      T2[a][b] = Bb[a][0] * Ai[0][b] + Bb[a][1] * Ai[1][b] + Bb[a][2] * Ai[2][b];     // Bbar A^-1
-    }
-  const double mw = mw_dev[0], sl = slam_dev[0];
-  const float Jbar = (float)((delta[i] - mw) * (lam[i] - sl));
-  float Ab[3][3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      const float t = Ai[a][0] * T1[0][b] + Ai[a][1] * T1[1][b] + Ai[a][2] * T1[2][b] +
-                      Ai2[a][0] * T2[0][b] + Ai2[a][1] * T2[1][b] + Ai2[a][2] * T2[2][b];
-      const float AbB = J * inner * Ai[a][b] - J * t;
-      Ab[a][b] = Jbar * J * Ai[a][b] - AbB;
-    }
-  S[i] = Ab[0][0];
-  S[n + i] = Ab[1][1];
-  S[2 * n + i] = Ab[2][2];
-  S[3 * n + i] = (double)Ab[0][1] + (double)Ab[1][0];
-  S[4 * n + i] = (double)Ab[0][2] + (double)Ab[2][0];
-  S[5 * n + i] = (double)Ab[1][2] + (double)Ab[2][1];
-}
-
 // psi_bar = sum_a D_aa(S_aa) + sum_{a<b} D_ab(S_ab): the transpose of psi -> Hess psi,
-// each second-difference stencil being self-adjoint on the periodic mesh.
-__global__ void k_psibar_H(Dims d, const double* __restrict__ S, double h, double* __restrict__ out) {
+// each second-difference stencil being self-adjoint on the periodic mesh.  S holds
+// double-float pairs (exact sums of FP32 values); the 21 weighted terms are accumulated
+// in a compensated pair (the weights 1/h^2, 1/(4h^2) are powers of two) and the sum is
+// written in FP64.
+__global__ void k_psibar_H(Dims d, const float2* __restrict__ S, float ih2, double* __restrict__ out) {
   const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y, z = blockIdx.z;
   if (x >= d.nx || y >= d.ny) return;
   const long long n = ncell(d);
   const Nbhd nb(d, x, y, z);
   auto C = [&](int k, int dx, int dy, int dz) { return S[k * n + nb(dx, dy, dz)]; };
-  const double ih2 = 1.0 / (h * h), iq = 0.25 / (h * h);
-  double v = (C(0, 1, 0, 0) - 2.0 * C(0, 0, 0, 0) + C(0, -1, 0, 0)) * ih2;
-  v += (C(1, 0, 1, 0) - 2.0 * C(1, 0, 0, 0) + C(1, 0, -1, 0)) * ih2;
-  v += (C(2, 0, 0, 1) - 2.0 * C(2, 0, 0, 0) + C(2, 0, 0, -1)) * ih2;
-  v += (C(3, 1, 1, 0) - C(3, 1, -1, 0) - C(3, -1, 1, 0) + C(3, -1, -1, 0)) * iq;
-  v += (C(4, 1, 0, 1) - C(4, 1, 0, -1) - C(4, -1, 0, 1) + C(4, -1, 0, -1)) * iq;
-  v += (C(5, 0, 1, 1) - C(5, 0, 1, -1) - C(5, 0, -1, 1) + C(5, 0, -1, -1)) * iq;
-  out[nb(0, 0, 0)] = v;
+  const float iq = 0.25f * ih2;
+  DfAcc acc{0.f, 0.f};
+  auto add = [&](float2 v, float w) {
+    acc.add(w * v.x);
+    acc.c += w * v.y;
+  };
+  add(C(0, 1, 0, 0), ih2);
+  add(C(0, 0, 0, 0), -2.f * ih2);
+  add(C(0, -1, 0, 0), ih2);
+  add(C(1, 0, 1, 0), ih2);
+  add(C(1, 0, 0, 0), -2.f * ih2);
+  add(C(1, 0, -1, 0), ih2);
+  add(C(2, 0, 0, 1), ih2);
+  add(C(2, 0, 0, 0), -2.f * ih2);
+  add(C(2, 0, 0, -1), ih2);
+  add(C(3, 1, 1, 0), iq);
+  add(C(3, 1, -1, 0), -iq);
+  add(C(3, -1, 1, 0), -iq);
+  add(C(3, -1, -1, 0), iq);
+  add(C(4, 1, 0, 1), iq);
+  add(C(4, 1, 0, -1), -iq);
+  add(C(4, -1, 0, 1), -iq);
+  add(C(4, -1, 0, -1), iq);
+  add(C(5, 0, 1, 1), iq);
+  add(C(5, 0, 1, -1), -iq);
+  add(C(5, 0, -1, 1), -iq);
+  add(C(5, 0, -1, -1), iq);
+  out[nb(0, 0, 0)] = (double)acc.s + (double)acc.c;
 }
 
 // out = J (lam - s) in FP64 from a double-float lam (delta_bar of the curvilinear adjoint).
@@ -855,6 +736,215 @@ __global__ void __launch_bounds__(CNT) k_geom_tiled(Dims d, const double* __rest
   }
 }
 
+// ---- adjoint of the geometry (Sec. 4.8, Eq. adj_op) ----
+
+// Per cell of the finest level: the cotangent of the triad A for the scalar
+//   <lam, b(J)> - <lam, M(B) phi>,  b = J (delta - m_w),
+// where Jbar = (delta - m_w)(lam - s_lam), s_lam = sum(J lam)/sum(J), and Bbar
+// comes from <lam, M phi> = sum_a sum_i sum_b B^{ab}_face(i) G^a_b[phi](i) (lam_i - lam_{i+a})/h,
+// B^{ab}_face(i) = (B^{ab}_i + B^{ab}_{i+a})/2.  With B = J A^-2 and J = det A:
+//   Abar_J = Jbar J A^-1,  Abar_B = J <Bbar, A^-2> A^-1 - J (A^-1 Bbar A^-2 + A^-2 Bbar A^-1).
+// Writes S = Abar_J - Abar_B symmetrised for the Hessian stencils:
+// S_aa = Abar_aa, S_ab = Abar_ab + Abar_ba (a < b), packed xx, yy, zz, xy, xz, yz.
+// Precision: the differences that cancel (second differences of psi, differences of phi
+// and lam across faces and edges) are formed in double-float from psi, phi (FP64,
+// converted once per cell in a z-streaming three-plane ring) and lam (double-float) and
+// rounded to FP32; the pointwise algebra of the 3 x 3 triad (adjugate, J, A^-1, A^-2 and
+// the cotangent products) runs in FP32, A having its eigenvalues in [1/2, 3/2] (FP64
+// arithmetic runs at a small fraction of the FP32 rate).  S is written as double-float
+// pairs: the diagonal entries exactly, the off-diagonal sums by an error-free addition.
+__global__ void __launch_bounds__(CNT) k_psibar_tiled(Dims d, const double* __restrict__ psi,
+                                                      const double* __restrict__ phi, const float2* __restrict__ lam,
+                                                      const double* __restrict__ delta,
+                                                      const double* __restrict__ mw_dev,
+                                                      const double* __restrict__ slam_dev, float ih, int sym,
+                                                      float2* __restrict__ S, int zc) {
+  __shared__ float2 rps[4][CSN], rph[4][CSN], rla[4][CSN];  // psi, phi, lam rings
+  const int tx = threadIdx.x % CTX, ty = threadIdx.x / CTX;
+  const int x0 = blockIdx.x * CTX, y0 = blockIdx.y * CTY, z0 = blockIdx.z * zc;
+  const int zend = min(z0 + zc, d.nz);
+  const int x = x0 + tx, y = y0 + ty;
+  const bool own = x < d.nx && y < d.ny;
+  const long long n = ncell(d);
+  const long long pst = (long long)d.nx * d.ny;
+  const int c = (ty + 1) * CSW + tx + 1;
+  const PlaneIdx PI = plane_idx(d, x0, y0);
+  double qps[CQ], qph[CQ];
+  float2 qla[CQ];
+  auto load = [&](int z) {
+    const int zw = z < 0 ? z + d.nz : (z >= d.nz ? z - d.nz : z);
+#pragma unroll
+    for (int k = 0; k < CQ; ++k)
+      if (threadIdx.x + k * CNT < CSN) {
+        const long long gi = (long long)zw * pst + PI.off[k];
+        qps[k] = psi[gi];
+        qph[k] = phi[gi];
+        qla[k] = lam[gi];
+      }
+  };
+  auto store = [&](int slot) {
+#pragma unroll
+    for (int k = 0; k < CQ; ++k) {
+      const int q = threadIdx.x + k * CNT;
+      if (q < CSN) {
+        rps[slot][q] = f64_to_df(qps[k]);
+        rph[slot][q] = f64_to_df(qph[k]);
+        rla[slot][q] = qla[k];
+      }
+    }
+  };
+  auto slot = [&](int p) { return (p - (z0 - 1)) & 3; };
+  load(z0 - 1);
+  store(slot(z0 - 1));
+  load(z0);
+  store(slot(z0));
+  load(z0 + 1);
+  const float ih2 = ih * ih, iq = 0.25f * ih2;  // powers of two
+  const double mw = mw_dev[0], sl = slam_dev[0];
+  for (int t = z0; t < zend; ++t) {
+    store(slot(t + 1));
+    __syncthreads();
+    if (t + 1 < zend) load(t + 2);
+    if (!own) continue;
+    const int s0 = slot(t - 1), s1 = slot(t), s2 = slot(t + 1);
+    auto at = [&](const float2 (*r)[CSN], int dx, int dy, int dz) {
+      return r[dz < 0 ? s0 : (dz > 0 ? s2 : s1)][c + dy * CSW + dx];
+    };
+    auto PS = [&](int dx, int dy, int dz) { return at(rps, dx, dy, dz); };
+    auto PH = [&](int dx, int dy, int dz) { return at(rph, dx, dy, dz); };
+    auto LA = [&](int dx, int dy, int dz) { return at(rla, dx, dy, dz); };
+    auto neg = [](float2 v) { return make_float2(-v.x, -v.y); };
+    // a - b of two double-float values, rounded to FP32
+    auto dd = [](float2 a, float2 b) {
+      float s, e;
+      two_sum(a.x, -b.x, s, e);
+      return s + (e + (a.y - b.y));
+    };
+    // triad at this cell: double-float second differences, then FP32
+    const float2 c2 = df_scale(PS(0, 0, 0), -2.0f);
+    auto second = [&](float2 p, float2 m) { return 1.0f + df_add(df_add(p, m), c2).x * ih2; };
+    auto mixed = [&](float2 pp, float2 pm, float2 mp, float2 mm) {
+      return df_add(df_add(pp, neg(pm)), df_add(mm, neg(mp))).x * iq;
+    };
+    float A[3][3];
+    A[0][0] = second(PS(1, 0, 0), PS(-1, 0, 0));
+    A[1][1] = second(PS(0, 1, 0), PS(0, -1, 0));
+    A[2][2] = second(PS(0, 0, 1), PS(0, 0, -1));
+    A[0][1] = A[1][0] = mixed(PS(1, 1, 0), PS(1, -1, 0), PS(-1, 1, 0), PS(-1, -1, 0));
+    A[0][2] = A[2][0] = mixed(PS(1, 0, 1), PS(1, 0, -1), PS(-1, 0, 1), PS(-1, 0, -1));
+    A[1][2] = A[2][1] = mixed(PS(0, 1, 1), PS(0, 1, -1), PS(0, -1, 1), PS(0, -1, -1));
+    float adj[3][3];
+    adj[0][0] = A[1][1] * A[2][2] - A[1][2] * A[1][2];
+    adj[1][1] = A[0][0] * A[2][2] - A[0][2] * A[0][2];
+    adj[2][2] = A[0][0] * A[1][1] - A[0][1] * A[0][1];
+    adj[0][1] = adj[1][0] = A[0][2] * A[1][2] - A[0][1] * A[2][2];
+    adj[0][2] = adj[2][0] = A[0][1] * A[1][2] - A[1][1] * A[0][2];
+    adj[1][2] = adj[2][1] = A[0][1] * A[0][2] - A[0][0] * A[1][2];
+    const float J = A[0][0] * adj[0][0] + A[0][1] * adj[0][1] + A[0][2] * adj[0][2];
+    const float iJ = 1.0f / J;
+    float Ai[3][3], Ai2[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) Ai[a][b] = adj[a][b] * iJ;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) Ai2[a][b] = Ai[a][0] * Ai[0][b] + Ai[a][1] * Ai[1][b] + Ai[a][2] * Ai[2][b];
+    // Bbar at this cell: faces a at i (own) and i - a (left neighbour's face); each face
+    // value G^a_b[phi] (lam_c - lam_{c+a}) / h from differences rounded to FP32 (ih = 1/h)
+    auto fbar = [&](int a, int b, int cx, int cy, int cz) -> float {
+      int px = cx, py = cy, pz = cz;
+      shift(a, 1, px, py, pz);
+      const float Lam = dd(LA(cx, cy, cz), LA(px, py, pz)) * ih;
+      float G;
+      if (a == b) {
+        G = dd(PH(px, py, pz), PH(cx, cy, cz)) * ih;
+      } else {
+        int c1x = cx, c1y = cy, c1z = cz, c2x = cx, c2y = cy, c2z = cz;
+        shift(b, 1, c1x, c1y, c1z);
+        shift(b, -1, c2x, c2y, c2z);
+        int d1x = px, d1y = py, d1z = pz, d2x = px, d2y = py, d2z = pz;
+        shift(b, 1, d1x, d1y, d1z);
+        shift(b, -1, d2x, d2y, d2z);
+        G = 0.25f * (dd(PH(c1x, c1y, c1z), PH(c2x, c2y, c2z)) + dd(PH(d1x, d1y, d1z), PH(d2x, d2y, d2z))) * ih;
+      }
+      return G * Lam;
+    };
+    float Bb[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      int mx = 0, my = 0, mz = 0;
+      shift(a, -1, mx, my, mz);
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+        Bb[a][b] = (sym && b != a) ? 0.f : 0.5f * (fbar(a, b, 0, 0, 0) + fbar(a, b, mx, my, mz));
+    }
+    if (sym) {
+      // symmetric variant: d<lam, S phi>/dC on the ab-edge at base e is
+      //   (1/2h^2) [(lam_e - lam_{e+a+b}) (phi_{e+a+b} - phi_e) + (lam_{e+a} - lam_{e+b}) (phi_{e+a} - phi_{e+b})],
+      // and each of the four edges around this cell takes a quarter of its B^{ab} (a < b).
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = a + 1; b < 3; ++b) {
+          float acc = 0.f;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            int ex = 0, ey = 0, ez = 0;
+            if (k & 1) shift(a, -1, ex, ey, ez);
+            if (k & 2) shift(b, -1, ex, ey, ez);
+            int ax = ex, ay = ey, az = ez, bx = ex, by = ey, bz = ez;
+            shift(a, 1, ax, ay, az);
+            shift(b, 1, bx, by, bz);
+            int px = ax, py = ay, pz = az;
+            shift(b, 1, px, py, pz);
+            acc += dd(LA(ex, ey, ez), LA(px, py, pz)) * dd(PH(px, py, pz), PH(ex, ey, ez)) +
+                   dd(LA(ax, ay, az), LA(bx, by, bz)) * dd(PH(ax, ay, az), PH(bx, by, bz));
+          }
+          Bb[a][b] = 0.125f * acc * ih2;
+        }
+    }
+    // Abar_B = J <Bbar, A^-2> A^-1 - J (A^-1 Bbar A^-2 + A^-2 Bbar A^-1)   (A symmetric)
+    float inner = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) inner += Bb[a][b] * Ai2[a][b];
+    float T1[3][3], T2[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        T1[a][b] = Bb[a][0] * Ai2[0][b] + Bb[a][1] * Ai2[1][b] + Bb[a][2] * Ai2[2][b];  // Bbar A^-2
+        T2[a][b] = Bb[a][0] * Ai[0][b] + Bb[a][1] * Ai[1][b] + Bb[a][2] * Ai[2][b];     // Bbar A^-1
+      }
+    const long long i = (long long)t * pst + (long long)y * d.nx + x;
+    const float Jbar = (float)((delta[i] - mw) * (df_to_f64(LA(0, 0, 0)) - sl));
+    float Ab[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const float t = Ai[a][0] * T1[0][b] + Ai[a][1] * T1[1][b] + Ai[a][2] * T1[2][b] +
+                        Ai2[a][0] * T2[0][b] + Ai2[a][1] * T2[1][b] + Ai2[a][2] * T2[2][b];
+        const float AbB = J * inner * Ai[a][b] - J * t;
+        Ab[a][b] = Jbar * J * Ai[a][b] - AbB;
+      }
+    S[i] = make_float2(Ab[0][0], 0.f);
+    S[n + i] = make_float2(Ab[1][1], 0.f);
+    S[2 * n + i] = make_float2(Ab[2][2], 0.f);
+    auto pair = [](float u, float v) {
+      float s, e;
+      two_sum(u, v, s, e);
+      return make_float2(s, e);
+    };
+    S[3 * n + i] = pair(Ab[0][1], Ab[1][0]);
+    S[4 * n + i] = pair(Ab[0][2], Ab[2][0]);
+    S[5 * n + i] = pair(Ab[1][2], Ab[2][1]);
+  }
+}
+
 // z chunk: at least four waves of four CTAs per SM.
 int curv_zchunk(Dims d) {
   const long long tiles = (long long)((d.nx + CTX - 1) / CTX) * ((d.ny + CTY - 1) / CTY);
@@ -1068,14 +1158,17 @@ __global__ void __launch_bounds__(CNT) k_curv_df_residual_tiled(Dims d, CurvCoef
 
 }  // namespace
 
-cudaError_t launch_psibar(cudaStream_t st, Dims d, const double* psi, const double* phi, const double* lam,
+cudaError_t launch_psibar(cudaStream_t st, Dims d, const double* psi, const double* phi, const float2* lam,
                           const double* delta, const double* mw_dev, const double* slam_dev, double h, int sym,
-                          double* S, double* out) {
-  k_psibar_A<<<cell_grid(d), dim3(BX, BY), 0, st>>>(d, psi, phi, lam, delta, mw_dev, slam_dev, h, sym, S);
+                          float2* S, double* out) {
+  int ex;
+  if (!(h > 0.0) || std::frexp(h, &ex) != 0.5 || ex < -20 || ex > 20) return cudaErrorInvalidValue;  // h = 2^l
+  k_psibar_tiled<<<curv_tiled_grid(d), CNT, 0, st>>>(d, psi, phi, lam, delta, mw_dev, slam_dev, (float)(1.0 / h), sym,
+                                                    S, curv_zchunk(d));
   note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_psibar_H<<<cell_grid(d), dim3(BX, BY), 0, st>>>(d, S, h, out);
+  k_psibar_H<<<cell_grid(d), dim3(BX, BY), 0, st>>>(d, S, (float)(1.0 / (h * h)), out);
   note_launch();
   return cudaGetLastError();
 }

@@ -220,8 +220,8 @@ extern "C" gbmg_status mg_solve_adjoint(gbmg_ctx* c, const double* phi_bar_dev, 
     TRY(launch_finalize(c->stream, part, pr, sc + S_SUM_F, 1.0));
     TRY(launch_finalize(c->stream, part1, pr, sc + S_SUMJ, 1.0));
     TRY(launch_ratio(c->stream, sc + S_SUM_F, sc + S_SUMJ, sc + S_MW));
-    TRY(launch_psibar(c->stream, L0.d, L0.psi, phi_dev, c->adj_lam, source_dev, sc + S_MW, sc + S_SLAM, L0.h,
-                      c->o.curv_sym, c->adj_S, psi_bar_dev));
+    TRY(launch_psibar(c->stream, L0.d, L0.psi, phi_dev, c->phi_df, source_dev, sc + S_MW, sc + S_SLAM, L0.h,
+                      c->o.curv_sym, (float2*)c->adj_S, psi_bar_dev));
   }
   TRY(cudaStreamSynchronize(c->stream));
   c->last = st;

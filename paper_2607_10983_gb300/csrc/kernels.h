@@ -141,11 +141,12 @@ cudaError_t launch_curv_df_residual(cudaStream_t st, Dims d, CurvCoef cf, const 
                                     int scale_J, const float2* u, int form, float* r, double* pr2, double* pf2);
 // partial sums of x * J and of J (df_partial_count(n) blocks each)
 cudaError_t launch_wsum(cudaStream_t st, long long n, const double* x, const float* J, double* pxj, double* pj);
-// psi_bar of the curvilinear adjoint on the finest level (S: 6 n doubles of scratch);
-// sym: the operator is the symmetric variant.
-cudaError_t launch_psibar(cudaStream_t st, Dims d, const double* psi, const double* phi, const double* lam,
+// psi_bar of the curvilinear adjoint on the finest level from the forward solution phi
+// (FP64) and the transposed-solve solution lam (double-float); S: 6 n pairs of scratch;
+// sym: the operator is the symmetric variant; h a power of two.
+cudaError_t launch_psibar(cudaStream_t st, Dims d, const double* psi, const double* phi, const float2* lam,
                           const double* delta, const double* mw_dev, const double* slam_dev, double h, int sym,
-                          double* S, double* out);
+                          float2* S, double* out);
 // out = J (lam - s) (nullable) and lam64 = lam (nullable), from double-float lam
 cudaError_t launch_jscale(cudaStream_t st, long long n, const float2* lam, const float* J, const double* s_dev,
                           double* out, double* lam64);
