@@ -159,6 +159,36 @@ def test_double_float_residual_is_the_fp64_residual(gb, shape, sym, monkeypatch)
     assert abs(rel - st.rel_res) < 0.05 * st.rel_res + 1e-14
 
 
+@pytest.mark.parametrize("shape", [(16, 24, 32), (32, 32, 32)])
+def test_transposed_double_float_residual_is_the_fp64_residual(gb, shape, monkeypatch):
+    # The adjoint's transposed solve M^T lam = phi_bar - mean(phi_bar) to 1e-12: its
+    # residual, evaluated in FP64 by the oracle's exact transpose with the GPU's FP32
+    # coefficients and FP32 face means, is the one the double-float kernel reported.
+    # lam is recovered up to a constant (which M^T annihilates) from source_bar = J (lam - s).
+    def face32(B, a, b):
+        c = B[a, b].astype(np.float32)
+        return (np.float32(0.5) * (c + curv.at(c, a, 1))).astype(np.float64)
+
+    psi = psi_field(shape, 19)
+    pbar = grf(shape, 20)
+    s = make(gb, shape, psi)
+    dbar, _, st = s.solve_adjoint(to_dev(pbar), tol=1e-12, max_vcycles=300)
+    assert st.status == 0 and st.rel_res <= 1e-12
+    J, B6 = s.curv_geometry(0)
+    J, B6 = J.double().cpu().numpy(), B6.double().cpu().numpy()
+    B = np.empty((3, 3) + shape)
+    for k, (a, b) in enumerate([(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]):
+        B[a, b] = B6[k]
+        B[b, a] = B6[k]
+    lam = dbar.cpu().numpy() / J
+    g = pbar - pbar.mean()
+    monkeypatch.setattr(curv, "face_coeff", face32)
+    res = (g - curv.apply_MT(lam, B, 1.0)) / J
+    rel = float(np.linalg.norm(res) / np.linalg.norm(g / J))
+    assert rel < 2e-12
+    assert abs(rel - st.rel_res) < 0.05 * st.rel_res + 1e-14
+
+
 def test_adjoint_matches_oracle(gb):
     shape = (16, 16, 16)
     psi = psi_field(shape, 14, 1.5, 0.4)
