@@ -262,15 +262,23 @@ __global__ void k_df_to_f64_x2(long long n, const float4* __restrict__ in, const
     ms.y = -ms.y;
   }
   const long long n2 = n / 2;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
-    const float4 v = in[i];
+  auto conv = [&](float4 v) {
     float2 a = make_float2(v.x, v.y), b = make_float2(v.z, v.w);
     if (shift) {
       a = df_add(a, ms);
       b = df_add(b, ms);
     }
-    out[i] = make_double2(df_to_f64(a), df_to_f64(b));
+    return make_double2(df_to_f64(a), df_to_f64(b));
+  };
+  // two grid strides per iteration: both loads are in flight before either conversion
+  const long long G = (long long)gridDim.x * blockDim.x;
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (; i + G < n2; i += 2 * G) {
+    const float4 v0 = in[i], v1 = in[i + G];
+    out[i] = conv(v0);
+    out[i + G] = conv(v1);
   }
+  if (i < n2) out[i] = conv(in[i]);
   if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
     float2 a = reinterpret_cast<const float2*>(in)[n - 1];
     if (shift) a = df_add(a, ms);
