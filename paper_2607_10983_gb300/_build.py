@@ -1,6 +1,6 @@
 """Build the CUDA library libgbmg.so in-tree for sm_103a (and the oracle's C parts, if any).
 
-Each .cu file under csrc/ is compiled to an object file in parallel, then linked
+Each .cu (and host-only .cpp) file under csrc/ is compiled to an object file in parallel, then linked
 into paper_2607_10983_gb300/_build/libgbmg.so.  Rebuilds only when a source or
 header is newer than the library.
 """
@@ -31,7 +31,7 @@ def nvcc() -> str:
 
 
 def sources() -> list[str]:
-    return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
 
 
 def _deps() -> list[str]:
@@ -47,7 +47,7 @@ def up_to_date() -> bool:
 
 
 def _compile(src: str, extra: list[str]) -> str:
-    obj = os.path.join(OUT_DIR, os.path.basename(src).replace(".cu", ".o"))
+    obj = os.path.join(OUT_DIR, os.path.splitext(os.path.basename(src))[0] + ".o")
     cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

@@ -12,11 +12,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-namespace gbmg {
+#include "host_math.h"
 
-struct Dims {
-  int nx, ny, nz;
-};
+namespace gbmg {
 
 __host__ __device__ __forceinline__ long long ncell(Dims d) { return (long long)d.nx * d.ny * d.nz; }
 

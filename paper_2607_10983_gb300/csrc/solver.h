@@ -27,13 +27,9 @@ gbmg_status fail(gbmg_status s, const std::string& msg);
 gbmg_status cuda_fail(cudaError_t e, const char* what);
 extern thread_local std::string g_last_error;
 
-std::vector<Dims> level_dims(int nx, int ny, int nz, int levels);
 // curvilinear / adjoint drivers (curv_solve.cu)
 gbmg_status curv_solve(gbmg_ctx* c, const double* F, double* phi, double tol, int maxv, gbmg_stats& st);
 
-bool dense_pinv(int n, const std::vector<double>& Lm, const std::vector<double>& w, std::vector<double>& G);
-std::vector<double> dense_flat(Dims d, double h);
-void chebyshev_schedule(int degree, double alpha, std::vector<double>& c1, std::vector<double>& c2);
 // Parameters of the single-CTA bottom cycle from level l (false when it does not apply).
 bool small_cycle_params(const gbmg_ctx* c, int l, SmallCycle* out);
 
