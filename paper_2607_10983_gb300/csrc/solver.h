@@ -105,7 +105,6 @@ namespace gbmg {
     if (s_ != GBMG_OK) return s_;   \
   } while (0)
 
-
 struct DeviceGuard {
   int prev = -1;
   explicit DeviceGuard(int dev) {
@@ -147,48 +146,5 @@ inline gbmg_status read_rel(gbmg_ctx* c, double& rel) {
   rel = f2 > 0.0 ? std::sqrt(r2 / f2) : std::sqrt(r2);
   return GBMG_OK;
 }
-
-// Convergence bookkeeping shared by the solve drivers: stop at tol, at max_vcycles,
-// on a non-finite residual, or when the residual grew tenfold over two cycles.
-struct Monitor {
-  gbmg_stats& st;
-  double tol;
-  int maxv;
-  std::vector<double> hist;  // hist[k] = relative residual after k cycles
-  Monitor(gbmg_stats& s, double t, int m) : st(s), tol(t), maxv(m) {}
-  void start(double rel) {
-    st.rel_res0 = rel;
-    st.rel_res = rel;
-    st.cycles = 0;
-    st.status = GBMG_OK;
-    hist.assign(1, rel);
-  }
-  bool done() {
-    if (!std::isfinite(st.rel_res)) {
-      st.status = GBMG_ERR_NONFINITE;
-      return true;
-    }
-    if (st.rel_res <= tol) return true;
-    if (st.cycles >= maxv) {
-      st.status = GBMG_ERR_NOT_CONVERGED;
-      return true;
-    }
-    return false;
-  }
-  // record the residual after one more cycle; true if the solve must stop (diverged)
-  bool record(double rel) {
-    if (st.cycles < 64) st.res_hist[st.cycles] = rel;
-    st.cycles += 1;
-    st.rel_res = rel;
-    hist.push_back(rel);
-    const size_t k = hist.size() - 1;
-    if (k >= 2 && std::isfinite(rel) && rel > 10.0 * hist[k - 2]) {
-      st.status = GBMG_ERR_DIVERGED;
-      return true;
-    }
-    return false;
-  }
-};
-
 
 }  // namespace gbmg

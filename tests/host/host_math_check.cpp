@@ -5,7 +5,10 @@
 //   cheb degree alpha              -> c1[0..degree-1] then c2[0..degree-1]
 //   flat nx ny nz h                -> the dense operator, row-major
 //   pinv n w[0..n-1] L[0..n*n-1]   -> 1 and G row-major, or 0 when singular
+//   monitor tol maxv k r[0..k-1]   -> status cycles rel_res0 rel_res res_hist[0..cycles-1] of
+//                                     the solve loop's bookkeeping fed the residuals r[0], r[1], ...
 #include <cstdio>
+#include <cstdlib>
 #include <iostream>
 #include <string>
 #include <vector>
@@ -45,6 +48,24 @@ int main() {
       const bool ok = gbmg::dense_pinv(n, L, w, G);
       std::printf("%d ", ok ? 1 : 0);
       if (ok) put(G);
+    } else if (cmd == "monitor") {
+      double tol;
+      int maxv, k;
+      std::cin >> tol >> maxv >> k;
+      std::vector<double> r(k);
+      for (double& x : r) {
+        std::string t;
+        std::cin >> t;
+        x = std::strtod(t.c_str(), nullptr);  // accepts nan and inf
+      }
+      gbmg_stats st{};
+      gbmg::Monitor mon(st, tol, maxv);
+      mon.start(r[0]);
+      // the solve loops: one V-cycle per pass, then the residual it left
+      for (int i = 1; !mon.done() && i < k; ++i)
+        if (mon.record(r[i])) break;
+      std::printf("%d %d %.17g %.17g ", (int)st.status, st.cycles, st.rel_res0, st.rel_res);
+      for (int i = 0; i < st.cycles && i < 64; ++i) std::printf("%.17g ", st.res_hist[i]);
     } else {
       std::fprintf(stderr, "unknown command %s\n", cmd.c_str());
       return 2;

@@ -3,7 +3,8 @@ own with the host C++ compiler: the level ladder against the paper's level count
 (Sec. 4.3.3), the Chebyshev schedule against the closed-form error polynomial of the
 semi-iteration (Sec. 2.3), the dense coarsest-level operator against a Kronecker
 construction of the periodic 7-point stencil, and the minimum-norm inverse of the
-coarsest solve against numpy's pseudo-inverse and its defining identities."""
+coarsest solve against numpy's pseudo-inverse and its defining identities, and the
+convergence monitor of the solve loops on residual sequences built to end each way."""
 import os
 import shutil
 import subprocess
@@ -21,7 +22,7 @@ def run(tmp_path_factory):
     if cxx is None:
         pytest.skip("no host C++ compiler")
     exe = str(tmp_path_factory.mktemp("host") / "host_math_check")
-    subprocess.run([cxx, "-std=c++17", "-O2", "-Wall", "-Werror", "-I", CSRC,
+    subprocess.run([cxx, "-std=c++17", "-O2", "-Wall", "-Werror", "-I", CSRC, "-I", os.path.join(ROOT, "include"),
                     os.path.join(ROOT, "tests", "host", "host_math_check.cpp"),
                     os.path.join(CSRC, "host_math.cpp"), "-o", exe], check=True)
 
@@ -112,6 +113,44 @@ def test_dense_pinv_identities_on_a_nonsymmetric_singular_operator(run):
     # a bordered system that is singular is reported, not inverted
     ok0, _ = _pinv_call(run, np.zeros((4, 4)), np.ones(4))
     assert ok0 == 0
+
+
+def _status_codes():
+    codes = {}
+    with open(os.path.join(ROOT, "include", "gbmg.h")) as fh:
+        for line in fh:
+            part = line.split("/*")[0].strip().rstrip(",")
+            if part.startswith("GBMG_") and "=" in part:
+                name, val = (x.strip() for x in part.split("="))
+                codes[name] = int(val)
+    return codes
+
+
+@pytest.mark.parametrize("case", ["converged", "at_start", "budget", "nonfinite", "diverged", "slow_growth",
+                                  "long"])
+def test_convergence_monitor(run, case):
+    S = _status_codes()
+    geo = [0.1 ** k for k in range(8)]                         # 1 ... 1e-7
+    tol, maxv, seq, want_status, want_cycles = {
+        "converged": (2e-6, 100, geo, "GBMG_OK", 6),
+        "at_start": (1e-6, 100, [1e-7, 1.0], "GBMG_OK", 0),
+        "budget": (1e-12, 3, [2.0 ** -k for k in range(10)], "GBMG_ERR_NOT_CONVERGED", 3),
+        "nonfinite": (1e-6, 100, [1.0, 0.5, float("nan"), 0.1], "GBMG_ERR_NONFINITE", 2),
+        # tenfold growth over two cycles stops the solve at once; slower growth does not
+        "diverged": (1e-6, 100, [1.0, 0.5, 0.9, 5.01, 0.01], "GBMG_ERR_DIVERGED", 3),
+        "slow_growth": (1e-6, 100, [1.0, 0.5, 9.9, 4.9, 1e-7], "GBMG_OK", 4),
+        "long": (1e-30, 80, [0.9 ** k for k in range(100)], "GBMG_ERR_NOT_CONVERGED", 80),
+    }[case]
+    line = "monitor %r %d %d %s" % (tol, maxv, len(seq), " ".join(repr(float(x)) for x in seq))
+    (v,) = run(line)
+    status, cycles = int(v[0]), int(v[1])
+    assert status == S[want_status] and cycles == want_cycles
+    assert v[2] == seq[0]
+    last = seq[cycles]
+    assert (np.isnan(v[3]) and np.isnan(last)) or v[3] == last
+    hist = v[4:]
+    assert len(hist) == min(cycles, 64)
+    np.testing.assert_array_equal(hist, np.array(seq[1:1 + len(hist)]))
 
 
 def test_library_defines_every_internal_symbol():
