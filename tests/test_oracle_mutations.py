@@ -1,8 +1,9 @@
 """Plants plausible mistakes in the oracle (on the CPU, one at a time, through
 monkeypatch) and checks that its pins catch each one: a dropped term, a flipped sign, a
 wrong weight or normalisation, an operand that is not the transpose, an index shifted
-by one, a missing projection.  Each planted mistake must make at least one of the pin
-tests named beside it fail with an AssertionError."""
+by one, a missing projection, a skipped coarse correction or preconditioner.  Each
+planted mistake must make at least one of the pin tests named beside it fail with an
+AssertionError."""
 import os
 
 import numpy as np
@@ -65,6 +66,24 @@ def _read_shifted(orig):
     return lambda field, pos: orig(np.roll(field, 1, axis=-1), pos)
 
 
+def _vjp_psi_bar_sign(orig):
+    def f(*a, **k):
+        dbar, pbar = orig(*a, **k)
+        return dbar, -pbar
+    return f
+
+
+def _predict_wrong_weight(orig):
+    def f(history, order, growth=1.0):
+        out = orig(history, order, growth)
+        return out + 0.01 * (history[0] - history[1]) if order >= 1 and len(history) > 1 else out
+    return f
+
+
+def _pcg_no_preconditioner(orig):
+    return lambda r, steps, precond, apply: orig(r, steps, lambda v: v, apply)
+
+
 MUTANTS = {
     "apply_A drops the z second difference": (
         flat, "apply_A", _drop_z_term, [lambda: TF.test_plane_wave_eigenvalue((8, 12, 16))]),
@@ -107,6 +126,18 @@ MUTANTS = {
         grad, "grad4_T", _grad_T_not_transpose, [TG.test_grad_transposes]),
     "CIC paint shifted by one cell": (
         pm, "cic_paint", _shift_x, [TP.test_paint_conserves_mass_and_hits_nodes, TP.test_read_is_transpose_of_paint]),
+    "V-cycle without the coarse correction": (
+        flat, "prolong", lambda o: (lambda ec: np.zeros(tuple(2 * n for n in ec.shape))),
+        [TF.test_plain_method_32_converges_to_fft, lambda: TF.test_convergence_factor_mesh_independent(GOLDEN)]),
+    "predictor with a wrong extrapolation weight": (
+        flat, "predict", _predict_wrong_weight, [TF.test_predictors_exact_on_their_sequences]),
+    "PCG without its preconditioner": (
+        flat, "pcg", _pcg_no_preconditioner, [TF.test_pcg_exact_preconditioner_converges_in_one_step]),
+    "psi_bar with its sign flipped": (
+        curv, "solve_vjp", _vjp_psi_bar_sign, [TC.test_vjp_against_central_differences]),
+    "binomial smoothing one pass short": (
+        curv, "smooth_binomial", lambda o: (lambda u, passes: o(u, max(0, passes - 1))),
+        [TC.test_binomial_smoothing_plane_wave_factor]),
     "CIC read from the wrong cell": (
         pm, "cic_read", _read_shifted, [TP.test_read_is_transpose_of_paint, TP.test_read_interpolates_linear_fields_exactly]),
 }
