@@ -74,9 +74,9 @@ def measured_peaks():
 
 
 KERNEL_SOURCES = {
-    "down0": ["legs.cuh", "legs.cu", "packed.cuh", "stencil.cuh", "common.cuh"],
-    "up0": ["legs.cuh", "legs.cu", "packed.cuh", "stencil.cuh", "common.cuh"],
-    "df0": ["dfk.cuh", "fused_kernels.cu", "packed.cuh", "stencil.cuh", "common.cuh"],
+    "down0": ["legs.cuh", "legs.cu", "packed.cuh", "stencil.cuh", "common.cuh", "host_math.h"],
+    "up0": ["legs.cuh", "legs.cu", "packed.cuh", "stencil.cuh", "common.cuh", "host_math.h"],
+    "df0": ["dfk.cuh", "fused_kernels.cu", "packed.cuh", "stencil.cuh", "common.cuh", "host_math.h"],
 }
 
 
