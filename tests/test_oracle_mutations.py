@@ -84,6 +84,24 @@ def _pcg_no_preconditioner(orig):
     return lambda r, steps, precond, apply: orig(r, steps, lambda v: v, apply)
 
 
+def _motion_source_sign(orig):
+    def f(*a, **k):
+        new, psidot = orig(*a, **k)
+        return -new, -psidot
+    return f
+
+
+def _force_sign(orig):
+    def f(*a, **k):
+        phi, F = orig(*a, **k)
+        return phi, -F
+    return f
+
+
+def _sym_not_symmetric(orig):
+    return lambda u, B, h=1.0: orig(u, B, h) + 0.01 * curv.at(u, 0, 1)
+
+
 MUTANTS = {
     "apply_A drops the z second difference": (
         flat, "apply_A", _drop_z_term, [lambda: TF.test_plane_wave_eigenvalue((8, 12, 16))]),
@@ -138,6 +156,18 @@ MUTANTS = {
     "binomial smoothing one pass short": (
         curv, "smooth_binomial", lambda o: (lambda u, passes: o(u, max(0, passes - 1))),
         [TC.test_binomial_smoothing_plane_wave_factor]),
+    "mesh-motion source with the wrong sign": (
+        curv, "mesh_motion_step", _motion_source_sign, [TC.test_mesh_motion_flat_mesh_is_spectral_solve]),
+    "PM force with the wrong sign": (
+        pm, "pm_force", _force_sign, [TP.test_force_pipeline_is_antisymmetric_for_a_pair]),
+    "Jacobi diagonal doubled": (
+        curv, "diag_M", lambda o: _scale(o, 2.0), [TC.test_psi_zero_solve_equals_flat_jacobi_cycle]),
+    "symmetric variant not symmetric": (
+        curv, "apply_M_sym", _sym_not_symmetric, [TC.test_sym_operator_is_symmetric_with_19_points]),
+    "symmetric-variant B cotangent off by 1%": (
+        curv, "Bbar_from_operator_sym", lambda o: _scale(o, 1.01), [TC.test_sym_Bbar_is_the_derivative_of_the_bilinear_form]),
+    "second-order gradient off by 1%": (
+        grad, "grad2", lambda o: _scale(o, 1.01), [TG.test_grad_symbols]),
     "CIC read from the wrong cell": (
         pm, "cic_read", _read_shifted, [TP.test_read_is_transpose_of_paint, TP.test_read_interpolates_linear_fields_exactly]),
 }
