@@ -363,6 +363,17 @@ gbmg_status mg_curv_apply(gbmg_ctx* ctx, int level, int dtype, int transpose, in
 /* Copy the geometry of a level: J (n floats) and B packed xx, yy, zz, xy, xz, yz (6 n
  * floats); either pointer may be NULL. */
 gbmg_status mg_curv_geometry(gbmg_ctx* ctx, int level, float* J_dev, float* B_dev);
+/* The FP32 level kernels of that V-cycle, one launch each, on level `level` (n floats
+ * per buffer, distinct buffers).  mg_curv_residual: out = r - op(u) / (h_l^2 J), the
+ * residual of L = M / J (Sec. 4.3, Eq. curv_linsys) or of the transposed-solve operator
+ * M^T / J.  mg_curv_smooth: one weighted-Jacobi sweep (Appendix B, Eq. jacobi)
+ * e_out = e_in + omega (J r - op(e_in) / h_l^2) / D with D the stencil's diagonal
+ * (op / h_l^2 applied to a unit vector), omega = opts.omega; e_in and e_out must differ.
+ * op as in mg_curv_apply. */
+gbmg_status mg_curv_residual(gbmg_ctx* ctx, int level, int transpose, const float* r_dev, const float* u_dev,
+                             float* out_dev);
+gbmg_status mg_curv_smooth(gbmg_ctx* ctx, int level, int transpose, const float* e_in_dev, const float* r_dev,
+                           float* e_out_dev);
 /* One FP32 curvilinear V-cycle (weighted Jacobi nu1/nu2) on L e = r (transpose 0) or on
  * the transposed-solve operator M^T / J (transpose 1), from e = 0 (S / J for either
  * value with opts.curv_sym). */
@@ -395,14 +406,19 @@ gbmg_status mg_df_residual(gbmg_ctx* ctx, const float* F_df_dev, double m, const
  * Writes rel_out_dev[0] = ||F - m - A phi|| / ||F - m|| (a device double), with
  * F = source_dev, phi = phi_dev (nx*ny*nz doubles on the current device),
  * m = mean(F) and A the 7-point periodic Laplacian with unit spacing: the quantity
- * mg_solve reports as rel_res0.  The residual is evaluated in double-float.
+ * mg_solve reports as rel_res0.  The residual is evaluated in double-float and rounded
+ * to FP32 per cell; the squares are summed in compensated (double-float) sums per
+ * plane and in FP64 across planes, so the ratio carries about 1e-7 relative error at
+ * any mesh size.
  *
  * Scratch: one fixed array of 2 * GBMG_NOALLOC_MAX_NZ + 8 doubles (about 64 KiB) in
  * the library's own device memory, held by every GPU that loads the library until
  * the process exits.  nz above GBMG_NOALLOC_MAX_NZ (or a side below 4) is rejected
  * with GBMG_ERR_INVALID_ARG.  The first call on a device looks the array's address
  * up on that device, with that device current; make that first call before any
- * stream capture.  Every call overwrites the scratch entries it reads (nothing has
+ * stream capture.  The address is kept for the life of the process: after a
+ * cudaDeviceReset of a device the library's device memory there is gone, and this call
+ * must not be used on that device again.  Every call overwrites the scratch entries it reads (nothing has
  * to start at zero) and the array keeps the last call's contents; all calls share
  * it, so calls that overlap on the GPU (unordered streams) race.  The work is
  * queued on cuda_stream (NULL = legacy default stream); the call does not wait.

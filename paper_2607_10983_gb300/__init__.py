@@ -99,6 +99,8 @@ _SIGS = {
     "mg_curv_apply": (_S, [_P, _I, _I, _I, _I, _P, _P]),
     "mg_curv_geometry": (_S, [_P, _I, _P, _P]),
     "mg_curv_vcycle": (_S, [_P, _I, _P, _P]),
+    "mg_curv_residual": (_S, [_P, _I, _I, _P, _P, _P]),
+    "mg_curv_smooth": (_S, [_P, _I, _I, _P, _P, _P]),
     "mg_profile_begin": (_S, [_P, _I]),
     "mg_profile_read": (_S, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "mg_profile_end": (_S, [_P]),
@@ -287,6 +289,22 @@ class Solver:
         B = torch.empty((6,) + shp, dtype=torch.float32, device=dev)
         _check(lib().mg_curv_geometry(self._c(), level, _ptr(J), _ptr(B)))
         return J, B
+
+    def curv_residual(self, level: int, r: torch.Tensor, u: torch.Tensor, transpose: bool = False):
+        """FP32 residual r - op(u) / (h^2 J) of a level (the V-cycle's tiled kernel)."""
+        shp = self.level_shape(level)
+        out = torch.empty_like(r)
+        _check(lib().mg_curv_residual(self._c(), level, int(transpose), _ptr(r, torch.float32, shp),
+                                      _ptr(u, torch.float32, shp), _ptr(out)))
+        return out
+
+    def curv_smooth(self, level: int, e: torch.Tensor, r: torch.Tensor, transpose: bool = False):
+        """One FP32 weighted-Jacobi sweep of a level (the V-cycle's tiled kernel); returns the new e."""
+        shp = self.level_shape(level)
+        out = torch.empty_like(e)
+        _check(lib().mg_curv_smooth(self._c(), level, int(transpose), _ptr(e, torch.float32, shp),
+                                    _ptr(r, torch.float32, shp), _ptr(out)))
+        return out
 
     def curv_vcycle(self, r: torch.Tensor, transpose: bool = False):
         out = torch.empty_like(r)

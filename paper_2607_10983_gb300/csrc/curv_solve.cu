@@ -245,6 +245,33 @@ extern "C" gbmg_status mg_curv_apply(gbmg_ctx* c, int level, int dtype, int tran
   return GBMG_OK;
 }
 
+// FP32 tiled kernels of the V-cycle's levels, one launch each (for tests and composition).
+static gbmg_status curv_component_check(gbmg_ctx* c, int level, const void* a, const void* b, const void* o,
+                                        const char* who) {
+  if (!c || !a || !b || !o || level < 0 || level >= c->L) return fail(GBMG_ERR_INVALID_ARG, std::string(who) + ": bad argument");
+  if (c->o.op != GBMG_OP_CURV19 || !c->geom_ready) return fail(GBMG_ERR_STATE, std::string(who) + ": no geometry set");
+  return GBMG_OK;
+}
+
+extern "C" gbmg_status mg_curv_residual(gbmg_ctx* c, int level, int transpose, const float* r, const float* u,
+                                        float* out) {
+  TRYS(curv_component_check(c, level, r, u, out, "mg_curv_residual"));
+  DeviceGuard g(c->device);
+  const Level& L = c->lv[level];
+  TRY(launch_curv_residual<float>(c->stream, L.d, L.cc, r, u, out, curv_form(c, transpose != 0), nullptr));
+  return GBMG_OK;
+}
+
+extern "C" gbmg_status mg_curv_smooth(gbmg_ctx* c, int level, int transpose, const float* e_in, const float* r,
+                                      float* e_out) {
+  TRYS(curv_component_check(c, level, e_in, r, e_out, "mg_curv_smooth"));
+  if (e_in == e_out) return fail(GBMG_ERR_INVALID_ARG, "mg_curv_smooth: e_in and e_out must differ");
+  DeviceGuard g(c->device);
+  const Level& L = c->lv[level];
+  TRY(launch_curv_jacobi<float>(c->stream, L.d, L.cc, r, e_in, e_out, curv_form(c, transpose != 0), (float)c->o.omega));
+  return GBMG_OK;
+}
+
 extern "C" gbmg_status mg_curv_geometry(gbmg_ctx* c, int level, float* J_out, float* B_out) {
   if (!c || level < 0 || level >= c->L) return fail(GBMG_ERR_INVALID_ARG, "mg_curv_geometry: bad argument");
   if (c->o.op != GBMG_OP_CURV19 || !c->geom_ready) return fail(GBMG_ERR_STATE, "mg_curv_geometry: no geometry set");

@@ -9,6 +9,7 @@
 // process exits.  Host code may not use the symbol as an address; the address of
 // the array on each device is obtained once with cudaGetSymbolAddress, on the first
 // call made on that device, with that device current.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 
@@ -26,7 +27,9 @@ constexpr int SCRATCH_DOUBLES = 2 * NOALLOC_MAX_NZ + 8;
 static __device__ __align__(256) double g_noalloc_scratch[SCRATCH_DOUBLES];
 
 constexpr int MAX_DEVICES = 64;
-double* g_scratch_addr[MAX_DEVICES] = {nullptr};
+// Device address of g_noalloc_scratch per device, looked up on the first call there.
+// Atomic: first calls from several host threads may race; each stores the same value.
+std::atomic<double*> g_scratch_addr[MAX_DEVICES];
 
 constexpr int NT = 256;
 
@@ -35,9 +38,9 @@ __global__ void k_plane_sum(gbmg::Dims d, const double* __restrict__ F, double* 
   __shared__ double sh[32];
   const int z = blockIdx.x;
   const long long base = (long long)z * d.nx * d.ny;
-  const int np = d.nx * d.ny;
+  const long long np = (long long)d.nx * d.ny;
   gbmg::DfAcc s{0.f, 0.f};
-  for (int i = threadIdx.x; i < np; i += blockDim.x) {
+  for (long long i = threadIdx.x; i < np; i += blockDim.x) {
     const float2 v = gbmg::f64_to_df(F[base + i]);
     s.add(v.x);
     s.c += v.y;
@@ -55,19 +58,20 @@ __global__ void k_mean(int nz, double inv_n, double* __restrict__ scratch) {
   if (threadIdx.x == 0) scratch[2 * NOALLOC_MAX_NZ] = s * inv_n;
 }
 
-// One block per z plane: sums of (F - m)^2 and of r^2, r = F - m - A phi in double-float.
+// One block per z plane: sums of (F - m)^2 and of r^2, r = F - m - A phi in double-float;
+// each square is rounded to FP32 and accumulated in a compensated (double-float) sum.
 __global__ void k_plane_resid(gbmg::Dims d, const double* __restrict__ F, const double* __restrict__ phi,
                               double* __restrict__ scratch) {
   __shared__ double sh[32];
   const int z = blockIdx.x;
-  const int np = d.nx * d.ny;
+  const long long np = (long long)d.nx * d.ny;
   const long long pst = np;
   const long long base = (long long)z * pst;
   const long long zm = (long long)(z == 0 ? d.nz - 1 : z - 1) * pst, zp = (long long)(z == d.nz - 1 ? 0 : z + 1) * pst;
   const float2 m = gbmg::f64_to_df(scratch[2 * NOALLOC_MAX_NZ]);
-  float f2 = 0.f, r2 = 0.f;
-  for (int i = threadIdx.x; i < np; i += blockDim.x) {
-    const int x = i % d.nx, y = i / d.nx;
+  gbmg::DfAcc f2{0.f, 0.f}, r2{0.f, 0.f};
+  for (long long i = threadIdx.x; i < np; i += blockDim.x) {
+    const int x = (int)(i % d.nx), y = (int)(i / d.nx);
     const int xm = x == 0 ? d.nx - 1 : x - 1, xp = x == d.nx - 1 ? 0 : x + 1;
     const int ym = y == 0 ? d.ny - 1 : y - 1, yp = y == d.ny - 1 ? 0 : y + 1;
     auto P = [&](long long zo, int xx, int yy) { return gbmg::f64_to_df(phi[zo + (long long)yy * d.nx + xx]); };
@@ -75,11 +79,11 @@ __global__ void k_plane_resid(gbmg::Dims d, const double* __restrict__ F, const 
     const float r = gbmg::df_resid(P(base, x, y), P(base, xm, y), P(base, xp, y), P(base, x, ym), P(base, x, yp),
                                    P(zm, x, y), P(zp, x, y), f, m);
     const float fm = __fadd_rn(__fsub_rn(f.x, m.x), __fsub_rn(f.y, m.y));
-    f2 += fm * fm;
-    r2 += r * r;
+    f2.add(fm * fm);
+    r2.add(r * r);
   }
-  const double bf = gbmg::block_sum_f(f2, sh);
-  const double br = gbmg::block_sum_f(r2, sh);
+  const double bf = gbmg::block_sum_acc(f2, sh);
+  const double br = gbmg::block_sum_acc(r2, sh);
   if (threadIdx.x == 0) {
     scratch[z] = bf;
     scratch[NOALLOC_MAX_NZ + z] = br;
@@ -115,14 +119,15 @@ extern "C" gbmg_status mg_rel_residual_noalloc(int nx, int ny, int nz, const dou
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return gbmg::cuda_fail(e, "mg_rel_residual_noalloc: cudaGetDevice");
   if (dev < 0 || dev >= MAX_DEVICES) return gbmg::fail(GBMG_ERR_INVALID_ARG, "mg_rel_residual_noalloc: device index above 63");
-  if (!g_scratch_addr[dev]) {
+  double* scratch = g_scratch_addr[dev].load(std::memory_order_acquire);
+  if (!scratch) {
     // set-up on the first call on this device (this device is current)
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return gbmg::cuda_fail(e, "mg_rel_residual_noalloc: cudaGetSymbolAddress");
-    g_scratch_addr[dev] = (double*)p;
+    scratch = (double*)p;
+    g_scratch_addr[dev].store(scratch, std::memory_order_release);
   }
-  double* scratch = g_scratch_addr[dev];
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const gbmg::Dims d{nx, ny, nz};
   k_plane_sum<<<nz, NT, 0, st>>>(d, source_dev, scratch);

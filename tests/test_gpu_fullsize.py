@@ -3,9 +3,10 @@
 512^3 warm-started sequence (device buffers, and host buffers through the sequence entry
 point), 256^3 differentiable flat solve, 256^3 moving-mesh solve with its adjoint, and the
 48-problem batch.  The oracle computes what it can at these
-sizes in seconds (FFT solves, one application of the FP64 curvilinear operator);
-the rest is checked through properties that hold at any size (residual of the FP64
-operator, central finite differences of the GPU forward map).
+sizes in seconds (FFT solves, one application of the FP64 curvilinear operator and of
+its transpose, the psi-bar cotangent chain given the GPU's phi and lam); the rest is
+checked through properties that hold at any size (residual of the FP64 operator,
+central finite differences of the GPU forward map).
 """
 import numpy as np
 import pytest
@@ -107,6 +108,26 @@ def test_moving_mesh_256(gb):
     dbar, psibar, st = s.solve_adjoint(pbar, phi=phi_t, source=to_dev(delta), want_psi_bar=True, tol=1e-10,
                                        max_vcycles=200)
     assert st.status == 0
+    # psi_bar element by element: the oracle's cotangent chain (Sec. 4.8, Eq. adj_op:
+    # B-cotangent of <lam, M phi>, triad cotangents of B = J A^-2 and of J, transposed
+    # Hessian) fed with the GPU's phi and the GPU's lam.  source_bar = J (lam - <lam>_J)
+    # with the GPU's FP32 J gives lam up to a constant, which neither cotangent sees.
+    J32 = J.double().cpu().numpy()
+    lam = dbar.cpu().numpy() / J32
+    lam -= lam.mean()
+    ph = phi_t.cpu().numpy()
+    A = curv.triad(psi, 1.0)
+    f = curv.weighted_projection(delta, lev.J)
+    Jbar = f * (lam - float((lam * lev.J).sum() / lev.J.sum()))
+    Abar = curv.Abar_from_J(A, Jbar) - curv.Abar_from_B(A, curv.Bbar_from_operator(lam, ph, 1.0))
+    del A
+    ref_psibar = curv.hessian_T(Abar, 1.0)
+    del Abar
+    assert rel_l2(psibar.cpu().numpy(), ref_psibar) < 1e-5
+    # and lam solves the transposed system under the oracle's FP64 operator
+    g = pbar.cpu().numpy() - float(pbar.mean())
+    res = np.linalg.norm((g - curv.apply_MT(lam, lev.B, 1.0)) / lev.J) / np.linalg.norm(g / lev.J)
+    assert res < 2e-6
     wd = to_dev(w)
 
     def L(d, p):
