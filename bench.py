@@ -202,59 +202,102 @@ def sources(n, seq, rank):
     return [d0 + (0.05 * t) * eta for t in range(seq)]
 
 
-# ------------------------------------------------------------------ CPU oracle sample
+# ------------------------------------------------------------------ CPU oracle
 
-def oracle_sample(n_full, seq, tol):
-    """One oracle V-cycle at 256^3 (scaled by (n/256)^3) times the oracle's cycles per solve.
+def workload_config(args, levels):
+    """The workload both arms run (the same dict on both lines)."""
+    return {"workload": f"periodic 3-D Poisson {args.n}^3, warm-started sequence of {args.seq} GRF sources "
+                        f"(P(k)~k^-2), tol {args.tol:g}, V({args.degree},{args.degree}) Chebyshev, {levels} levels",
+            "n": args.n, "sources": args.seq, "tol": args.tol, "levels": levels,
+            "l2": "inputs larger than L2 (1 GiB per field)"}
 
-    The cycles per solve come from the oracle's own solve of the same source recipe at
-    64^3 (the V-cycle's convergence factor is mesh-independent).
-    """
+
+def oracle_sample(src0, src1, args):
+    """The C FP64 V-cycle oracle (OpenMP over all host cores) on the first two solves of the
+    sequence: t = 0 from zero, t = 1 warm-started from the oracle's own t = 0 solution."""
     import numpy as np
 
-    from oracle import flat
-    from synth import grf
-    ns = min(256, n_full)
-    r = grf(ns, 5)
-    t0 = time.perf_counter()
-    flat.vcycle(0, np.zeros_like(r), r, len(flat.level_shapes(r.shape)))
-    t_cycle = (time.perf_counter() - t0) * (n_full / ns) ** 3
-    m = 64
-    d0, eta = grf(m, 2), grf(m, 3)
-    phi = np.zeros((m, m, m))
+    from oracle import cmg
+    s = cmg.Solver(src0.shape, degree=args.degree)
+    phi = np.zeros(src0.shape)
     cycles = []
-    for t in range(seq):
-        phi, hist = flat.mg_solve(d0 + (0.05 * t) * eta, phi0=phi, tol=tol, max_cycles=50)
-        cycles.append(len(hist) - 1)
-    cps = sum(cycles) / len(cycles)
-    return {"value": 1.0 / (t_cycle * cps), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"one oracle FP64 V-cycle at {ns}^3 ({t_cycle / (n_full / ns) ** 3:.2f} s, NumPy, one thread), "
-                       f"scaled by {(n_full / ns) ** 3:.0f} to {n_full}^3 and by the oracle's {cps:.2f} cycles per solve "
-                       f"on the same 10-source recipe at 64^3")}
+    t0 = time.perf_counter()
+    for F in (src0, src1):
+        phi, h = s.solve(F, phi, tol=args.tol, max_cycles=args.max_vcycles)
+        cycles.append(len(h) - 1)
+    dt = time.perf_counter() - t0
+    s.close()
+    return {"value": 2.0 / dt, "unit": UNIT, "cores": cmg.threads(), "kind": "oracle",
+            "sample": (f"C FP64 V-cycle oracle on {cmg.threads()} host threads: solves t = 0 (cold, {cycles[0]} "
+                       f"cycles) and t = 1 (warm, {cycles[1]} cycles) of the {args.n}^3 sequence, {dt:.1f} s")}
 
 
 def run_reference(args):
-    world = int(os.environ.get("WORLD_SIZE", "1"))
+    """The oracle arm: the C FP64 V-cycle oracle runs the same warm-started sequence on the
+    host cores.  One step is one V-cycle of the sequence (a 512^3 solve takes several
+    seconds per cycle on a CPU); when a solve reaches the tolerance the next source starts
+    from its solution.  solves/s = timed V-cycles / (the oracle's cycles per solve over the
+    solves it completed in this run) / timed seconds."""
+    import numpy as np
+
+    from oracle import cmg
     rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
         return
-    samples = []
+    from synth import grf
+    n, seq, tol = args.n, args.seq, args.tol
+    d0, eta = grf(n, 2), grf(n, 3)
+    s = cmg.Solver(n, degree=args.degree)
+    phi = np.zeros((n, n, n))
+    st = {"t": 0, "cyc": 0, "rel": None}
+    completed = []
+
+    def source(t):
+        return d0 + (0.05 * t) * eta
+
+    F = source(0)
+    timed_s, timed_cycles = 0.0, 0
     for k in range(args.warmup + args.steps):
+        if st["rel"] is not None and st["rel"] <= tol:
+            completed.append(st["cyc"])
+            s.end(phi)
+            st["t"] = (st["t"] + 1) % seq
+            if st["t"] == 0:
+                phi[:] = 0.0
+            F = source(st["t"])          # input formation, outside the timed interval
+            st["rel"], st["cyc"] = None, 0
         t0 = time.perf_counter()
-        s = oracle_sample(args.n, args.seq, args.tol)
+        if st["rel"] is None:
+            st["rel"] = s.begin(F, phi)
+        st["rel"] = s.cycle()
+        dt = time.perf_counter() - t0
+        st["cyc"] += 1
         if k >= args.warmup:
-            samples.append((s, time.perf_counter() - t0))
-    vals = [s["value"] for s, _ in samples]
-    value = statistics.median(vals)
-    cpu = dict(samples[-1][0])
-    cpu["value"] = value
+            timed_s += dt
+            timed_cycles += 1
+    # cycles per solve from the solves this run completed; with none, finish the current
+    # one (untimed) to learn its count
+    while not completed:
+        if st["rel"] <= tol or st["cyc"] >= args.max_vcycles:
+            completed.append(st["cyc"])
+            break
+        st["rel"] = s.cycle()
+        st["cyc"] += 1
+    s.close()
+    cps = sum(completed) / len(completed)
+    value = timed_cycles / cps / timed_s
+    cpu = {"value": value, "unit": UNIT, "cores": cmg.threads(), "kind": "oracle",
+           "sample": (f"C FP64 V-cycle oracle on {cmg.threads()} host threads; each step one V-cycle of the "
+                      f"{n}^3 sequence; {cps:.2f} cycles per solve over the {len(completed)} solves completed "
+                      f"(cycles {completed}, the cold t = 0 solve included)")}
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1000.0 * args.seq / value, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"periodic 3-D Poisson {args.n}^3, warm-started sequence of {args.seq} GRF sources, tol {args.tol:g}",
-                   "n": args.n, "sources": args.seq, "tol": args.tol},
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * timed_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(workload_config(args, s.levels), parallelism=f"replicas x{world}"),
+        "precision": "FP64 V-cycle",
+        "cycles_per_solve": cps,
         "cpu_baseline": cpu,
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -334,12 +377,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"periodic 3-D Poisson {n}^3, warm-started sequence of {seq} GRF sources "
-                               f"(P(k)~k^-2), tol {args.tol:g}, V({args.degree},{args.degree}) Chebyshev, "
-                               f"{solver.levels} levels, mixed precision"
-                               + ("" if not args.no_fused else ", unfused"),
-                   "n": n, "sources": seq, "tol": args.tol, "levels": solver.levels,
-                   "l2": "inputs larger than L2 (1 GiB per field)", "parallelism": f"replicas x{world}"},
+        "config": dict(workload_config(args, solver.levels), parallelism=f"replicas x{world}"),
+        "precision": "FP32 V-cycle inside double-float defect correction" + ("" if not args.no_fused else ", unfused"),
         "cycles_per_solve": sum(cycles_log) / max(1, len(cycles_log)),
         "gpu_launches": launches,
         "roofline": roofline,
@@ -364,7 +403,7 @@ def run_ours(args):
         line["pm_force_256"] = pm_force_leg(args, dev)
         torch.cuda.empty_cache()
         line["batched_48"] = batched_leg(args)
-        line["cpu_baseline"] = oracle_sample(n, seq, args.tol)
+        line["cpu_baseline"] = oracle_sample(host_src[0], host_src[1], args)
     if rank == 0:
         print(json.dumps(line))
     solver.close()
@@ -408,20 +447,22 @@ def baseline_legs(args, F, dev):
     import paper_2607_10983_gb300 as gb
     n = args.n
     out = {}
-    # plain FP64 V-cycle on the first three sources of the sequence (cold, warm, warm)
+    # plain FP64 V-cycle (one kernel per operation) on the headline's workload: the whole
+    # sequence, t = 0 from zero and every later source warm-started from the previous phi
     s64 = gb.Solver(n, prec="fp64", degree=args.degree)
     phi = torch.zeros_like(F[0])
-    cyc = 0
     s64.solve(F[1], phi.clone(), tol=1e-2, max_vcycles=1)
+    cycles = []
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for t in range(3):
-        _, st = s64.solve(F[t], phi, tol=args.tol, max_vcycles=args.max_vcycles)
-        cyc += st.cycles
+    for f in F:
+        _, st = s64.solve(f, phi, tol=args.tol, max_vcycles=args.max_vcycles)
+        cycles.append(st.cycles)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
-    out["plain_fp64_vcycle"] = {"solves_per_s": 3 / dt, "cycles_per_solve": cyc / 3,
-                                "ms_per_cycle": 1000 * dt / cyc, "sources": "t = 0, 1, 2 of the sequence"}
+    out["plain_fp64_vcycle"] = {"solves_per_s": len(F) / dt, "cycles_per_solve": sum(cycles) / len(F),
+                                "ms_per_cycle": 1000 * dt / sum(cycles), "cycles": cycles,
+                                "sources": f"the headline sequence, t = 0..{len(F) - 1}, warm-started"}
     s64.close()
     del phi
     # cuFFT spectral solve of the same 7-point operator (torch.fft), FP64 and FP32
@@ -434,7 +475,7 @@ def baseline_legs(args, F, dev):
     inv[0, 0, 0] = 0.0
     for name, dt_ in (("cufft_fp64", torch.float64), ("cufft_fp32", torch.float32)):
         iv = inv.to(dt_)
-        srcs = [f.to(dt_) for f in F[:3]]
+        srcs = [f.to(dt_) for f in F]
 
         def solve(f):
             return torch.fft.irfftn(torch.fft.rfftn(f) * iv, s=(n, n, n))
@@ -447,8 +488,8 @@ def baseline_legs(args, F, dev):
             solve(f)
         ev1.record()
         torch.cuda.synchronize()
-        out[name] = {"solves_per_s": 3 / (ev0.elapsed_time(ev1) / 1000.0),
-                     "note": "rfftn, divide by the 7-point symbol, irfftn; inputs resident"}
+        out[name] = {"solves_per_s": len(srcs) / (ev0.elapsed_time(ev1) / 1000.0),
+                     "note": "rfftn, divide by the 7-point symbol, irfftn; the headline's 10 sources, resident"}
         sol = solve(srcs[0]).double()
         if name == "cufft_fp64":
             ref64 = sol
