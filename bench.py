@@ -233,11 +233,10 @@ def oracle_sample(src0, src1, args):
 
 
 def run_reference(args):
-    """The oracle arm: the C FP64 V-cycle oracle runs the same warm-started sequence on the
-    host cores.  One step is one V-cycle of the sequence (a 512^3 solve takes several
-    seconds per cycle on a CPU); when a solve reaches the tolerance the next source starts
-    from its solution.  solves/s = timed V-cycles / (the oracle's cycles per solve over the
-    solves it completed in this run) / timed seconds."""
+    """The oracle arm: the C FP64 V-cycle oracle runs the same warm-started sequence on all
+    host cores.  One step is one solve of the sequence to the tolerance (t = 0 from zero,
+    each later source from the previous solution; the sequence restarts from zero after
+    its last source); solves/s = timed steps / timed seconds."""
     import numpy as np
 
     from oracle import cmg
@@ -250,54 +249,35 @@ def run_reference(args):
     d0, eta = grf(n, 2), grf(n, 3)
     s = cmg.Solver(n, degree=args.degree)
     phi = np.zeros((n, n, n))
-    st = {"t": 0, "cyc": 0, "rel": None}
-    completed = []
-
-    def source(t):
-        return d0 + (0.05 * t) * eta
-
-    F = source(0)
-    timed_s, timed_cycles = 0.0, 0
+    timed_s, cycles = 0.0, []
     for k in range(args.warmup + args.steps):
-        if st["rel"] is not None and st["rel"] <= tol:
-            completed.append(st["cyc"])
-            s.end(phi)
-            st["t"] = (st["t"] + 1) % seq
-            if st["t"] == 0:
-                phi[:] = 0.0
-            F = source(st["t"])          # input formation, outside the timed interval
-            st["rel"], st["cyc"] = None, 0
+        t = k % seq
+        if t == 0:
+            phi[:] = 0.0
+        F = d0 + (0.05 * t) * eta          # input formation, outside the timed interval
         t0 = time.perf_counter()
-        if st["rel"] is None:
-            st["rel"] = s.begin(F, phi)
-        st["rel"] = s.cycle()
+        phi, h = s.solve(F, phi, tol=tol, max_cycles=args.max_vcycles)
         dt = time.perf_counter() - t0
-        st["cyc"] += 1
+        if h[-1] > tol:
+            raise RuntimeError(f"oracle solve {t} did not reach {tol:g}")
         if k >= args.warmup:
             timed_s += dt
-            timed_cycles += 1
-    # cycles per solve from the solves this run completed; with none, finish the current
-    # one (untimed) to learn its count
-    while not completed:
-        if st["rel"] <= tol or st["cyc"] >= args.max_vcycles:
-            completed.append(st["cyc"])
-            break
-        st["rel"] = s.cycle()
-        st["cyc"] += 1
+            cycles.append(len(h) - 1)
+    levels = s.levels
     s.close()
-    cps = sum(completed) / len(completed)
-    value = timed_cycles / cps / timed_s
+    value = args.steps / timed_s
+    first = args.warmup % seq
     cpu = {"value": value, "unit": UNIT, "cores": cmg.threads(), "kind": "oracle",
-           "sample": (f"C FP64 V-cycle oracle on {cmg.threads()} host threads; each step one V-cycle of the "
-                      f"{n}^3 sequence; {cps:.2f} cycles per solve over the {len(completed)} solves completed "
-                      f"(cycles {completed}, the cold t = 0 solve included)")}
+           "sample": (f"C FP64 V-cycle oracle on {cmg.threads()} host threads; each step one {n}^3 solve of the "
+                      f"sequence (timed sources t = {first}, {(first + 1) % seq}, ... cycling through 0..{seq - 1}), "
+                      f"{sum(cycles) / len(cycles):.2f} cycles per solve")}
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * timed_s / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(workload_config(args, s.levels), parallelism=f"replicas x{world}"),
+        "config": dict(workload_config(args, levels), parallelism=f"replicas x{world}"),
         "precision": "FP64 V-cycle",
-        "cycles_per_solve": cps,
+        "cycles_per_solve": sum(cycles) / len(cycles),
         "cpu_baseline": cpu,
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
