@@ -82,7 +82,7 @@ struct DownTile {
 };
 template <int V>
 struct UpTile {
-  using T = PTile<64, 32, V, 512, 3>;
+  using T = PTile<64, 32, V, 384, 4>;
 };
 
 template <int V>

@@ -79,6 +79,13 @@ __device__ __forceinline__ float2 ld2(const float* p) { return __ldg(reinterpret
 __device__ __forceinline__ void st2(float* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
 
 // ------------------------------------------------------------------ down leg
+//
+// Addressing.  Every shared access of a thread is a compile-time offset from one of two
+// pointers (its first pair in the current and in the previous buffer of stage plane 0;
+// stage plane s sits 2 s PLANE further); global planes are reached through pointers that
+// advance by one plane per iteration (wrapped once at the end of the mesh), plus the
+// thread's fixed in-plane offsets; the coarse outputs a thread writes are fixed per
+// tile and computed once.  Meshes have fewer than 2^31 cells per plane.
 
 template <int V, class TL>
 __device__ __forceinline__ void down_segment(Dims d, const float* __restrict__ r, float* __restrict__ e_out,
@@ -86,17 +93,28 @@ __device__ __forceinline__ void down_segment(Dims d, const float* __restrict__ r
                                              float inv_h2, const Coef& cf, float* sm) {
   constexpr int H = V + 1, R = TL::R, WS = TL::WS, HALF = TL::HALF, PLANE = TL::PLANE, PAD = TL::PAD;
   constexpr int TX = TL::TX, TY = TL::TY, NT = TL::NT;
+  constexpr int SP = 2 * PLANE;                 // stage plane s, buffer b at (2 s + b) PLANE
   static_assert(TL::H == H, "down-leg halo");
-  constexpr int NCO = (TX / 2) * (TY / 2);  // coarse outputs per tile plane
-  // plane(s, b): even half at the pointer, odd half HALF later; s = 0..V-1 holds
-  // e_{s+1}, s = V the z-weighted residual
-  auto plane = [&](int s, int b) -> float* { return sm + (s * 2 + b) * PLANE + PAD; };
+  constexpr int NCO = (TX / 2) * (TY / 2);      // coarse outputs per tile plane
+  constexpr int NQ = (NCO + NT - 1) / NT;       // of them per thread
 
   const int tid = threadIdx.x;
-  const long long pst = (long long)d.nx * d.ny;
+  const int pst = d.nx * d.ny;
   PPos<TL> P;
   P.init(d, x0, y0);
-  const Dims dc{d.nx / 2, d.ny / 2, d.nz / 2};
+  const int cnx = d.nx >> 1, cny = d.ny >> 1;
+  float* const bs = sm + PAD + P.p0;            // the thread's first pair, stage plane 0, buffer 0
+  // coarse outputs of the thread: centre in the z-weighted plane and offset in the coarse
+  // plane (-1: none)
+  int qpp[NQ], qco[NQ];
+#pragma unroll
+  for (int i = 0; i < NQ; ++i) {
+    const int q = tid + i * NT;
+    const int ccx = q % (TX / 2), ccy = q / (TX / 2);
+    const int cX = (x0 >> 1) + ccx, cY = (y0 >> 1) + ccy;
+    qpp[i] = (H + 2 * ccy) * WS + TL::HX / 2 + ccx;
+    qco[i] = (q < NCO && cX < cnx && cY < cny) ? cY * cnx + cX : -1;
+  }
   const float2 Z = bcast(0.f), MIH2 = bcast(-inv_h2);
 
   float2 rq[V + 1][R];              // rq[i][j] = r at plane t - i
@@ -115,13 +133,14 @@ __device__ __forceinline__ void down_segment(Dims d, const float* __restrict__ r
   // the last coarse plane c = zend - 1 (a segment may end on an odd plane) is
   // written at t = c + V + 2
   const int tb = z0 - H, te = zend + V + 1;
-  {
-    const float* base = r + (long long)wrapmod(tb, d.nz) * pst;
+  int zl = wrapmod(tb, d.nz);                   // plane of the latest load of r
+  const float* rl = r + (size_t)zl * pst;
 #pragma unroll
-    for (int j = 0; j < R; ++j) rnext[j] = ld2(base + P.goff[j]);
-  }
+  for (int j = 0; j < R; ++j) rnext[j] = ld2(rl + P.goff[j]);
   for (int t = tb; t <= te; ++t) {
-    const int cur = (t - tb) & 1, prv = cur ^ 1;
+    const int cur = (t - tb) & 1;
+    float* const bc = bs + (cur ? PLANE : 0);
+    const float* const bp = bs + (cur ? 0 : PLANE);
 #pragma unroll
     for (int j = 0; j < R; ++j) {
 #pragma unroll
@@ -129,71 +148,75 @@ __device__ __forceinline__ void down_segment(Dims d, const float* __restrict__ r
       rq[0][j] = rnext[j];
     }
     if (t < te) {
-      const float* base = r + (long long)wrapmod(t + 1, d.nz) * pst;
+      if (++zl == d.nz) {
+        zl = 0;
+        rl = r;
+      } else {
+        rl += pst;
+      }
 #pragma unroll
-      for (int j = 0; j < R; ++j) rnext[j] = ld2(base + P.goff[j]);
+      for (int j = 0; j < R; ++j) rnext[j] = ld2(rl + P.goff[j]);
     }
     float2 en[V + 1][R], dn[V + 1][R];
     // stage 1 (pointwise, e starts at zero): e_1 = d_1 = c2_0 D^-1 r
     {
-      float* dE = plane(0, cur);
       const float2 A = bcast(cf.a[0]), MB = bcast(-cf.b[0]), C1 = bcast(cf.c1[0]);
 #pragma unroll
       for (int j = 0; j < R; ++j) {
         float2 dd = Z;
         en[1][j] = p_cheb(Z, rq[0][j], Z, Z, dd, A, MB, C1);
         dn[1][j] = dd;
-        const int p = P.p0 + j * WS;
-        dE[p] = en[1][j].x;
-        dE[p + HALF] = en[1][j].y;
+        bc[j * WS] = en[1][j].x;
+        bc[j * WS + HALF] = en[1][j].y;
       }
     }
     // stages 2..V: Chebyshev steps with the stencil on e_{s-1}
 #pragma unroll
     for (int s = 2; s <= V; ++s) {
-      const float* sE = plane(s - 2, prv);
-      float* dE = plane(s - 1, cur);
-      const int zp = t - s + 1;
+      const float* const sE = bp + (s - 2) * SP;
+      float* const dE = bc + (s - 1) * SP;
       const float2 A = bcast(cf.a[s - 1]), MB = bcast(-cf.b[s - 1]), C1 = bcast(cf.c1[s - 1]);
 #pragma unroll
       for (int j = 0; j < R; ++j) {
-        const int p = P.p0 + j * WS;
+        const int o = j * WS;
         const float2 c = wc[s][j];
-        const float2 ym = j > 0 ? wc[s][j - 1] : make_float2(sE[p - WS], sE[p - WS + HALF]);
-        const float2 yp = j < R - 1 ? wc[s][j + 1] : make_float2(sE[p + WS], sE[p + WS + HALF]);
-        const float2 sn = p_nbr_sum(sE[p - 1 + HALF], sE[p + 1], c, ym, yp, wp[s][j], en[s - 1][j]);
+        const float2 ym = j > 0 ? wc[s][j - 1] : make_float2(sE[o - WS], sE[o - WS + HALF]);
+        const float2 yp = j < R - 1 ? wc[s][j + 1] : make_float2(sE[o + WS], sE[o + WS + HALF]);
+        const float2 sn = p_nbr_sum(sE[o - 1 + HALF], sE[o + 1], c, ym, yp, wp[s][j], en[s - 1][j]);
         float2 dd = dh[s][j];
         en[s][j] = p_cheb(c, rq[s - 1][j], sn, c, dd, A, MB, C1);
         dn[s][j] = dd;
-        dE[p] = en[s][j].x;
-        dE[p + HALF] = en[s][j].y;
-        if (s == V && (P.tmask >> j & 1u) && zp >= z0 && zp < zend) st2(e_out + (long long)zp * pst + P.goff[j], en[s][j]);
+        dE[o] = en[s][j].x;
+        dE[o + HALF] = en[s][j].y;
       }
     }
-    if (V == 1) {
-      const int zp = t;
+    {
+      const int zp = t - V + 1;                 // plane of e_V finished in this iteration
+      if (zp >= z0 && zp < zend) {
+        float* const ez = e_out + (size_t)zp * pst;
 #pragma unroll
-      for (int j = 0; j < R; ++j)
-        if ((P.tmask >> j & 1u) && zp >= z0 && zp < zend) st2(e_out + (long long)zp * pst + P.goff[j], en[1][j]);
+        for (int j = 0; j < R; ++j)
+          if (P.tmask >> j & 1u) st2(ez + P.goff[j], en[V][j]);
+      }
     }
     // residual stage at plane t - V, then z weights of the restriction at c = t - V - 1
     {
-      const float* sE = plane(V - 1, prv);
-      float* zE = plane(V, cur);
+      const float* const sE = bp + (V - 1) * SP;
+      float* const zE = bc + V * SP;
       const int c = t - V - 1;
       const bool cz = ((c & 1) == 0) && c >= z0 && c < zend;
 #pragma unroll
       for (int j = 0; j < R; ++j) {
-        const int p = P.p0 + j * WS;
+        const int o = j * WS;
         const float2 cc = wc[V + 1][j];
-        const float2 ym = j > 0 ? wc[V + 1][j - 1] : make_float2(sE[p - WS], sE[p - WS + HALF]);
-        const float2 yp = j < R - 1 ? wc[V + 1][j + 1] : make_float2(sE[p + WS], sE[p + WS + HALF]);
-        const float2 sn = p_nbr_sum(sE[p - 1 + HALF], sE[p + 1], cc, ym, yp, wp[V + 1][j], en[V][j]);
+        const float2 ym = j > 0 ? wc[V + 1][j - 1] : make_float2(sE[o - WS], sE[o - WS + HALF]);
+        const float2 yp = j < R - 1 ? wc[V + 1][j + 1] : make_float2(sE[o + WS], sE[o + WS + HALF]);
+        const float2 sn = p_nbr_sum(sE[o - 1 + HALF], sE[o + 1], cc, ym, yp, wp[V + 1][j], en[V][j]);
         const float2 rn = p_resid(rq[V][j], sn, cc, MIH2);
         if (cz) {
           const float2 zw = p_fw3(rsp[j], rsc[j], rn);
-          zE[p] = zw.x;
-          zE[p + HALF] = zw.y;
+          zE[o] = zw.x;
+          zE[o + HALF] = zw.y;
         }
         rsp[j] = rsc[j];
         rsc[j] = rn;
@@ -205,18 +228,17 @@ __device__ __forceinline__ void down_segment(Dims d, const float* __restrict__ r
     {
       const int c = t - V - 2;
       if (((c & 1) == 0) && c >= z0 && c < zend) {
-        const float* zE = plane(V, prv);
-        const float* zO = zE + HALF;
-        for (int q = tid; q < NCO; q += NT) {
-          const int ccx = q % (TX / 2), ccy = q / (TX / 2);
-          const int cX = x0 / 2 + ccx, cY = y0 / 2 + ccy;
-          if (cX < dc.nx && cY < dc.ny) {
-            const int pp = (H + 2 * ccy) * WS + TL::HX / 2 + ccx;
-            const float y0v = fw3(zO[pp - 1 - WS], zO[pp - 1], zO[pp - 1 + WS]);
-            const float y1v = fw3(zE[pp - WS], zE[pp], zE[pp + WS]);
-            const float y2v = fw3(zO[pp - WS], zO[pp], zO[pp + WS]);
-            rc[((long long)(c >> 1) * dc.ny + cY) * dc.nx + cX] = fw3(y0v, y1v, y2v);
-          }
+        const float* const zE = sm + PAD + V * SP + (cur ? 0 : PLANE);
+        float* const rcz = rc + (size_t)(c >> 1) * (cnx * cny);
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) {
+          if (qco[i] < 0) continue;
+          const float* const e0 = zE + qpp[i];
+          const float* const o0 = e0 + HALF;
+          const float y0v = fw3(o0[-1 - WS], o0[-1], o0[-1 + WS]);
+          const float y1v = fw3(e0[-WS], e0[0], e0[WS]);
+          const float y2v = fw3(o0[-WS], o0[0], o0[WS]);
+          rcz[qco[i]] = fw3(y0v, y1v, y2v);
         }
       }
     }
@@ -237,11 +259,11 @@ __device__ __forceinline__ void down_segment(Dims d, const float* __restrict__ r
 
 // ------------------------------------------------------------------ up leg
 
-// Coarse nodes under the haloed fine region: I in [CX0, CX0 + CW), J in [CY0, CY0 + CH),
-// the +1 neighbour included.
-// The row stride CW >= WXP + 1 is chosen like the planes' row stride: threads of a
-// warp in the next row block read coarse row J + R/2, and the jump must keep the
-// warp's 32 loads on distinct banks.
+// Coarse nodes under the haloed fine region: I in [CX0, CX0 + CU), J in [CY0, CY0 + CH),
+// the +1 neighbour included; CH covers the rows of every thread column, idle ones too.
+// The row stride CW >= CU is chosen like the planes' row stride: threads of a warp in
+// the next row block read coarse rows about R/2 further on, and the jump should keep
+// the warp's 32 loads on distinct banks.
 constexpr int coarse_stride(int wxp, int r) {
   for (int cw = wxp + 1; cw < wxp + 33; ++cw)
     if (((r / 2) * cw - wxp) % 32 == 0) return cw;
@@ -252,63 +274,102 @@ template <class TL>
 struct PCoarse {
   static constexpr int CU = TL::WXP + 1;                  // coarse columns used
   static constexpr int CW = coarse_stride(TL::WXP, TL::R);
-  static constexpr int CH = TL::WY / 2 + 2;
+  static constexpr int CH = (TL::ROWS + 1) / 2 + 2;
   static constexpr int CN = CW * CH;
+  static constexpr int NXR = (TL::R + 1) / 2 + 1;        // coarse rows under a thread column
 };
+
+// e_0 = e + P e_c for the R pairs of a column: the trilinear prolongation as nested
+// midpoints (x, then y, then z; stencil.cuh's prolong_value), the x midpoints of each
+// coarse row formed once per column.  Row j of the column has y parity PAR ^ (j & 1)
+// and first coarse row (PAR + j) / 2 relative to the column's.
+template <int PAR, class TL>
+__device__ __forceinline__ void prolong_column(const float* __restrict__ c0, const float* __restrict__ c1, bool zodd,
+                                               float2 (&e)[TL::R]) {
+  using CT = PCoarse<TL>;
+  constexpr int R = TL::R, NXR = CT::NXR, CW = CT::CW;
+  float2 X[NXR], Y[NXR];
+#pragma unroll
+  for (int k = 0; k < NXR; ++k) {
+    const float v0 = c0[k * CW];
+    X[k] = make_float2(v0, half_sum(v0, c0[k * CW + 1]));
+  }
+  if (zodd) {
+#pragma unroll
+    for (int k = 0; k < NXR; ++k) {
+      const float v0 = c1[k * CW];
+      Y[k] = make_float2(v0, half_sum(v0, c1[k * CW + 1]));
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    const int J = (PAR + j) >> 1;
+    const bool dy = ((PAR + j) & 1) != 0;
+    float2 pv = dy ? p_half_sum(X[J], X[J + 1]) : X[J];
+    if (zodd) pv = p_half_sum(pv, dy ? p_half_sum(Y[J], Y[J + 1]) : Y[J]);
+    e[j] = p_add(e[j], pv);
+  }
+}
 
 template <int V, class TL>
 __device__ __forceinline__ void up_segment(Dims d, const float* __restrict__ e_in, const float* __restrict__ ec,
                                            const float* __restrict__ r, float* __restrict__ e_out, int x0, int y0,
                                            int z0, int zend, float inv_h2, const Coef& cf, float* sm) {
   constexpr int H = V, R = TL::R, WS = TL::WS, HALF = TL::HALF, PLANE = TL::PLANE, PAD = TL::PAD;
-  constexpr int NT = TL::NT;
+  constexpr int NT = TL::NT, SP = 2 * PLANE;
   static_assert(TL::H == H, "up-leg halo");
   using CT = PCoarse<TL>;
-  constexpr int CW = CT::CW, CN = CT::CN, CL = (CN + NT - 1) / NT;
-  // plane(s, b): e_s for s = 0..V-1 (e_0 = e + P e_c); then three coarse planes
-  auto plane = [&](int s, int b) -> float* { return sm + (s * 2 + b) * PLANE + PAD; };
-  float* cring = sm + V * 2 * PLANE;
+  constexpr int CW = CT::CW, CN = CT::CN, CU = CT::CU, CH = CT::CH;
+  constexpr int CL = (CU * CH + NT - 1) / NT;   // coarse cells a thread loads per plane
+  // stage plane s (e_s, s = 0..V-1), buffer b at (2 s + b) PLANE; then three coarse planes
+  float* const cring = sm + V * SP;
 
   const int tid = threadIdx.x;
-  const long long pst = (long long)d.nx * d.ny;
-  const Dims dc{d.nx / 2, d.ny / 2, d.nz / 2};
-  const long long cpst = (long long)dc.nx * dc.ny;
+  const int pst = d.nx * d.ny;
+  const int cnx = d.nx >> 1, cny = d.ny >> 1, cnz = d.nz >> 1;
+  const int cpst = cnx * cny;
   PPos<TL> P;
   P.init(d, x0, y0);
-  const float2 Z = bcast(0.f);
-  // coarse node under each pair (offset in the coarse tile) and the y parity
+  float* const bs = sm + PAD + P.p0;
+  // the column's rows: y parity of the first (tiles start on even rows) and the coarse
+  // row under it, relative to the ring's first row
   const int CX0 = floor_half(x0 - TL::HX), CY0 = floor_half(y0 - H);
-  int co[R];
-  unsigned oddy = 0;
-#pragma unroll
-  for (int j = 0; j < R; ++j) {
-    const int py = P.pyb * R + j;
-    co[j] = 0;
-    if (tid < TL::NCOL && py < TL::WY) {
-      const int I = CX0 + P.px, uy = y0 - H + py, J = floor_half(uy);
-      co[j] = (J - CY0) * CW + (I - CX0);
-      oddy |= (unsigned)(uy - 2 * J) << j;
-    }
-  }
-  // coarse tile cells this thread loads
-  int cgo[CL];
+  const int par0 = (H + P.pyb * R) & 1;
+  const int cb0 = tid < TL::NCOL ? (floor_half(y0 - H + P.pyb * R) - CY0) * CW + P.px : 0;
+  // coarse cells of the ring this thread loads: in-plane offset (-1: none) and ring offset
+  int cgo[CL], cso[CL];
 #pragma unroll
   for (int i = 0; i < CL; ++i) {
     const int q = tid + i * NT;
-    cgo[i] = -1;
-    if (q < CN && q % CW < CT::CU) cgo[i] = wrapmod(CX0 + q % CW, dc.nx) + wrapmod(CY0 + q / CW, dc.ny) * dc.nx;
+    const int ci = q % CU, cj = q / CU;
+    cso[i] = cj * CW + ci;
+    cgo[i] = q < CU * CH ? wrapmod(CX0 + ci, cnx) + wrapmod(CY0 + cj, cny) * cnx : -1;
   }
-  auto load_coarse = [&](int Ku, float (&vals)[CL]) {
-    const float* base = ec + (long long)wrapmod(Ku, dc.nz) * cpst;
+  // coarse planes: slot of plane Ku (Ku = floor(t / 2)) and the plane of the next load
+  const int tb = z0 - V, te = zend + V - 1;
+  const int K0 = floor_half(tb);
+  int ks = mod3(K0);
+  int kl = wrapmod(K0, cnz);
+  const float* ecl = ec + (size_t)kl * cpst;
+  auto load_coarse = [&](float (&vals)[CL]) {
 #pragma unroll
-    for (int i = 0; i < CL; ++i) vals[i] = cgo[i] >= 0 ? __ldg(base + cgo[i]) : 0.f;
+    for (int i = 0; i < CL; ++i) vals[i] = cgo[i] >= 0 ? __ldg(ecl + cgo[i]) : 0.f;
   };
-  auto store_coarse = [&](int Ku, const float (&vals)[CL]) {
-    float* dst = cring + mod3(Ku) * CN;
+  auto store_coarse = [&](int slot, const float (&vals)[CL]) {
+    float* const dst = cring + slot * CN;
 #pragma unroll
     for (int i = 0; i < CL; ++i)
-      if (cgo[i] >= 0) dst[tid + i * NT] = vals[i];
+      if (cgo[i] >= 0) dst[cso[i]] = vals[i];
   };
+  auto next_coarse = [&]() {
+    if (++kl == cnz) {
+      kl = 0;
+      ecl = ec;
+    } else {
+      ecl += cpst;
+    }
+  };
+  const float2 Z = bcast(0.f);
 
   float2 rq[V + 1][R];
   float2 wp[V + 1][R], wc[V + 1][R];
@@ -319,34 +380,38 @@ __device__ __forceinline__ void up_segment(Dims d, const float* __restrict__ e_i
 #pragma unroll
     for (int i = 0; i <= V; ++i) rq[i][j] = Z, dh[i][j] = Z, wp[i][j] = Z, wc[i][j] = Z;
   }
-  const int tb = z0 - V, te = zend + V - 1;
-  auto load = [&](int t) {
-    const long long base = (long long)wrapmod(t, d.nz) * pst;
-#pragma unroll
-    for (int j = 0; j < R; ++j) {
-      rnext[j] = ld2(r + base + P.goff[j]);
-      enext[j] = ld2(e_in + base + P.goff[j]);
-    }
-  };
+  int zl = wrapmod(tb, d.nz);                   // plane of the latest fine loads
+  size_t ol = (size_t)zl * pst;
   {
     float cv[CL];
-    const int K0 = floor_half(tb);
-    load_coarse(K0, cv);
-    store_coarse(K0, cv);
-    load_coarse(K0 + 1, cv);
-    store_coarse(K0 + 1, cv);
+    load_coarse(cv);
+    store_coarse(ks, cv);
+    next_coarse();
+    load_coarse(cv);
+    store_coarse(ks == 2 ? 0 : ks + 1, cv);
+    next_coarse();
   }
-  load(tb);
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    rnext[j] = ld2(r + ol + P.goff[j]);
+    enext[j] = ld2(e_in + ol + P.goff[j]);
+  }
   __syncthreads();
   for (int t = tb; t <= te; ++t) {
-    const int cur = (t - tb) & 1, prv = cur ^ 1;
+    const int cur = (t - tb) & 1;
+    float* const bc = bs + (cur ? PLANE : 0);
+    const float* const bp = bs + (cur ? 0 : PLANE);
+    const bool zodd = (t & 1) != 0;
+    if (!zodd && t != tb) ks = ks == 2 ? 0 : ks + 1;   // Ku advanced
+    const int ks1 = ks == 2 ? 0 : ks + 1;
     float2 en[V + 1][R], dn[V + 1][R];
-    const int Ku = floor_half(t);
-    const bool zodd = (t - 2 * Ku) != 0;
     // next coarse plane (needed from the next even t on), stored at the end of this iteration
     float cv[CL];
     const bool need_c = zodd && t < te;
-    if (need_c) load_coarse(Ku + 2, cv);
+    if (need_c) {
+      load_coarse(cv);
+      next_coarse();
+    }
 #pragma unroll
     for (int j = 0; j < R; ++j) {
 #pragma unroll
@@ -354,54 +419,64 @@ __device__ __forceinline__ void up_segment(Dims d, const float* __restrict__ e_i
       rq[0][j] = rnext[j];
       en[0][j] = enext[j];
     }
-    if (t < te) load(t + 1);
-    // stage 0: e_0 = e + P e_c (pointwise): x, then y, then z midpoints
-    {
-      const float* c0 = cring + mod3(Ku) * CN;
-      const float* c1 = cring + mod3(Ku + 1) * CN;
-      float* dE = plane(0, cur);
+    if (t < te) {
+      if (++zl == d.nz) {
+        zl = 0;
+        ol = 0;
+      } else {
+        ol += pst;
+      }
 #pragma unroll
       for (int j = 0; j < R; ++j) {
-        const bool dy = oddy >> j & 1u;
-        auto row = [&](const float* cp, int off) -> float2 {
-          const float v0 = cp[off];
-          return make_float2(v0, half_sum(v0, cp[off + 1]));
-        };
-        auto pl = [&](const float* cp) -> float2 {
-          const float2 v0 = row(cp, co[j]);
-          return dy ? p_half_sum(v0, row(cp, co[j] + CW)) : v0;
-        };
-        const float2 v0 = pl(c0);
-        const float2 pv = zodd ? p_half_sum(v0, pl(c1)) : v0;
-        en[0][j] = p_add(en[0][j], pv);
-        const int p = P.p0 + j * WS;
-        dE[p] = en[0][j].x;
-        dE[p + HALF] = en[0][j].y;
+        rnext[j] = ld2(r + ol + P.goff[j]);
+        enext[j] = ld2(e_in + ol + P.goff[j]);
+      }
+    }
+    // stage 0: e_0 = e + P e_c (pointwise)
+    {
+      const float* const c0 = cring + ks * CN + cb0;
+      const float* const c1 = cring + ks1 * CN + cb0;
+      if constexpr (R % 2 == 0) {
+        prolong_column<H & 1, TL>(c0, c1, zodd, en[0]);
+      } else {
+        if (par0) prolong_column<1, TL>(c0, c1, zodd, en[0]);
+        else prolong_column<0, TL>(c0, c1, zodd, en[0]);
+      }
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        bc[j * WS] = en[0][j].x;
+        bc[j * WS + HALF] = en[0][j].y;
       }
     }
     // stages 1..V: Chebyshev post-smoothing steps at plane t - s
 #pragma unroll
     for (int s = 1; s <= V; ++s) {
-      const float* sE = plane(s - 1, prv);
-      const int zp = t - s;
+      const float* const sE = bp + (s - 1) * SP;
+      float* const dE = bc + s * SP;
       const float2 A = bcast(cf.a[s - 1]), MB = bcast(-cf.b[s - 1]), C1 = bcast(cf.c1[s - 1]);
 #pragma unroll
       for (int j = 0; j < R; ++j) {
-        const int p = P.p0 + j * WS;
+        const int o = j * WS;
         const float2 c = wc[s][j];
-        const float2 ym = j > 0 ? wc[s][j - 1] : make_float2(sE[p - WS], sE[p - WS + HALF]);
-        const float2 yp = j < R - 1 ? wc[s][j + 1] : make_float2(sE[p + WS], sE[p + WS + HALF]);
-        const float2 sn = p_nbr_sum(sE[p - 1 + HALF], sE[p + 1], c, ym, yp, wp[s][j], en[s - 1][j]);
+        const float2 ym = j > 0 ? wc[s][j - 1] : make_float2(sE[o - WS], sE[o - WS + HALF]);
+        const float2 yp = j < R - 1 ? wc[s][j + 1] : make_float2(sE[o + WS], sE[o + WS + HALF]);
+        const float2 sn = p_nbr_sum(sE[o - 1 + HALF], sE[o + 1], c, ym, yp, wp[s][j], en[s - 1][j]);
         float2 dd = s == 1 ? Z : dh[s][j];
         en[s][j] = p_cheb(c, rq[s][j], sn, c, dd, A, MB, C1);
         dn[s][j] = dd;
         if (s < V) {
-          float* dE = plane(s, cur);
-          dE[p] = en[s][j].x;
-          dE[p + HALF] = en[s][j].y;
-        } else if ((P.tmask >> j & 1u) && zp >= z0 && zp < zend) {
-          st2(e_out + (long long)zp * pst + P.goff[j], en[s][j]);
+          dE[o] = en[s][j].x;
+          dE[o + HALF] = en[s][j].y;
         }
+      }
+    }
+    {
+      const int zp = t - V;
+      if (zp >= z0 && zp < zend) {
+        float* const ez = e_out + (size_t)zp * pst;
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+          if (P.tmask >> j & 1u) st2(ez + P.goff[j], en[V][j]);
       }
     }
 #pragma unroll
@@ -414,7 +489,7 @@ __device__ __forceinline__ void up_segment(Dims d, const float* __restrict__ e_i
 #pragma unroll
       for (int s = 2; s <= V; ++s) dh[s][j] = dn[s - 1][j];
     }
-    if (need_c) store_coarse(Ku + 2, cv);
+    if (need_c) store_coarse(ks1 == 2 ? 0 : ks1 + 1, cv);
     __syncthreads();
   }
 }
