@@ -56,7 +56,7 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="skip e2e, baselines and CPU oracle legs")
     p.add_argument("--max-vcycles", type=int, default=40)
     p.add_argument("--only", choices=["moving_mesh", "differentiable", "batched", "fixed_2_cycles", "predictors",
-                                      "pm_force", "e2e"],
+                                      "pm_force", "e2e", "coarse_store"],
                    help="run one extra workload alone and print its JSON object (no headline line)")
     p.add_argument("--no-autotune", action="store_true", help="batched leg: default grid and tiles")
     p.add_argument("--print-source-digests", action="store_true",
@@ -372,6 +372,7 @@ def run_ours(args):
         line["e2e"] = e2e_leg(args, solver, host_src)
         line["baselines"] = baseline_legs(args, F, dev)
         line["fixed_2_cycles"] = fixed_cycles_leg(args, solver, F)
+        line["coarse_store"] = coarse_store_leg(args, F, dev)
         line["predictors"] = predictors_leg(args, solver, F)
         line["krylov_2"] = krylov_leg(args, F)
         del F
@@ -477,6 +478,48 @@ def baseline_legs(args, F, dev):
             out[name]["rel_l2_vs_fp64"] = float(torch.linalg.vector_norm(sol - ref64)
                                                 / torch.linalg.vector_norm(ref64))
         del srcs, sol
+    return out
+
+
+def coarse_store_leg(args, F, dev):
+    """The sequence with the corrections of levels below 128^3 stored in FP32 (the headline),
+    BF16 or FP16 (opts.coarse_store): solves/s, cycles per solve and the last solution's
+    relative L2 error against the FP64 cuFFT solve of the same operator."""
+    import math
+
+    import torch
+
+    import paper_2607_10983_gb300 as gb
+    n = args.n
+    kz = 2 * math.pi * torch.fft.fftfreq(n, device=dev, dtype=torch.float64)
+    kx = 2 * math.pi * torch.fft.rfftfreq(n, device=dev, dtype=torch.float64)
+    lam = -4.0 * (torch.sin(kz / 2)[:, None, None] ** 2 + torch.sin(kz / 2)[None, :, None] ** 2
+                  + torch.sin(kx / 2)[None, None, :] ** 2)
+    lam[0, 0, 0] = 1.0
+    Fk = torch.fft.rfftn(F[-1]) / lam
+    Fk[0, 0, 0] = 0.0
+    ref = torch.fft.irfftn(Fk, s=(n, n, n))
+    del Fk, lam
+    out = {}
+    for store in ("fp32", "bf16", "fp16"):
+        s = gb.Solver(n, prec="mixed", degree=args.degree, coarse_store=store)
+        phi = torch.zeros_like(F[0])
+        s.solve(F[1], phi.clone(), tol=1e-2, max_vcycles=1)
+        cycles = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for f in F:
+            _, st = s.solve(f, phi, tol=args.tol, max_vcycles=args.max_vcycles)
+            cycles.append(st.cycles)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        err = float(torch.linalg.vector_norm(phi - ref) / torch.linalg.vector_norm(ref))
+        out[store] = {"solves_per_s": len(F) / dt, "cycles_per_solve": sum(cycles) / len(F), "cycles": cycles,
+                      "rel_l2_vs_fp64_fft": err}
+        s.close()
+        del phi
+    out["note"] = ("corrections of levels below 128^3 rounded to the format before prolongation (the bottom "
+                   "cycle's levels, 16^3 and below, stay FP32 inside it); timing includes the rounding passes")
     return out
 
 
@@ -813,6 +856,8 @@ def run_only(args):
         solver = gb.Solver(args.n, prec="mixed", degree=args.degree, fused=not args.no_fused)
         if args.only == "e2e":
             out = e2e_leg(args, solver, host)
+        elif args.only == "coarse_store":
+            out = coarse_store_leg(args, F, dev)
         else:
             leg = fixed_cycles_leg if args.only == "fixed_2_cycles" else predictors_leg
             out = leg(args, solver, F)

@@ -86,6 +86,13 @@ typedef struct {
                  /* over the edge's four cells and E_a the a-difference averaged over   */
                  /* the edge's two b-positions; M = M^T, 19 points, the same Fourier     */
                  /* symbol for constant B; forward and adjoint solves use M itself.     */
+  int coarse_store; /* flat + GBMG_MIXED only.  Storage of the correction that a coarse  */
+                 /* level (fewer than 128^3 cells) hands up to the next finer level:     */
+                 /* 0: FP32; 1: BF16; 2: FP16 (the north-star's precision option for    */
+                 /* coarse-level corrections; the paper runs FP32 throughout, Sec. 3.3). */
+                 /* The value is rounded to that format before the prolongation; levels */
+                 /* solved inside the shared-memory bottom cycle (16^3 and below) keep   */
+                 /* FP32 within it.  Not supported by batches.                          */
 } gbmg_opts;
 
 typedef struct {
@@ -369,6 +376,8 @@ gbmg_status mg_curv_geometry(gbmg_ctx* ctx, int level, float* J_dev, float* B_de
  * M^T / J.  mg_curv_smooth: one weighted-Jacobi sweep (Appendix B, Eq. jacobi)
  * e_out = e_in + omega (J r - op(e_in) / h_l^2) / D with D the stencil's diagonal
  * (op / h_l^2 applied to a unit vector), omega = opts.omega; e_in and e_out must differ.
+ * e_in NULL: the iterate is zero, and the sweep is the pointwise one the V-cycle uses
+ * for its first pre-smoothing sweep (the same values as a sweep of a zero array).
  * op as in mg_curv_apply. */
 gbmg_status mg_curv_residual(gbmg_ctx* ctx, int level, int transpose, const float* r_dev, const float* u_dev,
                              float* out_dev);

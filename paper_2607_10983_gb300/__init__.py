@@ -40,7 +40,8 @@ class _Opts(ctypes.Structure):
     _fields_ = [("op", ctypes.c_int), ("prec", ctypes.c_int), ("smoother", ctypes.c_int),
                 ("degree", ctypes.c_int), ("alpha", ctypes.c_double), ("nu1", ctypes.c_int),
                 ("nu2", ctypes.c_int), ("omega", ctypes.c_double), ("fused", ctypes.c_int),
-                ("krylov", ctypes.c_int), ("curv_sym", ctypes.c_int)]
+                ("krylov", ctypes.c_int), ("curv_sym", ctypes.c_int),
+                ("coarse_store", ctypes.c_int)]
 
 
 class _Stats(ctypes.Structure):
@@ -194,7 +195,7 @@ class Solver:
     def __init__(self, shape, levels: int = 0, degree: int = 3, prec: str = "mixed",
                  smoother: str | None = None, fused: bool = True, alpha: float = 8.0,
                  nu1: int = 2, nu2: int = 2, omega: float = 2.0 / 3.0, op: str = "flat", krylov: int = 0,
-                 curv_sym: bool = False):
+                 curv_sym: bool = False, coarse_store: str = "fp32"):
         L = lib()
         if smoother is None:
             smoother = "jacobi" if op == "curv" else "chebyshev"
@@ -208,6 +209,7 @@ class Solver:
         o.degree, o.alpha, o.nu1, o.nu2, o.omega, o.fused = degree, alpha, nu1, nu2, omega, int(fused)
         o.krylov = int(krylov)
         o.curv_sym = int(curv_sym)
+        o.coarse_store = {"fp32": 0, "bf16": 1, "fp16": 2}[coarse_store]
         self.prec = prec
         self.work_dtype = torch.float64 if prec == "fp64" else torch.float32
         ctx = _P()
@@ -298,10 +300,11 @@ class Solver:
                                       _ptr(u, torch.float32, shp), _ptr(out)))
         return out
 
-    def curv_smooth(self, level: int, e: torch.Tensor, r: torch.Tensor, transpose: bool = False):
-        """One FP32 weighted-Jacobi sweep of a level (the V-cycle's tiled kernel); returns the new e."""
+    def curv_smooth(self, level: int, e: torch.Tensor | None, r: torch.Tensor, transpose: bool = False):
+        """One FP32 weighted-Jacobi sweep of a level (the V-cycle's tiled kernel); returns the new e.
+        e None: sweep of a zero iterate (the pointwise first sweep of the V-cycle)."""
         shp = self.level_shape(level)
-        out = torch.empty_like(e)
+        out = torch.empty_like(r)
         _check(lib().mg_curv_smooth(self._c(), level, int(transpose), _ptr(e, torch.float32, shp),
                                     _ptr(r, torch.float32, shp), _ptr(out)))
         return out
@@ -497,8 +500,9 @@ class Solver:
 class Batch:
     """Independent flat solves of uneven sizes in one persistent launch (mg_batch_*)."""
 
-    def __init__(self, shapes, degree: int = 3, levels: int = 0):
-        self.solvers = [Solver(s, levels=levels, degree=degree, prec="mixed", fused=False) for s in shapes]
+    def __init__(self, shapes, degree: int = 3, levels: int = 0, coarse_store: str = "fp32"):
+        self.solvers = [Solver(s, levels=levels, degree=degree, prec="mixed", fused=False, coarse_store=coarse_store)
+                        for s in shapes]
         arr = (_P * len(self.solvers))(*[sv._ctx for sv in self.solvers])
         b = _P()
         _check(lib().mg_batch_create(ctypes.byref(b), arr, len(self.solvers),

@@ -712,6 +712,7 @@ extern "C" gbmg_status mg_batch_create(gbmg_batch** out, gbmg_ctx* const* ctxs, 
     if (c->L > BMAXL || c->L < 2) return fail(GBMG_ERR_INVALID_ARG, "mg_batch_create: each problem needs 2 to 16 levels");
     if (ncell(c->lv[0].d) >= (1ll << 31)) return fail(GBMG_ERR_INVALID_ARG, "mg_batch_create: a problem has 2^31 cells or more");
     if (c->o.degree > 8) return fail(GBMG_ERR_INVALID_ARG, "mg_batch_create: Chebyshev degree above 8");
+    if (c->o.coarse_store) return fail(GBMG_ERR_INVALID_ARG, "mg_batch_create: coarse_store is for single solves");
     if (c->o.degree != ctxs[0]->o.degree || c->o.alpha != ctxs[0]->o.alpha)
       return fail(GBMG_ERR_INVALID_ARG, "mg_batch_create: all contexts need the same smoother");
     if (c->device != ctxs[0]->device) return fail(GBMG_ERR_INVALID_ARG, "mg_batch_create: contexts on different devices");

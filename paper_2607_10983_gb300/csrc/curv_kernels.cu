@@ -317,6 +317,25 @@ __global__ void k_curv_jacobi(Dims d, CurvCoef cf, const T* __restrict__ r, cons
   e_out[i] = e_in[i] + omega * ((T(cf.J[i]) * r[i] * cf.h2 - Mh2) / Dh2);
 }
 
+// The first weighted-Jacobi sweep of a smoothing pass that starts from e = 0: op(0) = 0,
+// so the sweep is pointwise, e' = omega (J r h^2 - 0) / diag h^2, and reads only r, J and
+// the coefficients of the diagonal.  Written with the sweep's own expression, an explicit
+// zero iterate and operator value, so that it rounds exactly like k_curv_tiled<CM_JACOBI>
+// on a zero input (whose operator sum is +0).
+template <int FORM>
+__global__ void k_curv_jacobi_zero(Dims d, CurvCoef cf, const float* __restrict__ r, float* __restrict__ e_out,
+                                   float omega) {
+  const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y, z = blockIdx.z;
+  if (x >= d.nx || y >= d.ny) return;
+  const Nbhd nb(d, x, y, z);
+  const CoefAt Bc{cf, &nb};
+  const long long i = nb(0, 0, 0);
+  const float Dh2 = FORM == 2 ? diag_S_h2<float>(Bc) : diag_M_h2<float>(Bc);
+  const float Jc = cf.J[i], rc = r[i];
+  const float u0 = 0.f, Mh2 = 0.f;
+  e_out[i] = u0 + omega * ((Jc * rc * cf.h2 - Mh2) / Dh2);
+}
+
 // Dense matrix of the level operator (row-major n x n, FP64): entry (i, j) = (op(e_j) / J)_i.
 struct UnitAt {
   const Nbhd* nb;
@@ -1233,6 +1252,15 @@ cudaError_t launch_curv_jacobi(cudaStream_t st, Dims d, CurvCoef cf, const T* r,
   } else {
     k_curv_jacobi<T><<<cell_grid(d), dim3(BX, BY), 0, st>>>(d, cf, r, e_in, e_out, form, omega);
   }
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_curv_jacobi_zero(cudaStream_t st, Dims d, CurvCoef cf, const float* r, float* e_out, int form,
+                                    float omega) {
+  if (form < 0 || form > 2) return cudaErrorInvalidValue;
+  if (form == 2) k_curv_jacobi_zero<2><<<cell_grid(d), dim3(BX, BY), 0, st>>>(d, cf, r, e_out, omega);
+  else k_curv_jacobi_zero<0><<<cell_grid(d), dim3(BX, BY), 0, st>>>(d, cf, r, e_out, omega);
   note_launch();
   return cudaGetLastError();
 }

@@ -32,10 +32,19 @@ const float* curv_G<float>(const gbmg_ctx* c, bool tr) { return tr ? c->G32T : c
 template <>
 const double* curv_G<double>(const gbmg_ctx* c, bool tr) { return tr ? c->G64T : c->G64; }
 
+// nu weighted-Jacobi sweeps; from_zero: the iterate is zero, so the first sweep is the
+// pointwise one (no read of e; the same values as a full sweep of zeros)
 template <typename T>
-gbmg_status curv_smooth(gbmg_ctx* c, int l, T*& e, T*& eo, const T* r, int nu, bool tr) {
+gbmg_status curv_smooth(gbmg_ctx* c, int l, T*& e, T*& eo, const T* r, int nu, bool tr, bool from_zero) {
   const Level& L = c->lv[l];
   for (int k = 0; k < nu; ++k) {
+    if (k == 0 && from_zero) {
+      if constexpr (sizeof(T) == 4) {
+        TRY(launch_curv_jacobi_zero(c->stream, L.d, L.cc, r, eo, curv_form(c, tr), (float)c->o.omega));
+        std::swap(e, eo);
+        continue;
+      }
+    }
     ProfScope ps(c, l == 0 ? GBMG_PROF_CURV0 : GBMG_PROF_OFF);
     TRY(launch_curv_jacobi<T>(c->stream, L.d, L.cc, r, e, eo, curv_form(c, tr), (T)c->o.omega));
     std::swap(e, eo);
@@ -44,7 +53,9 @@ gbmg_status curv_smooth(gbmg_ctx* c, int l, T*& e, T*& eo, const T* r, int nu, b
 }
 
 // Curvilinear V-cycle for L_l e = r (or the transposed-solve operator), one kernel
-// per operation (Sec. 4.3, Eq. curv_error; Appendix B).
+// per operation (Sec. 4.3, Eq. curv_error; Appendix B), from e = 0: the iterate's
+// content is not read when nu1 > 0 (the first sweep is the pointwise one), and must be
+// zero otherwise.
 template <typename T>
 gbmg_status vcycle_curv(gbmg_ctx* c, int l, T*& e, T*& eo, const T* r, bool tr) {
   const Level& L = c->lv[l];
@@ -52,16 +63,16 @@ gbmg_status vcycle_curv(gbmg_ctx* c, int l, T*& e, T*& eo, const T* r, bool tr) 
     TRY(launch_coarse_matvec<T>(c->stream, c->nc, curv_G<T>(c, tr), r, e));
     return GBMG_OK;
   }
-  TRYS(curv_smooth<T>(c, l, e, eo, r, c->o.nu1, tr));
+  TRYS(curv_smooth<T>(c, l, e, eo, r, c->o.nu1, tr, true));
   TRY(launch_curv_residual<T>(c->stream, L.d, L.cc, r, e, (T*)L.t, curv_form(c, tr), nullptr));
   const Level& C = c->lv[l + 1];
   TRY(launch_restrict<T>(c->stream, L.d, (const T*)L.t, (T*)C.r));
   T* ce = (T*)C.e;
   T* ceo = (T*)C.e2;
-  if (l + 1 < c->L - 1) TRY(cudaMemsetAsync(ce, 0, (size_t)ncell(C.d) * sizeof(T), c->stream));
+  if (l + 1 < c->L - 1 && c->o.nu1 == 0) TRY(cudaMemsetAsync(ce, 0, (size_t)ncell(C.d) * sizeof(T), c->stream));
   TRYS(vcycle_curv<T>(c, l + 1, ce, ceo, (const T*)C.r, tr));
   TRY(launch_prolong_add<T>(c->stream, C.d, ce, e));
-  TRYS(curv_smooth<T>(c, l, e, eo, r, c->o.nu2, tr));
+  TRYS(curv_smooth<T>(c, l, e, eo, r, c->o.nu2, tr, false));
   return GBMG_OK;
 }
 
@@ -104,7 +115,7 @@ gbmg_status curv_solve_impl(gbmg_ctx* c, const double* src, const double* u_in, 
   while (!mon.done()) {
     float* e = (float*)L0.e;
     float* eo = (float*)L0.e2;
-    TRY(cudaMemsetAsync(e, 0, (size_t)n * sizeof(float), c->stream));
+    if (c->o.nu1 == 0) TRY(cudaMemsetAsync(e, 0, (size_t)n * sizeof(float), c->stream));
     TRYS(vcycle_curv<float>(c, 0, e, eo, r0, tr));
     TRY(launch_df_update(c->stream, n, c->phi_df, e, nullptr));
     {
@@ -264,11 +275,13 @@ extern "C" gbmg_status mg_curv_residual(gbmg_ctx* c, int level, int transpose, c
 
 extern "C" gbmg_status mg_curv_smooth(gbmg_ctx* c, int level, int transpose, const float* e_in, const float* r,
                                       float* e_out) {
-  TRYS(curv_component_check(c, level, e_in, r, e_out, "mg_curv_smooth"));
+  TRYS(curv_component_check(c, level, r, r, e_out, "mg_curv_smooth"));
   if (e_in == e_out) return fail(GBMG_ERR_INVALID_ARG, "mg_curv_smooth: e_in and e_out must differ");
   DeviceGuard g(c->device);
   const Level& L = c->lv[level];
-  TRY(launch_curv_jacobi<float>(c->stream, L.d, L.cc, r, e_in, e_out, curv_form(c, transpose != 0), (float)c->o.omega));
+  const int form = curv_form(c, transpose != 0);
+  if (e_in) TRY(launch_curv_jacobi<float>(c->stream, L.d, L.cc, r, e_in, e_out, form, (float)c->o.omega));
+  else TRY(launch_curv_jacobi_zero(c->stream, L.d, L.cc, r, e_out, form, (float)c->o.omega));
   return GBMG_OK;
 }
 

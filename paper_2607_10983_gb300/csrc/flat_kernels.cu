@@ -5,6 +5,9 @@
 // launch, one thread per cell, periodic neighbours by explicit index wrap.  In FP64
 // they form the baseline "plain FP64 V-cycle"; in FP32 they are the reference
 // against which the temporally blocked kernels are checked bit for bit.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "kernels.h"
 #include "stencil.cuh"
 
@@ -177,6 +180,16 @@ __global__ void k_shift(long long n, const T* __restrict__ x, const double* __re
   const T s = (T)shift[0];
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     out[i] = t_sub(x[i], s);
+}
+
+// Storage of a coarse-level correction in a 16-bit format: each value rounded to
+// nearest (ties to even) in BF16 (mode 1) or FP16 (mode 2) and held as FP32 again.
+template <int MODE>
+__global__ void k_round16(long long n, float* __restrict__ e) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float v = e[i];
+    e[i] = MODE == 1 ? __bfloat162float(__float2bfloat16_rn(v)) : __half2float(__float2half_rn(v));
+  }
 }
 
 // A few device scalars into page-locked host memory through its device address (no copy
@@ -408,6 +421,14 @@ cudaError_t launch_sum(cudaStream_t st, long long n, const T* x, double* ps, dou
 template <typename T>
 cudaError_t launch_shift(cudaStream_t st, long long n, const T* x, const double* shift, T* out) {
   k_shift<T><<<red_blocks(n), RED_THREADS, 0, st>>>(n, x, shift, out);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_round16(cudaStream_t st, long long n, float* e, int mode) {
+  if (mode == 1) k_round16<1><<<red_blocks(n), RED_THREADS, 0, st>>>(n, e);
+  else if (mode == 2) k_round16<2><<<red_blocks(n), RED_THREADS, 0, st>>>(n, e);
+  else return cudaErrorInvalidValue;
   note_launch();
   return cudaGetLastError();
 }

@@ -66,6 +66,7 @@ extern "C" void gbmg_default_opts(gbmg_opts* o) {
   o->fused = 1;
   o->krylov = 0;
   o->curv_sym = 0;
+  o->coarse_store = 0;
 }
 
 extern "C" const char* mg_status_string(gbmg_status s) {
@@ -116,6 +117,10 @@ extern "C" gbmg_status mg_setup(gbmg_ctx** out, int nx, int ny, int nz, int leve
   if (o.curv_sym != 0 && o.curv_sym != 1) return fail(GBMG_ERR_INVALID_ARG, "mg_setup: curv_sym must be 0 or 1");
   if (o.curv_sym && o.op != GBMG_OP_CURV19)
     return fail(GBMG_ERR_INVALID_ARG, "mg_setup: curv_sym needs the curvilinear operator");
+  if (o.coarse_store < 0 || o.coarse_store > 2)
+    return fail(GBMG_ERR_INVALID_ARG, "mg_setup: coarse_store must be 0 (FP32), 1 (BF16) or 2 (FP16)");
+  if (o.coarse_store && !(o.op == GBMG_OP_FLAT7 && o.prec == GBMG_MIXED))
+    return fail(GBMG_ERR_INVALID_ARG, "mg_setup: coarse_store needs the flat operator in mixed precision");
   const bool curv = o.op == GBMG_OP_CURV19;
 
   std::vector<Dims> dims = level_dims(nx, ny, nz, levels);

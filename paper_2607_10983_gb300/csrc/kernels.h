@@ -65,6 +65,8 @@ cudaError_t launch_sum(cudaStream_t st, long long n, const T* x, double* partial
 template <typename T>
 cudaError_t launch_shift(cudaStream_t st, long long n, const T* x, const double* shift_dev, T* out);
 
+// e[i] = e[i] rounded to BF16 (mode 1) or FP16 (mode 2), kept as FP32.
+cudaError_t launch_round16(cudaStream_t st, long long n, float* e, int mode);
 // out[0] = scale * (sum of `count` partials), summed in a fixed order (one block).
 cudaError_t launch_finalize(cudaStream_t st, const double* partials, long long count, double* out, double scale);
 // n <= 32 doubles from device memory into page-locked host memory (its device address)
@@ -133,6 +135,9 @@ template <typename T>
 cudaError_t launch_curv_jacobi(cudaStream_t st, Dims d, CurvCoef cf, const T* r, const T* e_in, T* e_out, int form,
                                T omega);
 // dense n x n matrix of op / J on a (small) level, FP64 row-major
+// e_out = the weighted-Jacobi sweep of an iterate that is zero (pointwise; FP32)
+cudaError_t launch_curv_jacobi_zero(cudaStream_t st, Dims d, CurvCoef cf, const float* r, float* e_out, int form,
+                                    float omega);
 cudaError_t launch_curv_dense(cudaStream_t st, Dims d, CurvCoef cf, int form, double* out);
 // double-float outer residual: r = b - op(u)/J with b = J (src - m) (scale_J) or src
 // block partial sums written by launch_curv_df_residual and launch_curv_residual<float>

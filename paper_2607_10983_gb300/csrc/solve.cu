@@ -81,6 +81,15 @@ bool gbmg::small_cycle_params(const gbmg_ctx* c, int l, SmallCycle* out) {
 
 namespace {
 
+// With opts.coarse_store, the correction of a level with fewer than 128^3 cells is held
+// in BF16 or FP16 from the moment it is handed up to the next finer level.
+constexpr long long kCoarseStoreCells = 128ll * 128 * 128;
+gbmg_status store_coarse_correction(gbmg_ctx* c, int l, float* e) {
+  if (!c->o.coarse_store || ncell(c->lv[l].d) >= kCoarseStoreCells) return GBMG_OK;
+  TRY(launch_round16(c->stream, ncell(c->lv[l].d), e, c->o.coarse_store));
+  return GBMG_OK;
+}
+
 // V-cycle (Sec. 2.3) on level l for A_l e = r, one kernel per operation.  e / eo are
 // the level's ping-pong buffers; on return e points at the result.
 template <typename T>
@@ -108,6 +117,7 @@ gbmg_status vcycle_unfused(gbmg_ctx* c, int l, T*& e, T*& eo, const T* r) {
   if (l + 1 < c->L - 1 && !(sizeof(T) == 4 && small_cycle_from(c, l + 1, nullptr)))
     TRY(cudaMemsetAsync(ce, 0, (size_t)ncell(C.d) * sizeof(T), c->stream));
   TRYS(vcycle_unfused<T>(c, l + 1, ce, ceo, (const T*)C.r));
+  if constexpr (sizeof(T) == 4) TRYS(store_coarse_correction(c, l + 1, (float*)ce));
   TRY(launch_prolong_add<T>(c->stream, C.d, ce, e));
   TRYS(smooth_pass<T>(c, l, e, eo, r, dv, true));
   return GBMG_OK;
@@ -146,6 +156,7 @@ gbmg_status vcycle_fused(gbmg_ctx* c, int l, float*& e, const float* r) {
   }
   float* ce = nullptr;
   TRYS(vcycle_fused(c, l + 1, ce, (const float*)C.r));
+  TRYS(store_coarse_correction(c, l + 1, ce));
   {
     ProfScope ps(c, l == 0 ? GBMG_PROF_UP0 : GBMG_PROF_OFF);
     TRY(launch_up_fused(c->stream, c->o.degree, L.d, (const float*)L.e, ce, r, (float*)L.e2, L.h,
