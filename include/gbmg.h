@@ -133,6 +133,18 @@ gbmg_status mg_set_stream(gbmg_ctx* ctx, void* cuda_stream);
  * is not positive (a folded mesh). */
 gbmg_status mg_set_geometry(gbmg_ctx* ctx, const double* psi_dev);
 
+/* Curvilinear contexts only: set the operator's coefficients directly instead of from psi.
+ * J_dev: the volume element sqrt(g) of the finest level (nx*ny*nz floats, > 0); B_dev: the
+ * six components of the symmetric B = sqrt(g) g^-1 (Sec. 4.3.1), 6 * nx*ny*nz floats packed
+ * xx, yy, zz, xy, xz, yz.  The operator M of Sec. 4.3.1 is built from them on the finest
+ * level; each coarser level takes the full-weighting restriction (Appendix B weights) of
+ * the finer level's J and B (the paper rebuilds coarse geometry from a restricted psi
+ * instead; with coefficients alone there is no psi to restrict).  The coarsest operator is
+ * inverted exactly.  mg_solve then needs coeffs_dev = NULL; mg_solve_adjoint gives
+ * source_bar but no psi_bar (GBMG_ERR_STATE).  Waits for the stream.  Errors as for
+ * mg_set_geometry. */
+gbmg_status mg_set_coefficients(gbmg_ctx* ctx, const float* J_dev, const float* B_dev);
+
 /* Solve A phi = F (Sec. 2.1) or, on a curvilinear context, L phi = f (Sec. 4.3).
  * source_dev: F (nx*ny*nz doubles; its mean, or volume-weighted mean for the
  * curvilinear operator, is projected out; the buffer is not modified).  coeffs_dev:

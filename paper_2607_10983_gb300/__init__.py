@@ -96,6 +96,7 @@ _SIGS = {
     "mg_df_to_f64": (_S, [_P, _LL, _P, _P]),
     "mg_df_residual": (_S, [_P, _P, _D, _P, _P]),
     "mg_set_geometry": (_S, [_P, _P]),
+    "mg_set_coefficients": (_S, [_P, _P, _P]),
     "mg_solve_adjoint": (_S, [_P, _P, _P, _P, _P, _P, _D, _I, ctypes.POINTER(_Stats)]),
     "mg_curv_apply": (_S, [_P, _I, _I, _I, _I, _P, _P]),
     "mg_curv_geometry": (_S, [_P, _I, _P, _P]),
@@ -246,6 +247,12 @@ class Solver:
     def set_geometry(self, psi: torch.Tensor):
         """Curvilinear contexts: set the deformation potential psi (float64, mesh shape)."""
         _check(lib().mg_set_geometry(self._c(), _ptr(psi, torch.float64, self.shape)))
+
+    def set_coefficients(self, J: torch.Tensor, B: torch.Tensor):
+        """Curvilinear contexts: set J (float32, mesh shape) and B (float32, (6,) + mesh shape,
+        packed xx, yy, zz, xy, xz, yz) directly; coarse levels restrict them."""
+        _check(lib().mg_set_coefficients(self._c(), _ptr(J, torch.float32, self.shape),
+                                         _ptr(B, torch.float32, (6,) + self.shape)))
 
     def solve(self, F: torch.Tensor, phi: torch.Tensor | None = None, tol: float = 1e-6,
               max_vcycles: int = 50, raise_on_nonconvergence: bool = False, psi: torch.Tensor | None = None):

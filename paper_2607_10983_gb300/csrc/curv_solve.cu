@@ -154,6 +154,33 @@ gbmg_status gbmg::curv_solve(gbmg_ctx* c, const double* F, double* phi, double t
   return curv_solve_impl(c, F, phi, phi, tol, maxv, st, false);
 }
 
+namespace {
+
+// Exact inverses of the coarsest operator and of its transposed-solve twin (minimum-norm,
+// left null vector J), built from the coarsest level's coefficients.  Waits for the stream.
+gbmg_status build_coarsest(gbmg_ctx* c, const char* who) {
+  const Level& C = c->lv[c->L - 1];
+  const int nc = c->nc;
+  std::vector<float> Jc(nc);
+  TRY(cudaMemcpyAsync(Jc.data(), C.cc.J, (size_t)nc * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  std::vector<double> Lm((size_t)nc * nc), G;
+  for (int tr = 0; tr < 2; ++tr) {
+    TRY(launch_curv_dense(c->stream, C.d, C.cc, curv_form(c, tr != 0), c->dense));
+    TRY(cudaMemcpyAsync(Lm.data(), c->dense, Lm.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    TRY(cudaStreamSynchronize(c->stream));
+    std::vector<double> w(Jc.begin(), Jc.end());
+    for (float v : Jc)
+      if (!(v > 0.f)) return fail(GBMG_ERR_INVALID_ARG, std::string(who) + ": non-positive volume element on the coarsest level");
+    if (!dense_pinv(nc, Lm, w, G)) return fail(GBMG_ERR_INVALID_ARG, std::string(who) + ": coarsest operator is singular");
+    std::vector<float> G32(G.begin(), G.end());
+    TRY(cudaMemcpy(tr ? c->G64T : c->G64, G.data(), G.size() * sizeof(double), cudaMemcpyHostToDevice));
+    TRY(cudaMemcpy(tr ? c->G32T : c->G32, G32.data(), G32.size() * sizeof(float), cudaMemcpyHostToDevice));
+  }
+  return GBMG_OK;
+}
+
+}  // namespace
+
 extern "C" gbmg_status mg_set_geometry(gbmg_ctx* c, const double* psi_dev) {
   if (!c || !psi_dev) return fail(GBMG_ERR_INVALID_ARG, "mg_set_geometry: NULL argument");
   if (c->o.op != GBMG_OP_CURV19) return fail(GBMG_ERR_STATE, "mg_set_geometry: context is not curvilinear");
@@ -171,24 +198,33 @@ extern "C" gbmg_status mg_set_geometry(gbmg_ctx* c, const double* psi_dev) {
     for (int k = 0; k < 6; ++k) o.B[k] = (float*)L.cc.B[k];
     TRY(launch_geom(c->stream, L.d, L.psi, L.h, o));
   }
-  // exact inverse of the coarsest operator and of its transposed-solve twin
-  const Level& C = c->lv[c->L - 1];
-  const int nc = c->nc;
-  std::vector<float> Jc(nc);
-  TRY(cudaMemcpyAsync(Jc.data(), C.cc.J, (size_t)nc * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
-  std::vector<double> Lm((size_t)nc * nc), G;
-  for (int tr = 0; tr < 2; ++tr) {
-    TRY(launch_curv_dense(c->stream, C.d, C.cc, curv_form(c, tr != 0), c->dense));
-    TRY(cudaMemcpyAsync(Lm.data(), c->dense, Lm.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    TRY(cudaStreamSynchronize(c->stream));
-    std::vector<double> w(Jc.begin(), Jc.end());
-    for (float v : Jc)
-      if (!(v > 0.f)) return fail(GBMG_ERR_INVALID_ARG, "mg_set_geometry: non-positive volume element on the coarsest level");
-    if (!dense_pinv(nc, Lm, w, G)) return fail(GBMG_ERR_INVALID_ARG, "mg_set_geometry: coarsest operator is singular");
-    std::vector<float> G32(G.begin(), G.end());
-    TRY(cudaMemcpy(tr ? c->G64T : c->G64, G.data(), G.size() * sizeof(double), cudaMemcpyHostToDevice));
-    TRY(cudaMemcpy(tr ? c->G32T : c->G32, G32.data(), G32.size() * sizeof(float), cudaMemcpyHostToDevice));
+  TRYS(build_coarsest(c, "mg_set_geometry"));
+  c->geom_ready = true;
+  c->geom_from_psi = true;
+  return GBMG_OK;
+}
+
+extern "C" gbmg_status mg_set_coefficients(gbmg_ctx* c, const float* J_dev, const float* B_dev) {
+  if (!c || !J_dev || !B_dev) return fail(GBMG_ERR_INVALID_ARG, "mg_set_coefficients: NULL argument");
+  if (c->o.op != GBMG_OP_CURV19) return fail(GBMG_ERR_STATE, "mg_set_coefficients: context is not curvilinear");
+  DeviceGuard g(c->device);
+  c->geom_ready = false;
+  c->geom_from_psi = false;
+  const size_t b0 = (size_t)ncell(c->lv[0].d) * sizeof(float);
+  for (int l = 0; l < c->L; ++l) {
+    Level& L = c->lv[l];
+    if (l == 0) {
+      TRY(cudaMemcpyAsync((float*)L.cc.J, J_dev, b0, cudaMemcpyDeviceToDevice, c->stream));
+      for (int k = 0; k < 6; ++k)
+        TRY(cudaMemcpyAsync((float*)L.cc.B[k], (const char*)B_dev + k * b0, b0, cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+      // coarse coefficients: full-weighting restriction of the finer level's coefficients
+      const Level& F = c->lv[l - 1];
+      TRY(launch_restrict<float>(c->stream, F.d, F.cc.J, (float*)L.cc.J));
+      for (int k = 0; k < 6; ++k) TRY(launch_restrict<float>(c->stream, F.d, F.cc.B[k], (float*)L.cc.B[k]));
+    }
   }
+  TRYS(build_coarsest(c, "mg_set_coefficients"));
   c->geom_ready = true;
   return GBMG_OK;
 }
@@ -211,6 +247,8 @@ extern "C" gbmg_status mg_solve_adjoint(gbmg_ctx* c, const double* phi_bar_dev, 
   if (!c->geom_ready) return fail(GBMG_ERR_STATE, "mg_solve_adjoint: no geometry set");
   if (psi_bar_dev && (!phi_dev || !source_dev))
     return fail(GBMG_ERR_INVALID_ARG, "mg_solve_adjoint: psi_bar needs the forward solution and source");
+  if (psi_bar_dev && !c->geom_from_psi)
+    return fail(GBMG_ERR_STATE, "mg_solve_adjoint: psi_bar needs a geometry set from psi, not raw coefficients");
   TRYS(ensure_adjoint_scratch(c));
   gbmg_stats st;
   std::memset(&st, 0, sizeof(st));

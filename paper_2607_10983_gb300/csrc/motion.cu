@@ -97,6 +97,7 @@ extern "C" gbmg_status mg_mesh_motion(gbmg_ctx* c, const double* rho_dev, double
   TRY(launch_shift<double>(c->stream, n, psi_inout_dev, c->scal + S_MOTION_MEAN, psi_inout_dev));
   TRY(cudaStreamSynchronize(c->stream));
   c->geom_ready = false;  // psi moved: the next curvilinear solve must set the geometry again
+  c->geom_from_psi = false;
   c->last = st;
   if (stats) *stats = st;
   return (gbmg_status)st.status;

@@ -60,7 +60,8 @@ struct gbmg_ctx {
   double* G64T = nullptr;       // curvilinear: pseudo-inverse of the transposed-solve operator
   float* G32T = nullptr;
   double* dense = nullptr;      // curvilinear: nc x nc scratch for the coarsest operator
-  bool geom_ready = false;      // curvilinear: mg_set_geometry has run
+  bool geom_ready = false;      // curvilinear: mg_set_geometry or mg_set_coefficients has run
+  bool geom_from_psi = false;   // the coefficients were built from psi (psi_bar needs psi)
   bool fused_all = false;       // testing: blocked kernels on every level of at least 16^3
   double* adj_S = nullptr;      // adjoint scratch (6 finest fields), allocated on first use
   double* adj_lam = nullptr;    // adjoint scratch (1 finest field)
