@@ -407,14 +407,16 @@ def e2e_leg(args, solver, host_src):
             raise RuntimeError("e2e sequence did not converge")
 
     step()
-    steps = max(1, min(args.steps, 2))
-    t0 = time.perf_counter()
+    steps = max(1, min(args.steps, 3))
+    per_step = []
     for _ in range(steps):
+        t0 = time.perf_counter()
         step()
-    dt = time.perf_counter() - t0
+        per_step.append(time.perf_counter() - t0)
+    dt = sum(per_step)
     b = n ** 3 * 8
     return {"value": seq * steps / dt, "unit": UNIT, "h2d_bytes_per_step": seq * b,
-            "d2h_bytes_per_step": seq * b,
+            "d2h_bytes_per_step": seq * b, "ms_per_step": [1000.0 * x for x in per_step],
             "api": "mg_solve_host_sequence (pinned host buffers; the first solve starts from zero, each later one "
                    "from the previous solution on the device)"}
 
