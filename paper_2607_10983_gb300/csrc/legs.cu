@@ -25,6 +25,8 @@
 // Schedule: persistent grid of one CTA per SM; the (tile, plane) pairs form one
 // tile-major list and CTA b runs the contiguous range [b T / G, (b+1) T / G), as one
 // z segment per tile it touches (each segment with its own warm-up planes).
+#include <type_traits>
+
 #include "legs.cuh"
 
 namespace gbmg {
@@ -72,13 +74,16 @@ k_up_fused(Dims d, const float* __restrict__ e_in, const float* __restrict__ ec,
 // ------------------------------------------------------------------ launch
 
 // Tiles per degree: 64 x 32 cells; block sizes are multiples of 128 threads
-// (registers are granted to groups of four warps).  Down leg: columns of R = 4 pairs,
-// 384 threads (the degree-4 leg, halo 5, uses 64 x 24 so its columns still fit).
-// Up leg: columns of R = 3 pairs, 512 threads (16 warps per SM; measured faster than
-// 4-pair columns for this leg, slower for the down leg, whose state per pair is larger).
+// (registers are granted to groups of four warps).  Down leg (degrees 1-3): columns of
+// R = 3 pairs, 512 threads: 16 warps per SM within 128 registers (0.554 ms at 512^3
+// against 0.595 with 4-pair columns in 384 threads, 12 warps at 168 registers: the leg
+// is bound by dependency latency, which more warps hide); degree 4 (halo 5) keeps 4-pair
+// columns, 384 threads and a 64 x 24 tile, which fit its shared memory.  Up leg: columns
+// of R = 4 pairs, 384 threads (even R makes each row's y parity, and with it the
+// prolongation's coarse-row pattern, a compile-time constant).
 template <int V>
 struct DownTile {
-  using T = PTile<64, (V >= 4 ? 24 : 32), V + 1, 384, 4>;
+  using T = typename std::conditional<(V >= 4), PTile<64, 24, V + 1, 384, 4>, PTile<64, 32, V + 1, 512, 3>>::type;
 };
 template <int V>
 struct UpTile {
