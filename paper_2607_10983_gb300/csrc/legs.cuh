@@ -55,7 +55,11 @@ struct PPos {
 #pragma unroll
     for (int j = 0; j < TL::R; ++j) {
       const int py = pyb * TL::R + j, uy = y0 - TL::H + py;
-      goff[j] = gx + wrapmod(uy, d.ny) * d.nx;
+      // rows beyond the haloed region (the last thread row's overhang, idle threads) read
+      // the region's last row again: cache hits instead of DRAM reads of rows no output
+      // depends on
+      const int ul = y0 - TL::H + (py < TL::WY ? py : TL::WY - 1);
+      goff[j] = gx + wrapmod(ul, d.ny) * d.nx;
       const bool in = threadIdx.x < TL::NCOL && px >= TL::HX / 2 && px < TL::HX / 2 + TL::TX / 2 &&
                       py >= TL::H && py < TL::H + TL::TY && ux < d.nx && uy < d.ny;
       if (in) tmask |= 1u << j;
