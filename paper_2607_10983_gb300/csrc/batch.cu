@@ -44,8 +44,8 @@ constexpr int DFZC = 32;         // z planes per item of the fused double-float 
 
 // tiles of the fused device code at BT threads
 // (columns of 3 pairs for both legs: this kernel holds the state of every phase under
-// one register limit of BT threads per SM, and 4-pair columns spill there, which the
-// separate leg kernels do not)
+// one register limit of BT threads per SM, and the up leg's 4-pair columns, which its
+// separate kernel uses, spill there)
 constexpr int down_ty(int v) { return v >= 4 ? 20 : 22; }
 constexpr int up_ty(int v) { return v >= 4 ? 20 : 24; }
 template <int V>
