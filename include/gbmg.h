@@ -88,8 +88,8 @@ typedef struct {
                  /* symbol for constant B; forward and adjoint solves use M itself.     */
   int coarse_store; /* flat + GBMG_MIXED only.  Storage of the correction that a coarse  */
                  /* level (fewer than 128^3 cells) hands up to the next finer level:     */
-                 /* 0: FP32; 1: BF16; 2: FP16 (the north-star's precision option for    */
-                 /* coarse-level corrections; the paper runs FP32 throughout, Sec. 3.3). */
+                 /* 0: FP32; 1: BF16; 2: FP16 (16-bit storage of coarse-level          */
+                 /* corrections; the paper runs FP32 throughout, Sec. 3.3).              */
                  /* The value is rounded to that format before the prolongation; levels */
                  /* solved inside the shared-memory bottom cycle (16^3 and below) keep   */
                  /* FP32 within it.  Not supported by batches.                          */

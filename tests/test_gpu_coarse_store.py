@@ -1,7 +1,7 @@
 """Coarse-level corrections stored in BF16 / FP16 (opts.coarse_store), against the oracle (GPU).
 
-The north-star's precision option: the correction a level of fewer than 128^3 cells hands
-up to the next finer level is held in a 16-bit format.  Inside the double-float defect
+A precision option of the mixed solve: the correction a level of fewer than 128^3 cells
+hands up to the next finer level is held in a 16-bit format.  Inside the double-float defect
 correction (Sec. 3.2) the converged solution must still be the FP64 oracle's FFT solution;
 the tests check that, the cycle cost, and that the rounding really takes place.
 """
