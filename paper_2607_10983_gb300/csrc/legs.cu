@@ -24,7 +24,10 @@
 //
 // Schedule: persistent grid of one CTA per SM; the (tile, plane) pairs form one
 // tile-major list and CTA b runs the contiguous range [b T / G, (b+1) T / G), as one
-// z segment per tile it touches (each segment with its own warm-up planes).
+// z segment per tile it touches (each segment with its own warm-up planes).  Each
+// tile's z stream starts at its own phase (tile_phase), so that neighbouring tiles
+// stream the same planes at about the same time and their shared halo rows are read
+// from DRAM about once.
 #include <type_traits>
 
 #include "legs.cuh"
@@ -44,11 +47,13 @@ k_down_fused(Dims d, const float* __restrict__ r, float* __restrict__ e_out, flo
   const long long b = (long long)(blockIdx.x + 1) * sc.total / gridDim.x;
   while (a < b) {
     const long long tile = a / d.nz;
-    const int z0 = (int)(a % d.nz);
-    const int zend = (int)(z0 + (b - a) < d.nz ? z0 + (b - a) : d.nz);
+    const int p0 = (int)(a - tile * d.nz);
+    const int z0 = (tile_phase(tile * d.nz, d.nz, sc.total, gridDim.x) + p0) % d.nz;
+    int len = (int)(b - a < d.nz - p0 ? b - a : d.nz - p0);
+    if (len > d.nz - z0) len = d.nz - z0;  // not taken (tile_phase): a run never crosses plane nz
     down_segment<V, TL>(d, r, e_out, rc, (int)(tile % sc.tiles_x) * TL::TX, (int)(tile / sc.tiles_x) * TL::TY, z0,
-                        zend, inv_h2, cf, sm);
-    a += zend - z0;
+                        z0 + len, inv_h2, cf, sm);
+    a += len;
     __syncthreads();
   }
 }
@@ -62,11 +67,13 @@ k_up_fused(Dims d, const float* __restrict__ e_in, const float* __restrict__ ec,
   const long long b = (long long)(blockIdx.x + 1) * sc.total / gridDim.x;
   while (a < b) {
     const long long tile = a / d.nz;
-    const int z0 = (int)(a % d.nz);
-    const int zend = (int)(z0 + (b - a) < d.nz ? z0 + (b - a) : d.nz);
+    const int p0 = (int)(a - tile * d.nz);
+    const int z0 = (tile_phase(tile * d.nz, d.nz, sc.total, gridDim.x) + p0) % d.nz;
+    int len = (int)(b - a < d.nz - p0 ? b - a : d.nz - p0);
+    if (len > d.nz - z0) len = d.nz - z0;  // not taken (tile_phase): a run never crosses plane nz
     up_segment<V, TL>(d, e_in, ec, r, e_out, (int)(tile % sc.tiles_x) * TL::TX, (int)(tile / sc.tiles_x) * TL::TY,
-                      z0, zend, inv_h2, cf, sm);
-    a += zend - z0;
+                      z0, z0 + len, inv_h2, cf, sm);
+    a += len;
     __syncthreads();
   }
 }

@@ -79,6 +79,23 @@ struct Sched {
   long long total;  // tiles * nz
 };
 
+// z phase of a tile's stream.  The (tile, plane) units [u0, u0 + nz) of one tile are
+// split among the CTAs of a contiguous-range schedule over `total` units and G CTAs;
+// position p of the tile is plane (phase + p) mod nz (the mesh is periodic in z, so a
+// tile's stream may start anywhere).  The phase puts plane 0 where the CTA owning the
+// tile's middle unit starts (or, if that CTA entered from the previous tile, where the
+// next CTA starts): that CTA then streams plane tau at its step tau, like the chosen
+// CTAs of the other tiles, so that neighbouring tiles read the halo rows they share at
+// about the same time (from L2 for the second reader).  As plane 0 falls on a CTA
+// boundary, no CTA's run within the tile crosses the end of the mesh.  The planes and
+// the arithmetic of every output are unchanged.
+__device__ __forceinline__ int tile_phase(long long u0, int nz, long long total, long long G) {
+  const long long bm = ((u0 + nz / 2 + 1) * G - 1) / total;  // owner of unit u0 + nz / 2
+  long long sb = bm * total / G;
+  if (sb < u0) sb = (bm + 1) * total / G;
+  return sb < u0 + nz ? (int)((u0 + nz - sb) % nz) : 0;
+}
+
 __device__ __forceinline__ float2 ld2(const float* p) { return __ldg(reinterpret_cast<const float2*>(p)); }
 __device__ __forceinline__ void st2(float* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
 
