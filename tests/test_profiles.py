@@ -22,8 +22,10 @@ def test_profiles_are_short_text_with_their_command():
 
 
 def test_traffic_table_covers_the_timed_families():
-    # one row per timed family: DRAM bytes per cell (at least the algorithmic bytes) and the
-    # 16-hex-digit source digest that bench.py compares before reporting roofline.traffic
+    # one row per timed family: DRAM bytes per cell and the 16-hex-digit source digest that
+    # bench.py compares before reporting roofline.traffic.  The bytes are at least the
+    # algorithmic bytes less what the L2 (126 MB on a GB300) can still hold as dirty lines
+    # when the kernel ends, per cell of the 384^3 capture.
     import bench
     rows = {}
     with open(os.path.join(PROFILES, "ncu_traffic.txt")) as fh:
@@ -33,5 +35,5 @@ def test_traffic_table_covers_the_timed_families():
                 rows[cols[0]] = (float(cols[3]), cols[4])
     assert set(rows) == {"down0", "up0", "df0"}
     for fam, (bpc, digest) in rows.items():
-        assert bpc >= 0.99 * bench.BYTES_PER_CELL[fam], fam
+        assert bpc >= bench.BYTES_PER_CELL[fam] - 126e6 / 384**3, fam
         assert re.fullmatch(r"[0-9a-f]{16}", digest), fam
