@@ -964,11 +964,13 @@ __global__ void __launch_bounds__(CNT) k_psibar_tiled(Dims d, const double* __re
   }
 }
 
-// z chunk: at least four waves of four CTAs per SM.
+// z chunk: halved until there are four waves of four CTAs per SM, down to 4 planes (on
+// small levels a CTA's planes are a chain of dependent load rounds: 8-plane chunks made
+// the 256^3 moving-mesh solve 2% slower); the outputs do not depend on it.
 int curv_zchunk(Dims d) {
   const long long tiles = (long long)((d.nx + CTX - 1) / CTX) * ((d.ny + CTY - 1) / CTY);
   int zc = d.nz;
-  while (zc > 8 && tiles * ((d.nz + zc - 1) / zc) < 4 * 4 * 152) zc = (zc + 1) / 2;
+  while (zc > 4 && tiles * ((d.nz + zc - 1) / zc) < 4 * 4 * 152) zc = (zc + 1) / 2;
   return zc;
 }
 dim3 curv_tiled_grid(Dims d) {
@@ -1220,11 +1222,20 @@ long long curv_partial_count(Dims d) {
   return (long long)g.x * g.y * g.z;
 }
 
+// FP32 sweeps and residuals of levels of at most 32^3 cells run one thread per cell
+// (k_curv_jacobi / k_curv_residual: every load of a cell in one round) instead of the
+// z-streaming tiles, whose few CTAs there take one dependent round of loads per plane.
+// Both evaluate the same operator templates in the same order, so the results are the
+// same bits (the moving-mesh solve's phi, delta-bar and psi-bar were compared).
+static bool curv_cellwise(Dims d) { return (long long)d.nx * d.ny * d.nz <= 32 * 32 * 32; }
+
 template <typename T>
 cudaError_t launch_curv_residual(cudaStream_t st, Dims d, CurvCoef cf, const T* r, const T* u, T* out, int form,
                                  double* partials) {
   if (form < 0 || form > 2) return cudaErrorInvalidValue;
-  if constexpr (sizeof(T) == 4) {
+  if (sizeof(T) == 4 && !partials && curv_cellwise(d)) {
+    k_curv_residual<T><<<cell_grid(d), dim3(BX, BY), 0, st>>>(d, cf, r, u, out, (T)(1.0 / cf.h2), form, partials);
+  } else if constexpr (sizeof(T) == 4) {
     const size_t sm = 4 * ring_slot_bytes<float>();
     const float ih2 = (float)(1.0 / cf.h2);
     const dim3 g = curv_tiled_grid(d);
@@ -1243,7 +1254,9 @@ template <typename T>
 cudaError_t launch_curv_jacobi(cudaStream_t st, Dims d, CurvCoef cf, const T* r, const T* e_in, T* e_out, int form,
                                T omega) {
   if (form < 0 || form > 2) return cudaErrorInvalidValue;
-  if constexpr (sizeof(T) == 4) {
+  if (sizeof(T) == 4 && curv_cellwise(d)) {
+    k_curv_jacobi<T><<<cell_grid(d), dim3(BX, BY), 0, st>>>(d, cf, r, e_in, e_out, form, omega);
+  } else if constexpr (sizeof(T) == 4) {
     const size_t sm = 4 * ring_slot_bytes<float>();
     const dim3 g = curv_tiled_grid(d);
     const int zc = curv_zchunk(d);
