@@ -5,6 +5,8 @@
 // launch, one thread per cell, periodic neighbours by explicit index wrap.  In FP64
 // they form the baseline "plain FP64 V-cycle"; in FP32 they are the reference
 // against which the temporally blocked kernels are checked bit for bit.
+#include <cstdint>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -137,6 +139,37 @@ __global__ void k_prolong_add(Dims dc, const T* __restrict__ c, T* __restrict__ 
   if (x >= df.nx || y >= df.ny) return;
   const long long i = lin(df, x, y, z);
   f[i] = t_add(f[i], prolong_value(c, dc, x, y, z));
+}
+
+// f += P c in FP32 with one thread per coarse cell (I, J, K): the eight coarse values at
+// I..I+1, J..J+1, K..K+1 (periodic) are loaded once and give the fine cells {2I, 2I+1} x
+// {2J, 2J+1} x {2K, 2K+1}, each formed like prolong_value (x, then y, then z midpoints,
+// the same roundings), so the results are the same bits as k_prolong_add's; the fine
+// rows are read and written as x-pairs (f 8-byte aligned).
+__global__ void k_prolong_add_blocks(Dims dc, const float* __restrict__ c, float* __restrict__ f) {
+  const int I = blockIdx.x * BX + threadIdx.x, J = blockIdx.y * BY + threadIdx.y, K = blockIdx.z;
+  if (I >= dc.nx || J >= dc.ny) return;
+  const Dims df{dc.nx * 2, dc.ny * 2, dc.nz * 2};
+  const int I1 = wrap_hi(I + 1, dc.nx), J1 = wrap_hi(J + 1, dc.ny), K1 = wrap_hi(K + 1, dc.nz);
+  // (fine x = 2I, fine x = 2I + 1) on the coarse row (jj, kk)
+  auto xpair = [&](int jj, int kk) {
+    const float v0 = c[lin(dc, I, jj, kk)];
+    return make_float2(v0, half_sum(v0, c[lin(dc, I1, jj, kk)]));
+  };
+  auto mid = [](float2 a, float2 b) { return make_float2(half_sum(a.x, b.x), half_sum(a.y, b.y)); };
+  const float2 xJK = xpair(J, K), xJ1K = xpair(J1, K), xJK1 = xpair(J, K1), xJ1K1 = xpair(J1, K1);
+  // fine rows 2J (dy = 0) and 2J + 1 (dy = 1) on the coarse planes K and K1
+  const float2 yK[2] = {xJK, mid(xJK, xJ1K)};
+  const float2 yK1[2] = {xJK1, mid(xJK1, xJ1K1)};
+#pragma unroll
+  for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy) {
+      const float2 v = dz ? mid(yK[dy], yK1[dy]) : yK[dy];
+      float2* const p = reinterpret_cast<float2*>(f + lin(df, 2 * I, 2 * J + dy, 2 * K + dz));
+      const float2 o = *p;
+      *p = make_float2(t_add(o.x, v.x), t_add(o.y, v.y));
+    }
 }
 
 // e = G r, one warp per row, lanes stride the columns; fixed summation order.
@@ -401,7 +434,10 @@ cudaError_t launch_restrict(cudaStream_t st, Dims fine, const T* f, T* c) {
 template <typename T>
 cudaError_t launch_prolong_add(cudaStream_t st, Dims coarse, const T* c, T* f) {
   const Dims df{coarse.nx * 2, coarse.ny * 2, coarse.nz * 2};
-  k_prolong_add<T><<<cell_grid(df), dim3(BX, BY), 0, st>>>(coarse, c, f);
+  if (sizeof(T) == 4 && ((uintptr_t)f & 7) == 0)
+    k_prolong_add_blocks<<<cell_grid(coarse), dim3(BX, BY), 0, st>>>(coarse, (const float*)c, (float*)f);
+  else
+    k_prolong_add<T><<<cell_grid(df), dim3(BX, BY), 0, st>>>(coarse, c, f);
   note_launch();
   return cudaGetLastError();
 }

@@ -78,6 +78,27 @@ def test_transfers(gb, shape, dtype, tol):
         assert rel_max(got, ref) < tol * 4
 
 
+@pytest.mark.parametrize("shape", [(32, 48, 64), (24, 24, 24), (16, 8, 32), (24, 20, 40), (20, 20, 20)])
+def test_prolong_add_fp32_forms_agree_bit_for_bit(gb, shape):
+    # FP32 prolongation into an 8-byte-aligned buffer runs one thread per coarse cell with
+    # x-pair accesses; into a view that starts one float further it runs one thread per
+    # fine cell: the same midpoints in the same order, so the same bits
+    s = gb.Solver(shape, prec="mixed")
+    for level in range(s.levels - 1):
+        fshape = s.level_shape(level)
+        base = to_dev(rand(fshape, 7), torch.float32)
+        coarse = to_dev(rand(s.level_shape(level + 1), 6), torch.float32)
+        aligned = base.clone()
+        buf = torch.empty(base.numel() + 1, dtype=torch.float32, device=DEV)
+        shifted = buf[1:].view(fshape)
+        shifted.copy_(base)
+        s.prolong_add(level, coarse, aligned)
+        s.prolong_add(level, coarse, shifted)
+        torch.cuda.synchronize()
+        assert aligned.data_ptr() % 8 == 0 and shifted.data_ptr() % 8 == 4
+        assert torch.equal(aligned, shifted)
+
+
 @pytest.mark.parametrize("shape", [(32, 32, 32), (24, 24, 24), (16, 8, 32), (8, 8, 8)])
 def test_coarse_solve(gb, shape):
     s = gb.Solver(shape, prec="fp64")
@@ -336,6 +357,20 @@ def test_fused_vcycle_bit_identical_to_unfused(gb, shape, degree, fused):
     r = to_dev(grf(shape, 19), torch.float32)
     a = gb.Solver(shape, prec="mixed", fused=fused, degree=degree).vcycle(r)
     b = gb.Solver(shape, prec="mixed", fused=False, degree=degree).vcycle(r)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+
+
+def test_fused_vcycle_bit_identical_with_more_tiles_than_ctas(gb):
+    # nx, ny, nz = 640, 512, 256: 160 tiles of 64 x 32 cells on the finest level, more than
+    # the 152 CTAs of the persistent legs, so some CTAs run whole tiles (whose z streams
+    # start at plane 0) and the others start at each tile's phase; the coarser levels have
+    # fewer tiles than CTAs, with runs that cross tile ends
+    shape = (256, 512, 640)
+    g = torch.Generator(device="cuda").manual_seed(23)
+    r = torch.randn(shape, generator=g, device="cuda", dtype=torch.float32)
+    a = gb.Solver(shape, prec="mixed", fused=1, degree=3).vcycle(r)
+    b = gb.Solver(shape, prec="mixed", fused=False, degree=3).vcycle(r)
     torch.cuda.synchronize()
     assert torch.equal(a, b)
 
