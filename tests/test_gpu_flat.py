@@ -192,7 +192,7 @@ def test_fixed_cycle_iterates_match_oracle(gb):
 
 
 @pytest.mark.parametrize("fused", [0, 2])
-@pytest.mark.parametrize("shape", [(32, 32, 32), (64, 64, 64), (16, 8, 32), (48, 48, 48)])
+@pytest.mark.parametrize("shape", [(32, 32, 32), (64, 64, 64), (16, 8, 32), (48, 48, 48), (56, 40, 112)])
 def test_mixed_solve_to_1e6(gb, shape, fused):
     F = grf(shape, 15)
     s = gb.Solver(shape, prec="mixed", fused=fused)
@@ -356,6 +356,20 @@ def test_fused_vcycle_bit_identical_to_unfused(gb, shape, degree, fused):
     # least 16^3)
     r = to_dev(grf(shape, 19), torch.float32)
     a = gb.Solver(shape, prec="mixed", fused=fused, degree=degree).vcycle(r)
+    b = gb.Solver(shape, prec="mixed", fused=False, degree=degree).vcycle(r)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("shape", [(112, 80, 144), (64, 112, 160), (56, 40, 112)])
+@pytest.mark.parametrize("degree", [2, 3])
+def test_fused_vcycle_bit_identical_on_ragged_tiles(gb, shape, degree):
+    # x and y sides that are not multiples of the 64 x 32 leg tiles (the last tile of each
+    # row and column hangs over the mesh) and odd coarse sides, blocked on every level of
+    # at least 16^3
+    g = torch.Generator(device="cuda").manual_seed(29)
+    r = torch.randn(shape, generator=g, device="cuda", dtype=torch.float32)
+    a = gb.Solver(shape, prec="mixed", fused=2, degree=degree).vcycle(r)
     b = gb.Solver(shape, prec="mixed", fused=False, degree=degree).vcycle(r)
     torch.cuda.synchronize()
     assert torch.equal(a, b)
