@@ -466,3 +466,27 @@ def test_krylov_option_validation(gb):
         gb.Solver(32, krylov=2, prec="fp64")
     with pytest.raises(gb.GbmgError):
         gb.Solver(16, op="curv", krylov=1)
+
+
+def test_solves_on_side_streams_match_default_stream(gb):
+    # every call runs on torch's current stream: two contexts solving on two side streams
+    # give the same bits as on the default stream
+    shape = (32, 48, 64)
+    F1, F2 = to_dev(grf(shape, 31)), to_dev(grf(shape, 32))
+    a = gb.Solver(shape, prec="mixed")
+    b = gb.Solver(shape, prec="mixed")
+    ref1, st1 = a.solve(F1, tol=1e-8)
+    ref2, st2 = b.solve(F2, tol=1e-8)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    s1.wait_stream(torch.cuda.current_stream())
+    s2.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s1):
+        p1, t1 = a.solve(F1, tol=1e-8)
+    with torch.cuda.stream(s2):
+        p2, t2 = b.solve(F2, tol=1e-8)
+        q2, _ = b.solve(F1, p2.clone(), tol=1e-8)
+    torch.cuda.synchronize()
+    assert (t1.cycles, t2.cycles) == (st1.cycles, st2.cycles)
+    assert torch.equal(p1, ref1) and torch.equal(p2, ref2)
+    ref = flat.fft_solve(grf(shape, 31))
+    assert np.linalg.norm(q2.cpu().numpy() - ref) / np.linalg.norm(ref) < 1e-7
