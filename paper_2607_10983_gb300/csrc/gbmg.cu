@@ -18,6 +18,7 @@ thread_local std::string g_last_error;
 
 static std::atomic<long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 gbmg_status fail(gbmg_status s, const std::string& msg) {
@@ -37,6 +38,9 @@ using namespace gbmg;
 // ------------------------------------------------------------------ context
 
 gbmg_ctx::~gbmg_ctx() {
+  for (cudaGraphExec_t g : cyc_exec)
+    if (g) cudaGraphExecDestroy(g);
+  if (cap_stream) cudaStreamDestroy(cap_stream);
   for (auto& v : prof_ev)
     for (cudaEvent_t e : v) cudaEventDestroy(e);
   for (cudaStream_t s : {seq_h2d, seq_d2h})

@@ -9,6 +9,7 @@ namespace gbmg {
 
 // Counts kernel launches made by this library (process-wide, for measurement).
 void note_launch();
+void note_launches(long long k);  // k launches at once (graph replays; negative: captured, not run)
 long long launch_count();
 
 // Number of per-block partial sums a reduction-producing launch writes for a level.

@@ -256,6 +256,68 @@ gbmg_status solve_fp64(gbmg_ctx* c, const double* F, double* phi, double tol, in
   return GBMG_OK;
 }
 
+// One cycle of the fused mixed solve on c->stream: V-cycle from zero on r0, phi_nxt =
+// phi_cur + e and r_nxt = F - m - A phi_nxt in double-float with their norms, and the
+// scalars copied to pinned host memory (read after the stream is synchronised).
+gbmg_status fused_cycle(gbmg_ctx* c, const float2* phi_cur, float2* phi_nxt, const float* r0, float* r_nxt) {
+  const Level& L0 = c->lv[0];
+  double* sc = c->scal;
+  double* part = c->partials;
+  double* part2 = c->partials + 2 * c->npart;
+  float* e = nullptr;
+  TRYS(vcycle_fused(c, 0, e, r0));
+  {
+    ProfScope ps(c, GBMG_PROF_DF0);
+    TRY(launch_df_update_residual(c->stream, L0.d, phi_cur, e, c->F_df, sc + S_MEAN_F, phi_nxt, r_nxt, part, part2,
+                                  nullptr));
+  }
+  TRY(launch_finalize(c->stream, part, df_update_residual_partials(L0.d), sc + S_R2, 1.0));
+  TRY(launch_scalars_to_host(c->stream, c->scal, c->host_scal_dev, 8));
+  return GBMG_OK;
+}
+
+// Cycles of small meshes run as a CUDA graph (their kernels are short, so launching them
+// one by one from the host would leave the GPU waiting): one graph per parity of the
+// potential buffers, captured on a private stream the first time that parity comes up
+// after a cycle of the context has run eagerly (which sets every kernel's one-time
+// attributes), then launched on c->stream.  Their arguments are the context's own
+// buffers and constants, so the same graphs serve every later solve.  Not while kernel
+// families are being timed, nor with rounded coarse corrections.  A failed capture
+// leaves the context on eager launches.
+bool cycle_graphs(const gbmg_ctx* c) {
+  return !c->cyc_off && c->prof_mask == 0 && c->o.coarse_store == 0 && ncell(c->lv[0].d) <= (1LL << 21);
+}
+
+gbmg_status capture_cycle(gbmg_ctx* c, int par, const float2* phi_cur, float2* phi_nxt, const float* r0,
+                          float* r_nxt) {
+  if (!c->cap_stream) TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  cudaStream_t user = c->stream;
+  const long long k0 = launch_count();
+  cudaGraph_t g = nullptr;
+  c->stream = c->cap_stream;
+  cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+  gbmg_status s = GBMG_OK;
+  if (e == cudaSuccess) {
+    s = fused_cycle(c, phi_cur, phi_nxt, r0, r_nxt);
+    const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
+    if (e2 != cudaSuccess) e = e2;
+  }
+  c->stream = user;
+  const long long nk = launch_count() - k0;  // kernels recorded, not run
+  note_launches(-nk);
+  cudaGraphExec_t x = nullptr;
+  if (e == cudaSuccess && s == GBMG_OK && g) e = cudaGraphInstantiate(&x, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess || s != GBMG_OK || !x) {
+    (void)cudaGetLastError();
+    c->cyc_off = true;
+    return GBMG_OK;
+  }
+  c->cyc_exec[par] = x;
+  c->cyc_kernels[par] = nk;
+  return GBMG_OK;
+}
+
 gbmg_status solve_mixed(gbmg_ctx* c, const double* F, const double* phi, double* phi_out, double tol, int maxv,
                         gbmg_stats& st) {
   const Level& L0 = c->lv[0];
@@ -290,10 +352,27 @@ gbmg_status solve_mixed(gbmg_ctx* c, const double* F, const double* phi, double*
   float* r_alt = c->r_alt;
   bool have_sum = c->o.fused;  // the fused residual kernels also sum phi
   while (!mon.done()) {
+    if (c->o.fused && !c->o.krylov) {
+      const int par = phi_cur == c->phi_df ? 0 : 1;
+      if (c->cyc_warm && cycle_graphs(c) && !c->cyc_exec[par]) TRYS(capture_cycle(c, par, phi_cur, phi_nxt, r0, r_alt));
+      if (c->cyc_warm && cycle_graphs(c) && c->cyc_exec[par]) {
+        TRY(cudaGraphLaunch(c->cyc_exec[par], c->stream));
+        note_launches(c->cyc_kernels[par]);
+      } else {
+        TRYS(fused_cycle(c, phi_cur, phi_nxt, r0, r_alt));
+        c->cyc_warm = true;
+      }
+      std::swap(phi_cur, phi_nxt);
+      std::swap(r0, r_alt);
+      TRY(cudaStreamSynchronize(c->stream));
+      const double f2 = c->host_scal[S_F2], r2 = c->host_scal[S_R2];
+      rel = f2 > 0.0 ? std::sqrt(r2 / f2) : std::sqrt(r2);
+      if (mon.record(rel)) break;
+      continue;
+    }
     if (c->o.fused) {
       float* e = nullptr;
-      if (c->o.krylov) TRYS(pcg_correction(c, r0, e));
-      else TRYS(vcycle_fused(c, 0, e, r0));
+      TRYS(pcg_correction(c, r0, e));
       {
         ProfScope ps(c, GBMG_PROF_DF0);
         TRY(launch_df_update_residual(c->stream, L0.d, phi_cur, e, c->F_df, sc + S_MEAN_F, phi_nxt, r_alt, part,

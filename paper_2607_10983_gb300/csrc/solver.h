@@ -90,6 +90,13 @@ struct gbmg_ctx {
   double* seq_phi[2] = {nullptr, nullptr};  // and the iterate, ping-pong
   cudaStream_t seq_h2d = nullptr, seq_d2h = nullptr;
   cudaEvent_t seq_ev[7] = {};
+  // mixed fused solves of small meshes: one cycle as a CUDA graph per parity of the
+  // potential buffers (captured on a private stream on first use, launched on `stream`)
+  cudaGraphExec_t cyc_exec[2] = {nullptr, nullptr};
+  long long cyc_kernels[2] = {0, 0};
+  cudaStream_t cap_stream = nullptr;
+  bool cyc_off = false;   // a capture failed: this context launches its cycles one by one
+  bool cyc_warm = false;  // a cycle has run eagerly (the kernels' one-time attributes are set)
   ~gbmg_ctx();
 };
 

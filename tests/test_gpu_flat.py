@@ -490,3 +490,29 @@ def test_solves_on_side_streams_match_default_stream(gb):
     assert torch.equal(p1, ref1) and torch.equal(p2, ref2)
     ref = flat.fft_solve(grf(shape, 31))
     assert np.linalg.norm(q2.cpu().numpy() - ref) / np.linalg.norm(ref) < 1e-7
+
+
+@pytest.mark.parametrize("shape", [(64, 64, 64), (32, 48, 64), (56, 40, 112)])
+def test_cycle_graphs_match_eager_cycles(gb, shape):
+    # meshes of at most 128^3 run their cycles as CUDA graphs; with kernel timing on they
+    # are launched one by one: same iterates, cycles and residual histories, on a warm
+    # sequence of three sources, and the graph replays are counted as kernel launches
+    F = [to_dev(grf(shape, 60 + k)) for k in range(3)]
+    g = gb.Solver(shape, prec="mixed")
+    eager = gb.Solver(shape, prec="mixed")
+    eager.profile_begin(["down0", "up0", "df0"])
+    pg = torch.zeros_like(F[0])
+    pe = torch.zeros_like(F[0])
+    for f in F:
+        n0 = gb.launch_count()
+        _, sg = g.solve(f, pg, tol=1e-9)
+        ng = gb.launch_count() - n0
+        n0 = gb.launch_count()
+        _, se = eager.solve(f, pe, tol=1e-9)
+        ne = gb.launch_count() - n0
+        assert sg.cycles == se.cycles and sg.history == se.history
+        assert torch.equal(pg, pe)
+        assert ng == ne
+    eager.profile_end()
+    ref = flat.fft_solve(grf(shape, 62))
+    assert np.linalg.norm(pg.cpu().numpy() - ref) / np.linalg.norm(ref) < 1e-8
