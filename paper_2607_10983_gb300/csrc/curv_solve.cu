@@ -79,6 +79,30 @@ gbmg_status vcycle_curv(gbmg_ctx* c, int l, T*& e, T*& eo, const T* r, bool tr) 
 // Mixed-precision solve of L u = f (forward, f = src - weighted mean) or of the
 // transposed problem M^T u = src - mean(src) (tr).  u_in NULL starts from zero;
 // u_out NULL leaves the result in c->phi_df only.
+// One cycle of the curvilinear solve on c->stream: FP32 V-cycle on r0, phi += e in
+// double-float, r0 = the double-float residual and its norm, the scalars copied to pinned
+// host memory.  Its launches depend only on the context and the orientation, so after a
+// cycle has run eagerly it is captured once as a CUDA graph per orientation and replayed
+// (not while kernel families are timed; the coefficients change in place).
+gbmg_status curv_cycle(gbmg_ctx* c, bool tr, float* r0) {
+  const Level& L0 = c->lv[0];
+  const long long n = ncell(L0.d);
+  double* sc = c->scal;
+  float* e = (float*)L0.e;
+  float* eo = (float*)L0.e2;
+  if (c->o.nu1 == 0) TRY(cudaMemsetAsync(e, 0, (size_t)n * sizeof(float), c->stream));
+  TRYS(vcycle_curv<float>(c, 0, e, eo, r0, tr));
+  TRY(launch_df_update(c->stream, n, c->phi_df, e, nullptr));
+  {
+    ProfScope ps(c, GBMG_PROF_DF0);
+    TRY(launch_curv_df_residual(c->stream, L0.d, L0.cc, c->F_df, sc + S_MEAN_F, tr ? 0 : 1, c->phi_df, curv_form(c, tr),
+                                r0, c->partials, nullptr));
+  }
+  TRY(launch_finalize(c->stream, c->partials, curv_partial_count(L0.d), sc + S_R2, 1.0));
+  TRY(launch_scalars_to_host(c->stream, c->scal, c->host_scal_dev, 8));
+  return GBMG_OK;
+}
+
 gbmg_status curv_solve_impl(gbmg_ctx* c, const double* src, const double* u_in, double* u_out, double tol, int maxv,
                             gbmg_stats& st, bool tr) {
   const Level& L0 = c->lv[0];
@@ -112,19 +136,19 @@ gbmg_status curv_solve_impl(gbmg_ctx* c, const double* src, const double* u_in, 
   TRYS(read_rel(c, rel));
   Monitor mon(st, tol, maxv);
   mon.start(rel);
+  const int k = tr ? 1 : 0;
   while (!mon.done()) {
-    float* e = (float*)L0.e;
-    float* eo = (float*)L0.e2;
-    if (c->o.nu1 == 0) TRY(cudaMemsetAsync(e, 0, (size_t)n * sizeof(float), c->stream));
-    TRYS(vcycle_curv<float>(c, 0, e, eo, r0, tr));
-    TRY(launch_df_update(c->stream, n, c->phi_df, e, nullptr));
-    {
-      ProfScope ps(c, GBMG_PROF_DF0);
-      TRY(launch_curv_df_residual(c->stream, L0.d, L0.cc, c->F_df, sc + S_MEAN_F, tr ? 0 : 1, c->phi_df, itr, r0,
-                                  part, nullptr));
+    const bool graphs = c->curv_warm[k] && !c->cyc_off && c->prof_mask == 0;
+    if (graphs && !c->curv_exec[k])
+      TRYS(capture_graph(c, [&]() { return curv_cycle(c, tr, r0); }, c->curv_exec[k], c->curv_kernels[k]));
+    if (graphs && c->curv_exec[k]) {
+      TRY(cudaGraphLaunch(c->curv_exec[k], c->stream));
+      note_launches(c->curv_kernels[k]);
+    } else {
+      TRYS(curv_cycle(c, tr, r0));
+      c->curv_warm[k] = true;
     }
-    TRY(launch_finalize(c->stream, part, pc, sc + S_R2, 1.0));
-    TRYS(read_rel(c, rel));
+    TRYS(rel_from_host(c, rel));
     if (mon.record(rel)) break;
   }
   if (u_out) {

@@ -40,6 +40,8 @@ using namespace gbmg;
 gbmg_ctx::~gbmg_ctx() {
   for (cudaGraphExec_t g : cyc_exec)
     if (g) cudaGraphExecDestroy(g);
+  for (cudaGraphExec_t g : curv_exec)
+    if (g) cudaGraphExecDestroy(g);
   if (cap_stream) cudaStreamDestroy(cap_stream);
   for (auto& v : prof_ev)
     for (cudaEvent_t e : v) cudaEventDestroy(e);

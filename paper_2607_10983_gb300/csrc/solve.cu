@@ -288,36 +288,6 @@ bool cycle_graphs(const gbmg_ctx* c) {
   return !c->cyc_off && c->prof_mask == 0 && c->o.coarse_store == 0 && ncell(c->lv[0].d) <= (1LL << 21);
 }
 
-gbmg_status capture_cycle(gbmg_ctx* c, int par, const float2* phi_cur, float2* phi_nxt, const float* r0,
-                          float* r_nxt) {
-  if (!c->cap_stream) TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
-  cudaStream_t user = c->stream;
-  const long long k0 = launch_count();
-  cudaGraph_t g = nullptr;
-  c->stream = c->cap_stream;
-  cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
-  gbmg_status s = GBMG_OK;
-  if (e == cudaSuccess) {
-    s = fused_cycle(c, phi_cur, phi_nxt, r0, r_nxt);
-    const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
-    if (e2 != cudaSuccess) e = e2;
-  }
-  c->stream = user;
-  const long long nk = launch_count() - k0;  // kernels recorded, not run
-  note_launches(-nk);
-  cudaGraphExec_t x = nullptr;
-  if (e == cudaSuccess && s == GBMG_OK && g) e = cudaGraphInstantiate(&x, g, 0);
-  if (g) cudaGraphDestroy(g);
-  if (e != cudaSuccess || s != GBMG_OK || !x) {
-    (void)cudaGetLastError();
-    c->cyc_off = true;
-    return GBMG_OK;
-  }
-  c->cyc_exec[par] = x;
-  c->cyc_kernels[par] = nk;
-  return GBMG_OK;
-}
-
 gbmg_status solve_mixed(gbmg_ctx* c, const double* F, const double* phi, double* phi_out, double tol, int maxv,
                         gbmg_stats& st) {
   const Level& L0 = c->lv[0];
@@ -354,7 +324,9 @@ gbmg_status solve_mixed(gbmg_ctx* c, const double* F, const double* phi, double*
   while (!mon.done()) {
     if (c->o.fused && !c->o.krylov) {
       const int par = phi_cur == c->phi_df ? 0 : 1;
-      if (c->cyc_warm && cycle_graphs(c) && !c->cyc_exec[par]) TRYS(capture_cycle(c, par, phi_cur, phi_nxt, r0, r_alt));
+      if (c->cyc_warm && cycle_graphs(c) && !c->cyc_exec[par])
+        TRYS(capture_graph(c, [&]() { return fused_cycle(c, phi_cur, phi_nxt, r0, r_alt); }, c->cyc_exec[par],
+                           c->cyc_kernels[par]));
       if (c->cyc_warm && cycle_graphs(c) && c->cyc_exec[par]) {
         TRY(cudaGraphLaunch(c->cyc_exec[par], c->stream));
         note_launches(c->cyc_kernels[par]);
@@ -364,9 +336,7 @@ gbmg_status solve_mixed(gbmg_ctx* c, const double* F, const double* phi, double*
       }
       std::swap(phi_cur, phi_nxt);
       std::swap(r0, r_alt);
-      TRY(cudaStreamSynchronize(c->stream));
-      const double f2 = c->host_scal[S_F2], r2 = c->host_scal[S_R2];
-      rel = f2 > 0.0 ? std::sqrt(r2 / f2) : std::sqrt(r2);
+      TRYS(rel_from_host(c, rel));
       if (mon.record(rel)) break;
       continue;
     }

@@ -97,6 +97,10 @@ struct gbmg_ctx {
   cudaStream_t cap_stream = nullptr;
   bool cyc_off = false;   // a capture failed: this context launches its cycles one by one
   bool cyc_warm = false;  // a cycle has run eagerly (the kernels' one-time attributes are set)
+  // curvilinear solves: one cycle as a CUDA graph per orientation (forward, transposed)
+  cudaGraphExec_t curv_exec[2] = {nullptr, nullptr};
+  long long curv_kernels[2] = {0, 0};
+  bool curv_warm[2] = {false, false};
   ~gbmg_ctx();
 };
 
@@ -145,6 +149,50 @@ struct ProfScope {
     if (on && cudaEventRecord(c->prof_ev[f][2 * c->prof_n[f] + 1], c->stream) == cudaSuccess) c->prof_n[f] += 1;
   }
 };
+
+// Captures the launches `body` makes on c->stream into a CUDA graph, on the context's
+// private capture stream (the caller's may be the legacy default stream, which cannot be
+// captured), and instantiates it into `exec`; nothing runs.  The recorded launches are
+// taken off the launch count and their number goes to `kernels`.  If capturing or
+// instantiating fails, `exec` stays null and the context is switched to eager launches.
+template <class Body>
+gbmg_status capture_graph(gbmg_ctx* c, Body body, cudaGraphExec_t& exec, long long& kernels) {
+  if (!c->cap_stream) TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  cudaStream_t user = c->stream;
+  const long long k0 = launch_count();
+  cudaGraph_t g = nullptr;
+  c->stream = c->cap_stream;
+  cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+  gbmg_status s = GBMG_OK;
+  if (e == cudaSuccess) {
+    s = body();
+    const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
+    if (e2 != cudaSuccess) e = e2;
+  }
+  c->stream = user;
+  const long long nk = launch_count() - k0;
+  note_launches(-nk);
+  cudaGraphExec_t x = nullptr;
+  if (e == cudaSuccess && s == GBMG_OK && g) e = cudaGraphInstantiate(&x, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess || s != GBMG_OK || !x) {
+    (void)cudaGetLastError();
+    c->cyc_off = true;
+    return GBMG_OK;
+  }
+  exec = x;
+  kernels = nk;
+  return GBMG_OK;
+}
+
+// The relative residual from the scalars a cycle copied to pinned host memory, after
+// waiting for the stream.
+inline gbmg_status rel_from_host(gbmg_ctx* c, double& rel) {
+  TRY(cudaStreamSynchronize(c->stream));
+  const double f2 = c->host_scal[S_F2], r2 = c->host_scal[S_R2];
+  rel = f2 > 0.0 ? std::sqrt(r2 / f2) : std::sqrt(r2);
+  return GBMG_OK;
+}
 
 // Reads ||F||^2 and ||r||^2 back and returns the relative residual.
 inline gbmg_status read_rel(gbmg_ctx* c, double& rel) {

@@ -174,3 +174,27 @@ def test_zero_iterate_sweep_equals_full_sweep(gb, shape, sym):
             full = s.curv_smooth(level, torch.zeros_like(r), r, transpose=tr)
             point = s.curv_smooth(level, None, r, transpose=tr)
             assert torch.equal(full.view(torch.int32), point.view(torch.int32))   # bit for bit
+
+
+@pytest.mark.parametrize("sym", [False, True])
+def test_cycle_graphs_match_eager_cycles(gb, sym):
+    # the curvilinear cycles run as CUDA graphs (one per orientation) unless kernel
+    # families are timed: same iterates, cycles and histories for forward and adjoint
+    # solves, also after the geometry has changed in place (a second psi)
+    shape = SHAPES[0]
+    g = gb.Solver(shape, op="curv", curv_sym=sym)
+    e = gb.Solver(shape, op="curv", curv_sym=sym)
+    e.profile_begin(["curv0", "df0"])
+    pbar = to_dev(np.random.default_rng(71).standard_normal(shape))
+    for k in range(2):
+        psi = to_dev(smoothed_grf(shape, 72 + k, 1.5, 0.4))
+        delta = to_dev(grf(shape, 74 + k))
+        pg, sg = g.solve(delta, tol=1e-9, max_vcycles=200, psi=psi)
+        pe, se = e.solve(delta, tol=1e-9, max_vcycles=200, psi=psi)
+        assert sg.cycles == se.cycles and sg.history == se.history
+        assert torch.equal(pg, pe)
+        dg, qg, ag = g.solve_adjoint(pbar, phi=pg, source=delta, want_psi_bar=True, tol=1e-9, max_vcycles=200)
+        de, qe, ae = e.solve_adjoint(pbar, phi=pe, source=delta, want_psi_bar=True, tol=1e-9, max_vcycles=200)
+        assert ag.cycles == ae.cycles and ag.history == ae.history
+        assert torch.equal(dg, de) and torch.equal(qg, qe)
+    e.profile_end()
