@@ -125,6 +125,15 @@ void mg_destroy(gbmg_ctx* ctx);
 /* Queue later work on `cuda_stream` (a cudaStream_t; NULL = legacy default stream). */
 gbmg_status mg_set_stream(gbmg_ctx* ctx, void* cuda_stream);
 
+/* Cycle graphs (default on).  A mixed fused flat solve (with FP32 coarse corrections)
+ * and a curvilinear solve run each V-cycle of the defect correction (Sec. 3.2) as one
+ * CUDA graph launch: the cycle's launches are captured once per context (per buffer
+ * parity or orientation, after one cycle has run eagerly) and replayed; the host still
+ * checks convergence after every cycle.  Results are the same bits either way.
+ * enable = 0 launches every kernel of every cycle from the host.  Timed kernel families
+ * (mg_profile_begin) are timed inside the graphs by event nodes. */
+gbmg_status mg_set_cycle_graphs(gbmg_ctx* ctx, int enable);
+
 /* Curvilinear contexts only: set the deformation potential psi (nx*ny*nz doubles,
  * cell units, periodic).  psi is restricted to every level by full weighting and the
  * triad A = I + Hess psi, sqrt(g) = det A and B = sqrt(g) g^-1 are rebuilt per level
@@ -323,7 +332,8 @@ typedef enum {
 } gbmg_prof_family;
 
 /* Start timing the kernel families whose bits (1 << family) are set in family_mask
- * (waits for the stream; clears earlier records). */
+ * (waits for the stream; clears earlier records).  Inside cycle graphs at most 8
+ * launches of a family per cycle are timed. */
 gbmg_status mg_profile_begin(gbmg_ctx* ctx, int family_mask);
 /* Number of timed launches of `family` since mg_profile_begin and their summed device
  * time in milliseconds (waits for the stream; timing continues). */

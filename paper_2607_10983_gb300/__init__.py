@@ -76,6 +76,7 @@ _SIGS = {
     "mg_setup": (_S, [ctypes.POINTER(_P), _I, _I, _I, _I, _I, ctypes.POINTER(_Opts), _P]),
     "mg_destroy": (None, [_P]),
     "mg_set_stream": (_S, [_P, _P]),
+    "mg_set_cycle_graphs": (_S, [_P, ctypes.c_int]),
     "mg_solve": (_S, [_P, _P, _P, _P, _D, _I, ctypes.POINTER(_Stats)]),
     "mg_solve_host": (_S, [_P, _P, _P, _D, _I, ctypes.POINTER(_Stats)]),
     "mg_solve_host_sequence": (_S, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_P), _P, _D, _I,
@@ -415,6 +416,10 @@ class Solver:
         return [Stats.from_c(st[t]) for t in range(count)]
 
     # -- measurement
+    def set_cycle_graphs(self, enable: bool):
+        """Run each V-cycle as one CUDA graph launch (default) or launch every kernel eagerly."""
+        _check(lib().mg_set_cycle_graphs(self._c(), 1 if enable else 0))
+
     def profile_begin(self, families):
         """Time every launch of the named kernel families (see PROF) with CUDA events."""
         mask = 0

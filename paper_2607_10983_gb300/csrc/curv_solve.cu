@@ -83,7 +83,7 @@ gbmg_status vcycle_curv(gbmg_ctx* c, int l, T*& e, T*& eo, const T* r, bool tr) 
 // double-float, r0 = the double-float residual and its norm, the scalars copied to pinned
 // host memory.  Its launches depend only on the context and the orientation, so after a
 // cycle has run eagerly it is captured once as a CUDA graph per orientation and replayed
-// (not while kernel families are timed; the coefficients change in place).
+// (the coefficients change in place; timed families are timed by event nodes).
 gbmg_status curv_cycle(gbmg_ctx* c, bool tr, float* r0) {
   const Level& L0 = c->lv[0];
   const long long n = ncell(L0.d);
@@ -138,10 +138,12 @@ gbmg_status curv_solve_impl(gbmg_ctx* c, const double* src, const double* u_in, 
   mon.start(rel);
   const int k = tr ? 1 : 0;
   while (!mon.done()) {
-    const bool graphs = c->curv_warm[k] && !c->cyc_off && c->prof_mask == 0;
+    sync_graph_mask(c);
+    const bool graphs = c->curv_warm[k] && !c->cyc_off;
     if (graphs && !c->curv_exec[k])
-      TRYS(capture_graph(c, [&]() { return curv_cycle(c, tr, r0); }, c->curv_exec[k], c->curv_kernels[k]));
-    if (graphs && c->curv_exec[k]) {
+      TRYS(capture_graph(c, 2 + k, [&]() { return curv_cycle(c, tr, r0); }, c->curv_exec[k], c->curv_kernels[k]));
+    const bool replay = graphs && c->curv_exec[k];
+    if (replay) {
       TRY(cudaGraphLaunch(c->curv_exec[k], c->stream));
       note_launches(c->curv_kernels[k]);
     } else {
@@ -149,6 +151,7 @@ gbmg_status curv_solve_impl(gbmg_ctx* c, const double* src, const double* u_in, 
       c->curv_warm[k] = true;
     }
     TRYS(rel_from_host(c, rel));
+    if (replay) gprof_collect(c, 2 + k);
     if (mon.record(rel)) break;
   }
   if (u_out) {

@@ -42,6 +42,11 @@ gbmg_ctx::~gbmg_ctx() {
     if (g) cudaGraphExecDestroy(g);
   for (cudaGraphExec_t g : curv_exec)
     if (g) cudaGraphExecDestroy(g);
+  for (auto& slot : gprof_ev)
+    for (auto& fam : slot)
+      for (auto& pr : fam)
+        for (cudaEvent_t ev : pr)
+          if (ev) cudaEventDestroy(ev);
   if (cap_stream) cudaStreamDestroy(cap_stream);
   for (auto& v : prof_ev)
     for (cudaEvent_t e : v) cudaEventDestroy(e);
@@ -277,6 +282,17 @@ extern "C" gbmg_status mg_set_stream(gbmg_ctx* ctx, void* s) {
   return GBMG_OK;
 }
 
+extern "C" gbmg_status mg_set_cycle_graphs(gbmg_ctx* ctx, int enable) {
+  if (!ctx) return fail(GBMG_ERR_INVALID_ARG, "mg_set_cycle_graphs: ctx is NULL");
+  DeviceGuard g(ctx->device);
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "mg_set_cycle_graphs");
+  ctx->cyc_off = enable == 0;
+  ctx->graph_mask = -1;  // drop the graphs captured so far
+  sync_graph_mask(ctx);
+  return GBMG_OK;
+}
+
 extern "C" int mg_num_levels(const gbmg_ctx* ctx) { return ctx ? ctx->L : 0; }
 
 extern "C" gbmg_status mg_level_dims(const gbmg_ctx* ctx, int level, int* nx, int* ny, int* nz) {
@@ -304,6 +320,19 @@ extern "C" gbmg_status mg_profile_begin(gbmg_ctx* ctx, int family_mask) {
   if (e != cudaSuccess) return cuda_fail(e, "mg_profile_begin");
   ctx->prof_mask = family_mask & ~1;
   for (int& n : ctx->prof_n) n = 0;
+  for (int& n : ctx->prof_gn) n = 0;
+  for (double& t : ctx->prof_gms) t = 0.0;
+  // event pairs for the cycle graphs' timed launches (created here, outside any capture)
+  for (auto& slot : ctx->gprof_ev)
+    for (int f = 1; f < 8; ++f) {
+      if (!(ctx->prof_mask >> f & 1)) continue;
+      for (auto& pr : slot[f])
+        for (cudaEvent_t& ev : pr)
+          if (!ev) {
+            e = cudaEventCreate(&ev);
+            if (e != cudaSuccess) return cuda_fail(e, "mg_profile_begin: cudaEventCreate");
+          }
+    }
   return GBMG_OK;
 }
 
@@ -319,8 +348,8 @@ extern "C" gbmg_status mg_profile_read(gbmg_ctx* ctx, int family, int* launches,
     if (e != cudaSuccess) return cuda_fail(e, "mg_profile_read: cudaEventElapsedTime");
     ms += t;
   }
-  if (launches) *launches = ctx->prof_n[family];
-  if (total_ms) *total_ms = ms;
+  if (launches) *launches = ctx->prof_n[family] + ctx->prof_gn[family];
+  if (total_ms) *total_ms = ms + ctx->prof_gms[family];
   return GBMG_OK;
 }
 
@@ -328,5 +357,7 @@ extern "C" gbmg_status mg_profile_end(gbmg_ctx* ctx) {
   if (!ctx) return fail(GBMG_ERR_INVALID_ARG, "mg_profile_end: ctx is NULL");
   ctx->prof_mask = 0;
   for (int& n : ctx->prof_n) n = 0;
+  for (int& n : ctx->prof_gn) n = 0;
+  for (double& t : ctx->prof_gms) t = 0.0;
   return GBMG_OK;
 }

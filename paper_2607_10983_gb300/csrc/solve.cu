@@ -276,17 +276,16 @@ gbmg_status fused_cycle(gbmg_ctx* c, const float2* phi_cur, float2* phi_nxt, con
   return GBMG_OK;
 }
 
-// Cycles of small meshes run as a CUDA graph (their kernels are short, so launching them
-// one by one from the host would leave the GPU waiting): one graph per parity of the
-// potential buffers, captured on a private stream the first time that parity comes up
-// after a cycle of the context has run eagerly (which sets every kernel's one-time
-// attributes), then launched on c->stream.  Their arguments are the context's own
-// buffers and constants, so the same graphs serve every later solve.  Not while kernel
-// families are being timed, nor with rounded coarse corrections.  A failed capture
-// leaves the context on eager launches.
-bool cycle_graphs(const gbmg_ctx* c) {
-  return !c->cyc_off && c->prof_mask == 0 && c->o.coarse_store == 0 && ncell(c->lv[0].d) <= (1LL << 21);
-}
+// Cycles run as CUDA graphs (on small meshes the kernels are short, so launching them
+// one by one from the host would leave the GPU waiting; on large ones the host is ahead
+// except right after each cycle's convergence check): one graph per parity of the
+// potential buffers, captured the first time that parity comes up after a cycle of the
+// context has run eagerly (which sets every kernel's one-time attributes), then launched
+// on c->stream.  Their arguments are the context's own buffers and constants, so the
+// same graphs serve every later solve.  Timed kernel families are timed by event nodes
+// of the graphs (read after each replay).  Not with rounded coarse corrections.  A failed
+// capture leaves the context on eager launches.
+bool cycle_graphs(const gbmg_ctx* c) { return !c->cyc_off && c->o.coarse_store == 0; }
 
 gbmg_status solve_mixed(gbmg_ctx* c, const double* F, const double* phi, double* phi_out, double tol, int maxv,
                         gbmg_stats& st) {
@@ -324,10 +323,12 @@ gbmg_status solve_mixed(gbmg_ctx* c, const double* F, const double* phi, double*
   while (!mon.done()) {
     if (c->o.fused && !c->o.krylov) {
       const int par = phi_cur == c->phi_df ? 0 : 1;
+      sync_graph_mask(c);
       if (c->cyc_warm && cycle_graphs(c) && !c->cyc_exec[par])
-        TRYS(capture_graph(c, [&]() { return fused_cycle(c, phi_cur, phi_nxt, r0, r_alt); }, c->cyc_exec[par],
+        TRYS(capture_graph(c, par, [&]() { return fused_cycle(c, phi_cur, phi_nxt, r0, r_alt); }, c->cyc_exec[par],
                            c->cyc_kernels[par]));
-      if (c->cyc_warm && cycle_graphs(c) && c->cyc_exec[par]) {
+      const bool replay = c->cyc_warm && cycle_graphs(c) && c->cyc_exec[par];
+      if (replay) {
         TRY(cudaGraphLaunch(c->cyc_exec[par], c->stream));
         note_launches(c->cyc_kernels[par]);
       } else {
@@ -337,6 +338,7 @@ gbmg_status solve_mixed(gbmg_ctx* c, const double* F, const double* phi, double*
       std::swap(phi_cur, phi_nxt);
       std::swap(r0, r_alt);
       TRYS(rel_from_host(c, rel));
+      if (replay) gprof_collect(c, par);
       if (mon.record(rel)) break;
       continue;
     }

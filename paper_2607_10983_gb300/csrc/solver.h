@@ -90,8 +90,8 @@ struct gbmg_ctx {
   double* seq_phi[2] = {nullptr, nullptr};  // and the iterate, ping-pong
   cudaStream_t seq_h2d = nullptr, seq_d2h = nullptr;
   cudaEvent_t seq_ev[7] = {};
-  // mixed fused solves of small meshes: one cycle as a CUDA graph per parity of the
-  // potential buffers (captured on a private stream on first use, launched on `stream`)
+  // mixed fused solves: one cycle as a CUDA graph per parity of the potential buffers
+  // (captured on a private stream on first use, launched on `stream`)
   cudaGraphExec_t cyc_exec[2] = {nullptr, nullptr};
   long long cyc_kernels[2] = {0, 0};
   cudaStream_t cap_stream = nullptr;
@@ -101,6 +101,16 @@ struct gbmg_ctx {
   cudaGraphExec_t curv_exec[2] = {nullptr, nullptr};
   long long curv_kernels[2] = {0, 0};
   bool curv_warm[2] = {false, false};
+  // kernel timing inside the cycle graphs: per graph slot (flat parity 0 / 1, curvilinear
+  // orientation 0 / 1), family and timed launch an event pair that the graph's nodes record
+  // on every replay; read after each replay into the per-family totals
+  static constexpr int GSLOTS = 4, GPAIRS = 8;
+  cudaEvent_t gprof_ev[GSLOTS][8][GPAIRS][2] = {};
+  int gprof_cnt[GSLOTS][8] = {};
+  int cap_slot = -1;            // slot of the graph being captured (-1: none)
+  int graph_mask = 0;           // prof_mask the cycle graphs were captured with
+  double prof_gms[8] = {};      // graph-timed milliseconds and launches per family
+  int prof_gn[8] = {};
   ~gbmg_ctx();
 };
 
@@ -134,8 +144,20 @@ struct ProfScope {
   gbmg_ctx* c;
   int f;
   bool on = false;
+  int k = -1;  // pair of the cycle graph being captured (-1: eager)
   ProfScope(gbmg_ctx* ctx, int family) : c(ctx), f(family) {
     if (family <= GBMG_PROF_OFF || family > 7 || !(c->prof_mask >> family & 1)) return;
+    if (c->cap_slot >= 0) {
+      // inside a capture: the events were created by mg_profile_begin; launches of a
+      // family beyond GPAIRS per cycle are not timed
+      const int n = c->gprof_cnt[c->cap_slot][f];
+      cudaEvent_t* p = c->gprof_ev[c->cap_slot][f][n < gbmg_ctx::GPAIRS ? n : 0];
+      if (n >= gbmg_ctx::GPAIRS || !p[0] || !p[1]) return;
+      // (external: an event-record node of the graph, not a capture dependency)
+      on = cudaEventRecordWithFlags(p[0], c->stream, cudaEventRecordExternal) == cudaSuccess;
+      k = n;
+      return;
+    }
     std::vector<cudaEvent_t>& ev = c->prof_ev[f];
     const size_t need = 2 * (size_t)c->prof_n[f] + 2;
     while (ev.size() < need) {
@@ -146,9 +168,42 @@ struct ProfScope {
     on = cudaEventRecord(ev[2 * c->prof_n[f]], c->stream) == cudaSuccess;
   }
   ~ProfScope() {
-    if (on && cudaEventRecord(c->prof_ev[f][2 * c->prof_n[f] + 1], c->stream) == cudaSuccess) c->prof_n[f] += 1;
+    if (!on) return;
+    if (k >= 0) {
+      if (cudaEventRecordWithFlags(c->gprof_ev[c->cap_slot][f][k][1], c->stream, cudaEventRecordExternal) == cudaSuccess)
+        c->gprof_cnt[c->cap_slot][f] = k + 1;
+      return;
+    }
+    if (cudaEventRecord(c->prof_ev[f][2 * c->prof_n[f] + 1], c->stream) == cudaSuccess) c->prof_n[f] += 1;
   }
 };
+
+// Drops the cycle graphs when the set of timed families has changed since they were
+// captured (they are captured again, with or without event nodes).
+inline void sync_graph_mask(gbmg_ctx* c) {
+  if (c->graph_mask == c->prof_mask) return;
+  for (cudaGraphExec_t& g : c->cyc_exec)
+    if (g) cudaGraphExecDestroy(g), g = nullptr;
+  for (cudaGraphExec_t& g : c->curv_exec)
+    if (g) cudaGraphExecDestroy(g), g = nullptr;
+  for (auto& row : c->gprof_cnt)
+    for (int& n : row) n = 0;
+  c->graph_mask = c->prof_mask;
+}
+
+// After a replay of the graph in `slot` has finished: its timed launches into the totals.
+inline void gprof_collect(gbmg_ctx* c, int slot) {
+  for (int f = 1; f < 8; ++f)
+    for (int k = 0; k < c->gprof_cnt[slot][f]; ++k) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, c->gprof_ev[slot][f][k][0], c->gprof_ev[slot][f][k][1]) == cudaSuccess) {
+        c->prof_gms[f] += t;
+        c->prof_gn[f] += 1;
+      } else {
+        (void)cudaGetLastError();  // not counted; leaves no error behind for later launches
+      }
+    }
+}
 
 // Captures the launches `body` makes on c->stream into a CUDA graph, on the context's
 // private capture stream (the caller's may be the legacy default stream, which cannot be
@@ -156,12 +211,14 @@ struct ProfScope {
 // taken off the launch count and their number goes to `kernels`.  If capturing or
 // instantiating fails, `exec` stays null and the context is switched to eager launches.
 template <class Body>
-gbmg_status capture_graph(gbmg_ctx* c, Body body, cudaGraphExec_t& exec, long long& kernels) {
+gbmg_status capture_graph(gbmg_ctx* c, int slot, Body body, cudaGraphExec_t& exec, long long& kernels) {
   if (!c->cap_stream) TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
   cudaStream_t user = c->stream;
   const long long k0 = launch_count();
   cudaGraph_t g = nullptr;
   c->stream = c->cap_stream;
+  for (int& n : c->gprof_cnt[slot]) n = 0;
+  c->cap_slot = slot;
   cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
   gbmg_status s = GBMG_OK;
   if (e == cudaSuccess) {
@@ -169,6 +226,7 @@ gbmg_status capture_graph(gbmg_ctx* c, Body body, cudaGraphExec_t& exec, long lo
     const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
     if (e2 != cudaSuccess) e = e2;
   }
+  c->cap_slot = -1;
   c->stream = user;
   const long long nk = launch_count() - k0;
   note_launches(-nk);

@@ -178,12 +178,14 @@ def test_zero_iterate_sweep_equals_full_sweep(gb, shape, sym):
 
 @pytest.mark.parametrize("sym", [False, True])
 def test_cycle_graphs_match_eager_cycles(gb, sym):
-    # the curvilinear cycles run as CUDA graphs (one per orientation) unless kernel
-    # families are timed: same iterates, cycles and histories for forward and adjoint
-    # solves, also after the geometry has changed in place (a second psi)
+    # the curvilinear cycles run as CUDA graphs (one per orientation) unless switched
+    # off: same iterates, cycles and histories for forward and adjoint solves, also after
+    # the geometry has changed in place (a second psi), and the same timed launches
     shape = SHAPES[0]
     g = gb.Solver(shape, op="curv", curv_sym=sym)
     e = gb.Solver(shape, op="curv", curv_sym=sym)
+    e.set_cycle_graphs(False)
+    g.profile_begin(["curv0", "df0"])
     e.profile_begin(["curv0", "df0"])
     pbar = to_dev(np.random.default_rng(71).standard_normal(shape))
     for k in range(2):
@@ -197,4 +199,8 @@ def test_cycle_graphs_match_eager_cycles(gb, sym):
         de, qe, ae = e.solve_adjoint(pbar, phi=pe, source=delta, want_psi_bar=True, tol=1e-9, max_vcycles=200)
         assert ag.cycles == ae.cycles and ag.history == ae.history
         assert torch.equal(dg, de) and torch.equal(qg, qe)
+    for fam in ("curv0", "df0"):
+        (cg, tg), (ce, te) = g.profile_read(fam), e.profile_read(fam)
+        assert cg == ce > 0 and tg > 0.0 and te > 0.0
+    g.profile_end()
     e.profile_end()

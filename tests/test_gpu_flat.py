@@ -494,13 +494,17 @@ def test_solves_on_side_streams_match_default_stream(gb):
 
 @pytest.mark.parametrize("shape", [(64, 64, 64), (32, 48, 64), (56, 40, 112)])
 def test_cycle_graphs_match_eager_cycles(gb, shape):
-    # meshes of at most 128^3 run their cycles as CUDA graphs; with kernel timing on they
-    # are launched one by one: same iterates, cycles and residual histories, on a warm
-    # sequence of three sources, and the graph replays are counted as kernel launches
+    # mixed fused solves run their cycles as CUDA graphs unless switched off: same
+    # iterates, cycles and residual histories on a warm sequence of three sources, the
+    # graph replays counted as kernel launches, and the timed families (event nodes inside
+    # the graphs) timed at the same launches
     F = [to_dev(grf(shape, 60 + k)) for k in range(3)]
     g = gb.Solver(shape, prec="mixed")
     eager = gb.Solver(shape, prec="mixed")
-    eager.profile_begin(["down0", "up0", "df0"])
+    eager.set_cycle_graphs(False)
+    fams = ["down0", "up0", "df0"]
+    g.profile_begin(fams)
+    eager.profile_begin(fams)
     pg = torch.zeros_like(F[0])
     pe = torch.zeros_like(F[0])
     for f in F:
@@ -513,6 +517,11 @@ def test_cycle_graphs_match_eager_cycles(gb, shape):
         assert sg.cycles == se.cycles and sg.history == se.history
         assert torch.equal(pg, pe)
         assert ng == ne
+    for fam in fams:  # (meshes below 2^18 cells have no fused legs on level 0)
+        (cg, tg), (ce, te) = g.profile_read(fam), eager.profile_read(fam)
+        assert cg == ce and (cg == 0 or (tg > 0.0 and te > 0.0))
+    assert g.profile_read("df0")[0] > 0
+    g.profile_end()
     eager.profile_end()
     ref = flat.fft_solve(grf(shape, 62))
     assert np.linalg.norm(pg.cpu().numpy() - ref) / np.linalg.norm(ref) < 1e-8
