@@ -283,9 +283,9 @@ gbmg_status fused_cycle(gbmg_ctx* c, const float2* phi_cur, float2* phi_nxt, con
 // context has run eagerly (which sets every kernel's one-time attributes), then launched
 // on c->stream.  Their arguments are the context's own buffers and constants, so the
 // same graphs serve every later solve.  Timed kernel families are timed by event nodes
-// of the graphs (read after each replay).  Not with rounded coarse corrections.  A failed
-// capture leaves the context on eager launches.
-bool cycle_graphs(const gbmg_ctx* c) { return !c->cyc_off && c->o.coarse_store == 0; }
+// of the graphs (read after each replay).  A failed capture leaves the context on eager
+// launches.
+bool cycle_graphs(const gbmg_ctx* c) { return !c->cyc_off; }
 
 gbmg_status solve_mixed(gbmg_ctx* c, const double* F, const double* phi, double* phi_out, double tol, int maxv,
                         gbmg_stats& st) {
