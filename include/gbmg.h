@@ -125,8 +125,8 @@ void mg_destroy(gbmg_ctx* ctx);
 /* Queue later work on `cuda_stream` (a cudaStream_t; NULL = legacy default stream). */
 gbmg_status mg_set_stream(gbmg_ctx* ctx, void* cuda_stream);
 
-/* Cycle graphs (default on).  A mixed fused flat solve (plain V-cycle corrections, not
- * krylov) and a curvilinear solve run each V-cycle of the defect correction (Sec. 3.2) as one
+/* Cycle graphs (default on).  A mixed fused flat solve (V-cycle or krylov corrections)
+ * and a curvilinear solve run each V-cycle of the defect correction (Sec. 3.2) as one
  * CUDA graph launch: the cycle's launches are captured once per context (per buffer
  * parity or orientation, after one cycle has run eagerly) and replayed; the host still
  * checks convergence after every cycle.  Results are the same bits either way.

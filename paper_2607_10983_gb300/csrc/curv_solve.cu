@@ -132,7 +132,7 @@ gbmg_status curv_solve_impl(gbmg_ctx* c, const double* src, const double* u_in, 
                               part1));
   TRY(launch_finalize(c->stream, part, pc, sc + S_R2, 1.0));
   TRY(launch_finalize(c->stream, part1, pc, sc + S_F2, 1.0));
-  double rel;
+  double rel = 0.0;
   TRYS(read_rel(c, rel));
   Monitor mon(st, tol, maxv);
   mon.start(rel);

@@ -240,7 +240,7 @@ gbmg_status solve_fp64(gbmg_ctx* c, const double* F, double* phi, double tol, in
     return GBMG_OK;
   };
   TRYS(resnorm());
-  double rel;
+  double rel = 0.0;
   TRYS(read_rel(c, rel));
   Monitor mon(st, tol, maxv);
   mon.start(rel);
@@ -256,16 +256,18 @@ gbmg_status solve_fp64(gbmg_ctx* c, const double* F, double* phi, double tol, in
   return GBMG_OK;
 }
 
-// One cycle of the fused mixed solve on c->stream: V-cycle from zero on r0, phi_nxt =
-// phi_cur + e and r_nxt = F - m - A phi_nxt in double-float with their norms, and the
-// scalars copied to pinned host memory (read after the stream is synchronised).
-gbmg_status fused_cycle(gbmg_ctx* c, const float2* phi_cur, float2* phi_nxt, const float* r0, float* r_nxt) {
+// One cycle of the fused mixed solve on c->stream: the correction e of r0 (a V-cycle from
+// zero, or the preconditioned CG steps of krylov, which overwrite r0), phi_nxt = phi_cur +
+// e and r_nxt = F - m - A phi_nxt in double-float with their norms, and the scalars copied
+// to pinned host memory (read after the stream is synchronised).
+gbmg_status fused_cycle(gbmg_ctx* c, const float2* phi_cur, float2* phi_nxt, float* r0, float* r_nxt) {
   const Level& L0 = c->lv[0];
   double* sc = c->scal;
   double* part = c->partials;
   double* part2 = c->partials + 2 * c->npart;
   float* e = nullptr;
-  TRYS(vcycle_fused(c, 0, e, r0));
+  if (c->o.krylov) TRYS(pcg_correction(c, r0, e));
+  else TRYS(vcycle_fused(c, 0, e, r0));
   {
     ProfScope ps(c, GBMG_PROF_DF0);
     TRY(launch_df_update_residual(c->stream, L0.d, phi_cur, e, c->F_df, sc + S_MEAN_F, phi_nxt, r_nxt, part, part2,
@@ -312,7 +314,7 @@ gbmg_status solve_mixed(gbmg_ctx* c, const double* F, const double* phi, double*
     TRY(launch_finalize(c->stream, part, pc, sc + S_R2, 1.0));
     TRY(launch_finalize(c->stream, part1, pc, sc + S_F2, 1.0));
   }
-  double rel;
+  double rel = 0.0;
   TRYS(read_rel(c, rel));
   Monitor mon(st, tol, maxv);
   mon.start(rel);
@@ -321,7 +323,7 @@ gbmg_status solve_mixed(gbmg_ctx* c, const double* F, const double* phi, double*
   float* r_alt = c->r_alt;
   bool have_sum = c->o.fused;  // the fused residual kernels also sum phi
   while (!mon.done()) {
-    if (c->o.fused && !c->o.krylov) {
+    if (c->o.fused) {
       const int par = phi_cur == c->phi_df ? 0 : 1;
       sync_graph_mask(c);
       if (c->cyc_warm && cycle_graphs(c) && !c->cyc_exec[par])
@@ -342,18 +344,7 @@ gbmg_status solve_mixed(gbmg_ctx* c, const double* F, const double* phi, double*
       if (mon.record(rel)) break;
       continue;
     }
-    if (c->o.fused) {
-      float* e = nullptr;
-      TRYS(pcg_correction(c, r0, e));
-      {
-        ProfScope ps(c, GBMG_PROF_DF0);
-        TRY(launch_df_update_residual(c->stream, L0.d, phi_cur, e, c->F_df, sc + S_MEAN_F, phi_nxt, r_alt, part,
-                                      part2, nullptr));
-      }
-      std::swap(phi_cur, phi_nxt);
-      std::swap(r0, r_alt);
-      TRY(launch_finalize(c->stream, part, pu, sc + S_R2, 1.0));
-    } else {
+    {
       float* e = (float*)L0.e;
       float* eo = (float*)L0.e2;
       if (c->o.krylov) {

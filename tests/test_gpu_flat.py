@@ -525,3 +525,18 @@ def test_cycle_graphs_match_eager_cycles(gb, shape):
     eager.profile_end()
     ref = flat.fft_solve(grf(shape, 62))
     assert np.linalg.norm(pg.cpu().numpy() - ref) / np.linalg.norm(ref) < 1e-8
+
+
+def test_krylov_cycle_graphs_match_eager_cycles(gb):
+    # the MG-preconditioned CG corrections keep their scalars on the device, so their
+    # cycles are graph launches too: the same bits as launched one by one
+    shape = (64, 64, 64)
+    F = to_dev(grf(shape, 63))
+    g = gb.Solver(shape, prec="mixed", krylov=2)
+    e = gb.Solver(shape, prec="mixed", krylov=2)
+    e.set_cycle_graphs(False)
+    for _ in range(2):
+        pg, sg = g.solve(F, tol=1e-9)
+        pe, se = e.solve(F, tol=1e-9)
+        assert sg.cycles == se.cycles and sg.history == se.history
+        assert torch.equal(pg, pe)
